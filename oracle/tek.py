@@ -1,0 +1,131 @@
+"""Oracle for the twisted Eguchi-Kawai (TEK) pieces of one NSPT Langevin step.
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+Links are series U of shape (..., 4, T+1, N, N) with N = L^2.  All products
+are the oracle star product of ``polymat``.  Readings of the paper that these
+functions fix (each pinned by a test):
+
+* twist: z_{mu nu} = exp(2 pi i k eps_{mu nu} / L) with eps = +1 for mu < nu and
+  -1 for mu > nu, so z_{nu mu} = conj(z_{mu nu}) (Eq. 1, antisymmetric exponent);
+* staple: the second term of S_mu enters with a PLUS sign,
+  S_mu = U_mu star sum_{nu != mu} [ z_{mu nu} U_nu U_mu^+ U_nu^+
+                                   + conj(z_{mu nu}) U_nu^+ U_mu^+ U_nu ],
+  which is what differentiating the action of Eq. 1 gives (Eqs. 2-3 print a
+  minus; the finite-difference drift test fails for the minus sign);
+* drift: F^(k) = i [S^(k) - S^(k)^H - Tr(S^(k) - S^(k)^H)/N], with beta
+  absorbed by the rescaled time of Eq. 3;
+* Langevin step (Euler-Maruyama in the rescaled time):
+  X^(0) = 0, X^(1) = eps F^(1) + sqrt(2 eps) eta, X^(k>=2) = eps F^(k),
+  U' = exp_star(i X) star U; order 0 of U is left unchanged.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import polymat as pm
+
+
+def twist_phases(L: int, flux: int) -> np.ndarray:
+    """4 x 4 complex array z[mu, nu] = exp(2 pi i flux eps_{mu nu} / L); the
+    diagonal (never used) is set to 0."""
+    z = np.zeros((4, 4), np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            eps = 1 if mu < nu else -1
+            z[mu, nu] = np.exp(2j * np.pi * flux * eps / L)
+    return z
+
+
+def plaquette(U, z, mu: int, nu: int):
+    """Series of z_{mu nu} U_mu U_nu U_mu^+ U_nu^+ (the Eq. 1 plaquette)."""
+    Um, Un = U[..., mu, :, :, :], U[..., nu, :, :, :]
+    P = pm.star(pm.star(pm.star(Um, Un), pm.dagger(Um)), pm.dagger(Un))
+    return z[mu, nu] * P
+
+
+def action(U, z) -> np.ndarray:
+    """Order-truncated TEK action with beta stripped (Eq. 1):
+    S~^(k) = 12 N delta_{k0} - sum_{mu != nu} Tr[ (z U_mu U_nu U_mu^+ U_nu^+)^(k) ].
+    Returns shape (..., T+1), complex (real up to rounding)."""
+    U = np.asarray(U)
+    N = U.shape[-1]
+    T = U.shape[-3] - 1
+    S = np.zeros(U.shape[:-4] + (T + 1,), np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            P = plaquette(U, z, mu, nu)
+            S = S - np.trace(P, axis1=-2, axis2=-1)
+    S[..., 0] += 12 * N
+    return S
+
+
+def staple(U, z) -> np.ndarray:
+    """S_mu^(k) of Eq. 3 (plus sign on the second term, see the module
+    docstring), for mu = 0..3.  Shape (..., 4, T+1, N, N)."""
+    U = np.asarray(U)
+    out = np.zeros_like(U, dtype=np.complex128)
+    for mu in range(4):
+        Um = U[..., mu, :, :, :]
+        Umd = pm.dagger(Um)
+        inner = np.zeros_like(Um, dtype=np.complex128)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            Un = U[..., nu, :, :, :]
+            Und = pm.dagger(Un)
+            inner = inner + z[mu, nu] * pm.star(pm.star(Un, Umd), Und)
+            inner = inner + np.conj(z[mu, nu]) * pm.star(pm.star(Und, Umd), Un)
+        out[..., mu, :, :, :] = pm.star(Um, inner)
+    return out
+
+
+def drift(U, z) -> np.ndarray:
+    """F_mu^(k) = i [S^(k) - S^(k)^H - Tr(S^(k) - S^(k)^H)/N] (Eqs. 2-3, beta
+    absorbed).  Hermitian and traceless order by order."""
+    S = staple(U, z)
+    N = S.shape[-1]
+    D = S - np.conj(np.swapaxes(S, -1, -2))
+    tr = np.trace(D, axis1=-2, axis2=-1)
+    D = D - (tr / N)[..., None, None] * np.eye(N)
+    return 1j * D
+
+
+def exp_star(Y) -> np.ndarray:
+    """exp_star(Y) = sum_{n=0}^{T} Y^{star n} / n! for a series with Y^(0) = 0
+    (then Y^{star n} starts at order n and the sum is exact through order T)."""
+    Y = np.asarray(Y, np.complex128)
+    if np.any(Y[..., 0, :, :] != 0):
+        raise ValueError("exp_star needs Y^(0) = 0")
+    T = Y.shape[-3] - 1
+    N = Y.shape[-1]
+    E = pm.identity_series(N, T, Y.shape[:-3])
+    P = E.copy()
+    for n in range(1, T + 1):
+        P = pm.star(P, Y) / n
+        E = E + P
+    return E
+
+
+def langevin_step(U, eta, z, eps: float):
+    """One NSPT Langevin step of all four links (Eq. 3 in rescaled time).
+
+    U   : (..., 4, T+1, N, N) link series
+    eta : (..., 4, N, N) traceless Hermitian Gaussian noise (order g^1)
+    Returns (U_new, F) with F the drift of the input links.
+    """
+    U = np.asarray(U, np.complex128)
+    eta = np.asarray(eta, np.complex128)
+    F = drift(U, z)
+    X = eps * F
+    X[..., :, 0, :, :] = 0.0
+    if X.shape[-3] > 1:
+        X[..., :, 1, :, :] += math.sqrt(2.0 * eps) * eta
+    Unew = pm.star(exp_star(1j * X), U)
+    return Unew, F

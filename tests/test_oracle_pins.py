@@ -1,0 +1,493 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test compares the oracle with something other than itself: a library
+routine on a special case, exact integer arithmetic, closed forms, evaluation of
+the truncated series at a small coupling against plain matrix functions, or a
+finite-difference derivative of an independently written function.  A planted
+mistake (a dropped term, a wrong sign, a transposed operand) fails at least one.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import numpy.polynomial.polynomial as npoly
+import pytest
+import scipy.linalg as sla
+
+import nspt_synth as syn
+from oracle import polymat as pm
+from oracle import tek
+
+# ----------------------------------------------------------------------------
+# star product (Eq. 5)
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("T", [0, 1, 4, 9])
+def test_star_1x1_is_scalar_polynomial_product(T):
+    g = syn.rng(11 + T)
+    a = syn.gaussian(g, T + 1, 1.0)
+    b = syn.gaussian(g, T + 1, 1.0)
+    C = pm.star(a.reshape(T + 1, 1, 1), b.reshape(T + 1, 1, 1))[:, 0, 0]
+    ref = npoly.polymul(a, b)[: T + 1]
+    np.testing.assert_allclose(C, ref, rtol=0, atol=1e-14)
+
+
+def _exact_star(Ai, Bi):
+    """Brute force over Python integers (Gaussian integers as (re, im) pairs)."""
+    T1, N = Ai.shape[0], Ai.shape[1]
+    out = [[[(0, 0)] * N for _ in range(N)] for _ in range(T1)]
+    for k in range(T1):
+        for i in range(N):
+            for j in range(N):
+                re = im = 0
+                for l in range(k + 1):
+                    for m in range(N):
+                        ar, ai = int(Ai[l, i, m].real), int(Ai[l, i, m].imag)
+                        br, bi = int(Bi[k - l, m, j].real), int(Bi[k - l, m, j].imag)
+                        re += ar * br - ai * bi
+                        im += ar * bi + ai * br
+                out[k][i][j] = (re, im)
+    return out
+
+
+def test_star_integer_inputs_bit_exact():
+    g = syn.rng(5)
+    A = syn.integer_series(g, 3, 5, 1)[0]
+    B = syn.integer_series(g, 3, 5, 1)[0]
+    C = pm.star(A, B)
+    ex = _exact_star(A, B)
+    for k in range(6):
+        for i in range(3):
+            for j in range(3):
+                assert C[k, i, j].real == ex[k][i][j][0]
+                assert C[k, i, j].imag == ex[k][i][j][1]
+
+
+def test_star_exact_fractions_object_arrays():
+    A = np.empty((3, 2, 2), dtype=object)
+    B = np.empty((3, 2, 2), dtype=object)
+    vals = [Fraction(n, d) for n, d in [(1, 3), (2, 7), (-5, 11), (3, 2)]]
+    for k in range(3):
+        for i in range(2):
+            for j in range(2):
+                A[k, i, j] = vals[(k + i + 2 * j) % 4] * (k + 1)
+                B[k, i, j] = vals[(2 * k + j + i) % 4] - k
+    C = pm.star(A, B)
+    # C_2 = A_0 B_2 + A_1 B_1 + A_2 B_0, written out entry by entry
+    for i in range(2):
+        for j in range(2):
+            s = Fraction(0)
+            for l in range(3):
+                for m in range(2):
+                    s += A[l, i, m] * B[2 - l, m, j]
+            assert C[2, i, j] == s
+
+
+def test_identity_and_shift():
+    g = syn.rng(7)
+    N, T = 4, 6
+    A = syn.series_batch(g, N, T, 2)
+    I = pm.identity_series(N, T, (2,))
+    np.testing.assert_array_equal(pm.star(A, I), A)
+    np.testing.assert_array_equal(pm.star(I, A), A)
+    S = np.zeros_like(I)
+    S[:, 1] = np.eye(N)                     # the series g * 1
+    C = pm.star(A, S)
+    assert np.all(C[:, 0] == 0)
+    np.testing.assert_array_equal(C[:, 1:], A[:, :-1])
+
+
+def test_diagonal_inputs_are_independent_scalar_products():
+    g = syn.rng(8)
+    N, T = 3, 5
+    a = syn.gaussian(g, (T + 1, N), 1.0)
+    b = syn.gaussian(g, (T + 1, N), 1.0)
+    A = np.zeros((T + 1, N, N), np.complex128)
+    B = np.zeros_like(A)
+    for i in range(N):
+        A[:, i, i] = a[:, i]
+        B[:, i, i] = b[:, i]
+    C = pm.star(A, B)
+    for i in range(N):
+        np.testing.assert_allclose(C[:, i, i], npoly.polymul(a[:, i], b[:, i])[: T + 1], atol=1e-14)
+    off = C.copy()
+    for i in range(N):
+        off[:, i, i] = 0
+    assert np.all(off == 0)
+
+
+def test_star_keeps_matrix_order():
+    g = syn.rng(9)
+    A = syn.series_batch(g, 3, 2, 1)[0]
+    B = syn.series_batch(g, 3, 2, 1)[0]
+    C = pm.star(A, B)
+    np.testing.assert_allclose(C[1], A[0] @ B[1] + A[1] @ B[0], atol=1e-15)
+    assert np.abs(C[1] - (B[0] @ A[1] + B[1] @ A[0])).max() > 1e-3
+
+
+def test_truncated_series_evaluates_to_matrix_product():
+    # sum_k g^k C_k = A(g) B(g) + O(g^{T+1})
+    rg = syn.rng(10)
+    N, T = 4, 3
+    A = syn.series_batch(rg, N, T, 1)[0]
+    B = syn.series_batch(rg, N, T, 1)[0]
+    C = pm.star(A, B)
+    errs = []
+    for gc in (1e-2, 2e-2):
+        pw = gc ** np.arange(T + 1)
+        Ag = np.tensordot(pw, A, 1)
+        Bg = np.tensordot(pw, B, 1)
+        Cg = np.tensordot(pw, C, 1)
+        errs.append(np.abs(Ag @ Bg - Cg).max())
+    assert errs[0] < 1e-7
+    assert 2 ** (T + 1) * 0.6 < errs[1] / errs[0] < 2 ** (T + 1) * 1.6
+
+
+def test_associativity_bilinearity_and_dagger():
+    g = syn.rng(12)
+    N, T = 4, 5
+    A, B, C = (syn.series_batch(g, N, T, 1)[0] for _ in range(3))
+    np.testing.assert_allclose(pm.star(pm.star(A, B), C), pm.star(A, pm.star(B, C)), atol=1e-13)
+    a, b = 0.3 - 1.2j, 2.5 + 0.1j
+    np.testing.assert_allclose(pm.star(a * A + b * C, B), a * pm.star(A, B) + b * pm.star(C, B), atol=1e-13)
+    np.testing.assert_allclose(pm.dagger(pm.star(A, B)), pm.star(pm.dagger(B), pm.dagger(A)), atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# FFT-CONV by direct DFT (Sec. 2, Steps 1-5)
+# ----------------------------------------------------------------------------
+
+
+def test_forward_dft_matches_library_special_case():
+    # with w = exp(+2 pi i/M) and no normalisation, Step 2 equals M * numpy's ifft
+    g = syn.rng(13)
+    T, M = 5, 16
+    A = syn.series_batch(g, 3, T, 2)
+    At = pm.dft_forward(A, M)
+    pad = np.zeros((2, M, 3, 3), np.complex128)
+    pad[:, : T + 1] = A
+    np.testing.assert_allclose(At, M * np.fft.ifft(pad, axis=1), atol=1e-13)
+    back = pm.dft_inverse(At, M)
+    np.testing.assert_allclose(back, np.fft.fft(At, axis=1) / M, atol=1e-14)
+    np.testing.assert_allclose(back[:, : T + 1], A, atol=1e-14)
+
+
+def test_twiddles_against_long_double_definition():
+    for M in (2, 3, 32, 64, 128):
+        w = pm.twiddle_powers(M)
+        assert w[0] == 1
+        np.testing.assert_allclose(np.abs(w), 1, atol=2e-16)
+        np.testing.assert_allclose(w ** M, 1, atol=1e-13)
+        np.testing.assert_allclose(w, np.exp(2j * np.pi * np.arange(M) / M), atol=1e-15)
+
+
+@pytest.mark.parametrize("N,T", [(1, 0), (2, 1), (3, 2), (4, 7), (2, 8)])
+def test_dftconv_equals_naive_bruteforce(N, T):
+    g = syn.rng(100 + 10 * N + T)
+    A = syn.series_batch(g, N, T, 2)
+    B = syn.series_batch(g, N, T, 2)
+    ref = pm.star(A, B)
+    for M in {2 * T + 1, pm.default_fft_len(T), 2 * T + 3}:
+        C = pm.star_dftconv(A, B, M)
+        np.testing.assert_allclose(C, ref, atol=1e-13, rtol=0)
+
+
+def test_dftconv_aliases_below_the_bound():
+    # M = 2T wraps order 2T onto order 0: C_0 picks up A_T B_T
+    g = syn.rng(21)
+    N, T = 3, 4
+    A = syn.series_batch(g, N, T, 1)[0]
+    B = syn.series_batch(g, N, T, 1)[0]
+    ref = pm.star(A, B)
+    C = pm.star_dftconv(A, B, 2 * T)
+    np.testing.assert_allclose(C[0], ref[0] + A[T] @ B[T], atol=1e-13)
+    assert np.abs(C[0] - ref[0]).max() > 1e-2
+
+
+def test_dftconv_integer_inputs_round_to_exact():
+    g = syn.rng(22)
+    A = syn.integer_series(g, 4, 7, 1)[0]
+    B = syn.integer_series(g, 4, 7, 1)[0]
+    C = pm.star_dftconv(A, B)
+    ex = _exact_star(A, B)
+    assert np.abs(C - np.round(C.real) - 1j * np.round(C.imag)).max() < 1e-9
+    for k in range(8):
+        for i in range(4):
+            for j in range(4):
+                assert round(C[k, i, j].real) == ex[k][i][j][0]
+                assert round(C[k, i, j].imag) == ex[k][i][j][1]
+
+
+# ----------------------------------------------------------------------------
+# backward (truncated correlation)
+# ----------------------------------------------------------------------------
+
+
+def _loss(A, B, W):
+    return float(np.real(np.sum(np.conj(W) * pm.star(A, B))))
+
+
+def test_backward_central_finite_differences():
+    g = syn.rng(31)
+    N, T = 3, 4
+    A = syn.series_batch(g, N, T, 1)[0]
+    B = syn.series_batch(g, N, T, 1)[0]
+    W = syn.gaussian(g, A.shape, 1.0)
+    gA, gB = pm.star_backward(A, B, W)
+    h = 1e-6
+    for (X, gX, which) in ((A, gA, 0), (B, gB, 1)):
+        for idx in [(0, 0, 1), (2, 1, 2), (T, 2, 0), (1, 1, 1)]:
+            for d, part in ((1.0, "re"), (1j, "im")):
+                Xp = X.copy()
+                Xm = X.copy()
+                Xp[idx] += h * d
+                Xm[idx] -= h * d
+                if which == 0:
+                    fd = (_loss(Xp, B, W) - _loss(Xm, B, W)) / (2 * h)
+                else:
+                    fd = (_loss(A, Xp, W) - _loss(A, Xm, W)) / (2 * h)
+                an = gX[idx].real if part == "re" else gX[idx].imag
+                assert abs(fd - an) < 1e-8 * max(1.0, abs(an))
+
+
+def test_backward_adjoint_identity():
+    g = syn.rng(32)
+    N, T = 4, 6
+    A = syn.series_batch(g, N, T, 2)
+    B = syn.series_batch(g, N, T, 2)
+    W = syn.gaussian(g, A.shape, 1.0)
+    gA, gB = pm.star_backward(A, B, W)
+    lhs = np.real(np.vdot(W, pm.star(A, B)))
+    # the loss is linear in each operand separately
+    assert abs(lhs - np.real(np.vdot(gA, A))) < 1e-11 * abs(lhs) + 1e-12
+    assert abs(lhs - np.real(np.vdot(gB, B))) < 1e-11 * abs(lhs) + 1e-12
+
+
+def test_backward_1x1_is_scalar_correlation():
+    g = syn.rng(33)
+    T = 6
+    a, b, w = (syn.gaussian(g, T + 1, 1.0) for _ in range(3))
+    gA, gB = pm.star_backward(a.reshape(-1, 1, 1), b.reshape(-1, 1, 1), w.reshape(-1, 1, 1))
+    # gA_j = sum_k w_k conj(b_{k-j}): numpy.correlate(w, b, 'full') at lag j
+    full = np.correlate(w, b, "full")          # c[n] = sum_m w[m+n-(T)] conj(b[m])
+    np.testing.assert_allclose(gA[:, 0, 0], full[T:], atol=1e-14)
+    full2 = np.correlate(w, a, "full")
+    np.testing.assert_allclose(gB[:, 0, 0], full2[T:], atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# exp_star
+# ----------------------------------------------------------------------------
+
+
+def test_exp_star_single_order_closed_form():
+    g = syn.rng(41)
+    N, T = 3, 6
+    X = syn.gaussian(g, (N, N), 1.0 / N)
+    Y = np.zeros((T + 1, N, N), np.complex128)
+    Y[1] = X
+    E = tek.exp_star(Y)
+    for k in range(T + 1):
+        np.testing.assert_allclose(E[k], np.linalg.matrix_power(X, k) / math.factorial(k), atol=1e-14)
+
+
+def test_exp_star_inverse_and_expm_evaluation():
+    rg = syn.rng(42)
+    N, T = 3, 4
+    Y = syn.gaussian(rg, (T + 1, N, N), 1.0 / N)
+    Y[0] = 0
+    E = tek.exp_star(Y)
+    Einv = tek.exp_star(-Y)
+    I = pm.identity_series(N, T)
+    np.testing.assert_allclose(pm.star(E, Einv), I, atol=1e-14)
+    errs = []
+    for gc in (1e-2, 2e-2):
+        pw = gc ** np.arange(T + 1)
+        ref = sla.expm(np.tensordot(pw, Y, 1))
+        errs.append(np.abs(np.tensordot(pw, E, 1) - ref).max())
+    assert errs[0] < 1e-9
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+
+
+# ----------------------------------------------------------------------------
+# TEK: twist, action, drift, Langevin
+# ----------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("L,k", [(3, 1), (5, 2), (11, 3)])
+def test_twist_eaters_satisfy_twisted_vacuum(L, k):
+    G = syn.twist_eaters(L, k)
+    z = tek.twist_phases(L, k)
+    N = L * L
+    for mu in range(4):
+        np.testing.assert_allclose(G[mu] @ G[mu].conj().T, np.eye(N), atol=1e-12)
+        assert abs(np.linalg.det(G[mu]) - 1) < 1e-10
+        for nu in range(4):
+            if mu == nu:
+                continue
+            P = z[mu, nu] * G[mu] @ G[nu] @ G[mu].conj().T @ G[nu].conj().T
+            np.testing.assert_allclose(P, np.eye(N), atol=1e-12)
+            assert z[nu, mu] == np.conj(z[mu, nu])
+
+
+def test_vacuum_has_zero_action_and_force():
+    L, k, T = 3, 1, 3
+    N = L * L
+    U = np.zeros((4, T + 1, N, N), np.complex128)
+    U[:, 0] = syn.twist_eaters(L, k)
+    z = tek.twist_phases(L, k)
+    S = tek.action(U, z)
+    assert np.abs(S).max() < 1e-12
+    F = tek.drift(U, z)
+    assert np.abs(F).max() < 1e-12
+
+
+def test_action_is_real_and_drift_hermitian_traceless():
+    g = syn.rng(51)
+    U = syn.link_series(g, 3, 1, 3, 1)[0]
+    z = tek.twist_phases(3, 1)
+    S = tek.action(U, z)
+    assert np.abs(S.imag).max() < 1e-12 * max(1, np.abs(S).max())
+    F = tek.drift(U, z)
+    np.testing.assert_allclose(F, np.conj(np.swapaxes(F, -1, -2)), atol=1e-13)
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-13
+
+
+def _staple_minus_sign(U, z):
+    """The staple with the second term's sign as printed in Eqs. 2-3 (minus):
+    a planted alternative that the finite-difference test must reject."""
+    out = np.zeros_like(U)
+    for mu in range(4):
+        Um = U[mu]
+        Umd = pm.dagger(Um)
+        inner = np.zeros_like(Um)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            Un, Und = U[nu], pm.dagger(U[nu])
+            inner += z[mu, nu] * pm.star(pm.star(Un, Umd), Und)
+            inner -= np.conj(z[mu, nu]) * pm.star(pm.star(Und, Umd), Un)
+        out[mu] = pm.star(Um, inner)
+    return out
+
+
+def _fd_drift_check(U, z, F, mu, X, h=1e-5):
+    """Returns max_k |dS~^(k)/de - (-Tr[X F^(k)])| and the scale."""
+    Up, Um = U.copy(), U.copy()
+    Ep, Em = sla.expm(1j * h * X), sla.expm(-1j * h * X)
+    Up[mu] = Ep[None] @ U[mu]
+    Um[mu] = Em[None] @ U[mu]
+    dS = (tek.action(Up, z) - tek.action(Um, z)) / (2 * h)
+    pred = -np.einsum("ij,kji->k", X, F[mu])
+    return np.abs(dS - pred).max(), np.abs(pred).max()
+
+
+def test_drift_is_minus_gradient_of_truncated_action():
+    g = syn.rng(52)
+    L, k, T = 3, 1, 3
+    U = syn.link_series(g, L, k, T, 1)[0]
+    # a non-vacuum order 0 so that every order has a nonzero drift
+    U[:, 0] = syn.haar_sun(g, L * L, 4)
+    z = tek.twist_phases(L, k)
+    F = tek.drift(U, z)
+    X = syn.hermitian_traceless(g, L * L, 1)[0]
+    for mu in range(4):
+        err, scale = _fd_drift_check(U, z, F, mu, X)
+        assert err < 1e-7 * scale, (mu, err, scale)
+    # planted mistake: the minus-sign staple violates the identity
+    S_bad = _staple_minus_sign(U, z)
+    N = L * L
+    D = S_bad - np.conj(np.swapaxes(S_bad, -1, -2))
+    D = D - (np.trace(D, axis1=-2, axis2=-1) / N)[..., None, None] * np.eye(N)
+    F_bad = 1j * D
+    err, scale = _fd_drift_check(U, z, F_bad, 0, X)
+    assert err > 1e-3 * scale
+
+
+def _nonpert_staple(Ug, z):
+    S = []
+    for mu in range(4):
+        Um = Ug[mu]
+        acc = np.zeros_like(Um)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            Un = Ug[nu]
+            acc += z[mu, nu] * Un @ Um.conj().T @ Un.conj().T
+            acc += np.conj(z[mu, nu]) * Un.conj().T @ Um.conj().T @ Un
+        S.append(Um @ acc)
+    return np.stack(S)
+
+
+def test_langevin_step_matches_nonperturbative_update():
+    # sum_k g^k U'^(k) = expm(i X(g)) U(g) + O(g^{T+1}) with
+    # X(g) = eps (F(g) - F^(0)) + g sqrt(2 eps) eta and F(g) from plain products
+    rg = syn.rng(53)
+    L, k, T, eps = 3, 1, 3, 0.05
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    U[:, 0] = syn.haar_sun(rg, N, 4)           # generic order 0: F^(0) != 0
+    eta = syn.hermitian_noise(rg, N, 4)
+    z = tek.twist_phases(L, k)
+    Unew, F = tek.langevin_step(U, eta, z, eps)
+    errs = []
+    for gc in (5e-3, 1e-2):
+        pw = gc ** np.arange(T + 1)
+        Ug = np.einsum("k,mkij->mij", pw, U)
+        S = _nonpert_staple(Ug, z)
+        D = S - np.conj(np.swapaxes(S, -1, -2))
+        D = D - (np.trace(D, axis1=-2, axis2=-1) / N)[:, None, None] * np.eye(N)
+        Fg = 1j * D
+        ref = []
+        for mu in range(4):
+            Xg = eps * (Fg[mu] - F[mu, 0]) + gc * math.sqrt(2 * eps) * eta[mu]
+            ref.append(sla.expm(1j * Xg) @ Ug[mu])
+        ref = np.stack(ref)
+        got = np.einsum("k,mkij->mij", pw, Unew)
+        errs.append(np.abs(got - ref).max())
+    assert errs[0] < 1e-8
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+
+
+def _unitary_series(rg, L, k, T):
+    N = L * L
+    H = syn.gaussian(rg, (4, T + 1, N, N), 1.0 / N)
+    H = 0.5 * (H + np.conj(np.swapaxes(H, -1, -2)))
+    H[:, 0] = 0
+    E = tek.exp_star(1j * H)
+    G = np.zeros((4, T + 1, N, N), np.complex128)
+    G[:, 0] = syn.twist_eaters(L, k)
+    return pm.star(E, G)
+
+
+def test_langevin_step_preserves_unitary_series():
+    rg = syn.rng(54)
+    L, k, T = 3, 1, 4
+    N = L * L
+    U = _unitary_series(rg, L, k, T)
+    I = pm.identity_series(N, T, (4,))
+    np.testing.assert_allclose(pm.star(U, pm.dagger(U)), I, atol=1e-13)
+    eta = syn.hermitian_noise(rg, N, 4)
+    Unew, F = tek.langevin_step(U, eta, tek.twist_phases(L, k), 0.01)
+    np.testing.assert_allclose(pm.star(Unew, pm.dagger(Unew)), I, atol=1e-13)
+    np.testing.assert_array_equal(Unew[:, 0], U[:, 0])
+    assert np.abs(Unew - U).max() > 1e-3
+
+
+def test_langevin_small_eps_first_order():
+    rg = syn.rng(55)
+    L, k, T = 3, 1, 3
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    z = tek.twist_phases(L, k)
+    eta = np.zeros((4, 9, 9), np.complex128)
+    d = []
+    for eps in (1e-4, 2e-4):
+        Unew, F = tek.langevin_step(U, eta, z, eps)
+        X = F.copy()
+        X[:, 0] = 0
+        lin = 1j * pm.star(X, U)
+        d.append(np.abs((Unew - U) / eps - lin).max())
+        scale = np.abs(lin).max()
+    assert d[0] < 1e-3 * scale
+    assert 1.6 < d[1] / d[0] < 2.4
