@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the NSPT polynomial-matrix product on one B300 (or N replicas).
+
+Metric: poly-matrix products/s (and effective TFLOP/s) at SU(225), O(g^63):
+the truncated product C_k = sum_{l<=k} A_l B_{k-l}, k = 0..63, of two series of
+225 x 225 complex matrices (Eq. 5), by FFT-CONV (Sec. 2, Steps 1-5) with M = 128,
+batch 4 (one product per link direction).  One step = one call of
+nspt_polymat_mul on a batch of 4 products with inputs resident in HBM; the
+inputs (2 x 207 MB) and the spectra exceed the 126 MB L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica on its own batch
+(weak scaling; the products are independent, no data-path collective); rank 0
+prints the JSON line with the max-over-ranks time.  `--impl reference` times the
+FP64 CPU oracle (a deliberately slow, plain program) on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nspt_synth as syn  # noqa: E402
+
+METRIC = "poly-matrix products/s at SU(225) O(g^63), FFT-CONV, batch 4"
+N_DEF, T_DEF, BATCH = 225, 63, 4
+
+
+def fft_flops(N, M):
+    """Algorithmic FLOPs of one FFT-CONV product: M complex N^3 GEMMs plus three
+    M-point radix-2 transforms over N^2 entries (5 M log2 M real flops each)."""
+    return 8.0 * N ** 3 * M + 3 * 5.0 * N * N * M * math.log2(M)
+
+
+def naive_flops(N, T):
+    return 8.0 * N ** 3 * (T + 1) * (T + 2) / 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["split", "fp64"], default=None)
+    ap.add_argument("--T", type=int, default=T_DEF)
+    ap.add_argument("--N", type=int, default=N_DEF)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64/T=31 comparison legs")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def inputs(N, T, batch, seed):
+    g = syn.rng(seed)
+    return syn.series_batch(g, N, T, batch), syn.series_batch(g, N, T, batch)
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        n = [d.get("num_threads", 0) for d in info if d.get("user_api") == "blas"]
+        return int(max(n)) if n else 1
+    except Exception:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def time_oracle_products(N, T, nprod, seed):
+    """Wall time of the oracle's FFT-CONV (direct DFT, Sec. 2 Steps 1-5) on
+    `nprod` products of the workload's shape."""
+    from oracle import polymat as pm
+    A, B = inputs(N, T, nprod, seed)
+    t0 = time.perf_counter()
+    pm.star_dftconv(A, B)
+    return time.perf_counter() - t0
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    N, T = args.N, args.T
+    nprod = BATCH
+    for _ in range(args.warmup):
+        time_oracle_products(N, T, nprod, syn.SEED_BASE + 2)
+    times = [time_oracle_products(N, T, nprod, syn.SEED_BASE + 2) for _ in range(args.steps)]
+    tot = sum(times)
+    value = args.steps * nprod / tot
+    cores = oracle_threads()
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": "SU(%d) O(g^%d) FFT-CONV (oracle direct DFT)" % (N, T), "N": N, "T": T,
+                   "batch": BATCH, "sample": "the whole batch of 4 products per step"},
+        "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
+                         "sample": "batch of 4 products (N=%d, T=%d) per step, numpy FP64 oracle, %s"
+                                   % (N, T, cpu_model())},
+        "e2e": {"value": value, "unit": "products/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="nspt_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                rows.append((float(p[1]), float(p[2]), float(p[3]), p[5], p[6], p[7], p[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [r for r in rows if r[2] > 200.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in load for i, v in enumerate(r[3:7]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(load), "power_w_max": max(r[2] for r in rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+def fp64_peak_tflops(torch):
+    """Measured FP64 denominator (the peaks file has none): cuBLAS DGEMM 4096^3, best of 5."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn_like(a)
+    c = a @ b
+    torch.cuda.synchronize()
+    best = 1e9
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        s.record()
+        torch.matmul(a, b, out=c)
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e))
+    del a, b, c
+    return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+def time_steps(torch, fn, steps, warmup, barrier):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(st)
+    for _ in range(steps):
+        fn()
+    e.record(st)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e)
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist  # noqa: F811
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import paper_2001_02835_b300 as nspt
+    if nspt.lib().nspt_init() != 0:
+        raise SystemExit("libnspt: nspt_init failed (not an sm_103 device?)")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N, T = args.N, args.T
+    M = 1 << math.ceil(math.log2(2 * (T + 1)))
+    prec = args.prec or "split"
+    A, B = inputs(N, T, BATCH, syn.SEED_BASE + 2 + 1000 * rank)
+    dA = torch.from_numpy(A).cuda()
+    dB = torch.from_numpy(B).cuda()
+    dC = torch.empty_like(dA)
+    kw = dict(algo="fft", prec=prec)
+    try:
+        nspt.polymat_mul(dA, dB, dC, **kw)
+    except nspt.NsptError as ex:
+        if prec == "split" and args.prec is None:
+            prec = "fp64"
+            kw["prec"] = prec
+        else:
+            raise ex
+    fn = lambda: nspt.polymat_mul(dA, dB, dC, **kw)  # noqa: E731
+
+    # timed region (stage events on, clocks sampled)
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    l0 = nspt.launch_count()
+    nspt.profile_begin(100000)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = time_steps(torch, fn, args.steps, 0, barrier)
+    stages = nspt.profile_end()
+    launches = nspt.launch_count() - l0
+    clocks = clk.summary()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * BATCH * args.steps / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty_like(hA).pin_memory()
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        dB.copy_(hB, non_blocking=True)
+        nspt.polymat_mul(dA, dB, dC, **kw)
+        hC.copy_(dC, non_blocking=True)
+
+    e2e_steps = max(3, args.steps // 2)
+    ms_e2e = time_steps(torch, e2e_step, e2e_steps, 1, barrier)
+    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = ws * BATCH * e2e_steps / (float(t.item()) * 1e-3)
+    nbytes = A.nbytes
+
+    peaks, peak_kind = measured_peaks()
+    # dominant kernel of the step
+    dom = max(stages.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    if dom_name == "gemm_tc":
+        slices = 6
+        pairs = slices * (slices + 1) // 2
+        flops = pairs * 4 * 2.0 * N ** 3 * M * BATCH / max(1, dom_n // args.steps)
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"kernel": dom_name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "%s bf16_tflops_sustained" % peak_kind}
+    elif dom_name in ("gemm_mode", "gemm_conv"):
+        f64 = fp64_peak_tflops(torch)
+        flops = 8.0 * N ** 3 * M * BATCH / max(1, dom_n // args.steps)
+        achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": f64, "unit": "TFLOP/s",
+                "frac": achieved / f64, "traffic": None,
+                "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (FP64 pipe)"}
+    else:
+        byts = (T + 1 + M) * N * N * 16.0 * BATCH
+        achieved = byts / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "peak_source": "%s hbm_gbs" % peak_kind}
+
+    extras = {}
+    if not args.no_extras and ws == 1:
+        # FP64 form at the same workload, and the paper's timing point T = 31
+        if prec != "fp64":
+            kw64 = dict(algo="fft", prec="fp64")
+            ms64 = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kw64), 3, 1, barrier)
+            extras["fp64_fft_T%d" % T] = {"products_per_s": BATCH * 3 / (ms64 * 1e-3), "ms_per_step": ms64 / 3}
+        A31, B31 = inputs(N, 31, BATCH, syn.SEED_BASE + 1)
+        a31, b31 = torch.from_numpy(A31).cuda(), torch.from_numpy(B31).cuda()
+        c31 = torch.empty_like(a31)
+        for p in ([prec] if prec == "fp64" else [prec, "fp64"]):
+            ms31 = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="fft", prec=p), 3, 1, barrier)
+            extras["%s_fft_T31" % p] = {"products_per_s": BATCH * 3 / (ms31 * 1e-3), "ms_per_step": ms31 / 3,
+                                        "eff_tflops": fft_flops(N, 64) * BATCH * 3 / (ms31 * 1e-3) / 1e12}
+        msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
+        extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
+                                    "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
+        del a31, b31, c31
+
+    cpu = None
+    if rank == 0:
+        # bounded sample: whole batches of the workload through the oracle on the
+        # host cores, repeated until about 10 s of CPU time (at most 30 s)
+        done, tcpu = 0, 0.0
+        while tcpu < 10.0 and done < 64:
+            tcpu += time_oracle_products(N, T, BATCH, syn.SEED_BASE + 2)
+            done += BATCH
+            if tcpu > 30.0:
+                break
+        cpu = {"value": done / tcpu, "unit": "products/s", "cores": oracle_threads(), "kind": "oracle",
+               "sample": "%d products (N=%d, T=%d, M=%d) by the numpy FP64 oracle's direct-DFT FFT-CONV on %s"
+                         % (done, N, T, M, cpu_model())}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "c128 in/out; " + ("bf16 slices x6, fp32 exact partials" if prec == "split" else "f64"),
+            "data": "synthetic (Haar SU(N) order 0, Gaussian var 1/N orders >= 1, seed 200102837)",
+            "config": {"workload": "SU(%d) O(g^%d) FFT-CONV M=%d batch %d, %s form" % (N, T, M, BATCH, prec),
+                       "N": N, "T": T, "M": M, "batch_per_gpu": BATCH, "prec": prec,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs 2 x %.0f MB > 126 MB L2, no flush" % (nbytes / 1e6)},
+            "eff_tflops": fft_flops(N, M) * value / 1e12,
+            "roofline": roof,
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "products/s", "h2d_bytes_per_step": 2 * nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "extras": extras,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

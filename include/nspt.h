@@ -1,0 +1,166 @@
+/*
+ * nspt.h -- C ABI of the B300 (sm_103a) library for the NSPT hot path of the
+ * twisted Eguchi-Kawai model: the truncated product of polynomial matrices
+ * (Eqs. 4-5, Sec. 2), computed naively or by FFT-CONV (Sec. 2, Steps 1-5), its
+ * backward, and one NSPT Langevin step of the four links (Eqs. 1-3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - A "series" is T+1 coefficient matrices, each N x N complex128 stored
+ *   row-major with interleaved (re, im) doubles.  A batch of series is
+ *   [batch][T+1][N][N]; entry (i, j) of order k of batch element b sits at
+ *   element ((b*(T+1) + k)*N + i)*N + j.
+ * - Every data pointer is a DEVICE pointer (cudaMalloc / torch CUDA memory),
+ *   8-byte aligned at least; the caller owns every buffer.  The library never
+ *   allocates, synchronises or reads device memory back inside a call: all
+ *   work is enqueued on `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *   default stream), so calls can be captured into CUDA graphs once the
+ *   library has been initialised on the device (see nspt_init).
+ * - Scratch memory comes from the caller: opts->workspace of at least
+ *   nspt_workspace_size(...) bytes, 256-byte aligned.  Too small -> NSPT_ERR_WORKSPACE.
+ * - Outputs must not overlap inputs (NSPT_ERR_ALIAS), except where stated.
+ * - A call returns NSPT_OK or a negative nspt_status; no exception crosses the
+ *   ABI.  NSPT_ERR_CUDA: a launch failed; nspt_last_error() names it.
+ */
+#ifndef NSPT_H
+#define NSPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NSPT_API __attribute__((visibility("default")))
+#else
+#define NSPT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nspt_status {
+  NSPT_OK = 0,
+  NSPT_ERR_ARG = -1,          /* bad size, NULL pointer, bad option */
+  NSPT_ERR_ALIAS = -2,        /* an output overlaps an input */
+  NSPT_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
+  NSPT_ERR_WORKSPACE = -4,    /* opts->workspace missing or too small */
+  NSPT_ERR_CUDA = -5,         /* CUDA runtime error (see nspt_last_error) */
+  NSPT_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */
+  NSPT_ERR_DEVICE = -7        /* the device is not an sm_103 part */
+} nspt_status;
+
+/* algorithm of the star product */
+enum { NSPT_ALGO_NAIVE = 0, /* Eq. 5: C_k = sum_l A_l B_{k-l}, (T+1)(T+2)/2 GEMMs */
+       NSPT_ALGO_FFT = 1,   /* Sec. 2 Steps 1-5: M-point order FFT, M mode GEMMs, inverse FFT */
+       NSPT_ALGO_AUTO = 2 };/* FFT when T >= 3, else naive */
+
+/* arithmetic of the mode GEMMs */
+enum { NSPT_PREC_FP64 = 0,  /* plain FP64 everywhere (the paper's ZGEMM form) */
+       NSPT_PREC_SPLIT = 1  /* FP64 spectra split into BF16 slices, tensor-core GEMMs with exact
+                               FP32 partial sums, double-word recombination */ };
+
+/* which call a workspace is sized for */
+enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2 };
+
+#define NSPT_RESCALE_AUTO (-1000)
+
+typedef struct nspt_opts {
+  int algo;            /* NSPT_ALGO_*; default NSPT_ALGO_AUTO */
+  int prec;            /* NSPT_PREC_*; default NSPT_PREC_FP64 */
+  int fft_len;         /* M; 0 = smallest power of two >= 2(T+1); else a power of two
+                          >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
+  int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
+  int complex_mode;    /* split form: 4 (four real products per complex product); 0 = 4 */
+  int rescale_log2r;   /* split form: per-order rescale A_k, B_k -> r^k A_k, r^k B_k with
+                          r = 2^rescale_log2r, undone exactly on C; NSPT_RESCALE_AUTO = fit
+                          r from the operands' order magnitudes on the host (never
+                          used inside graph capture); default 0 */
+  void* workspace;     /* device scratch, >= nspt_workspace_size() bytes */
+  size_t workspace_bytes;
+} nspt_opts;
+
+/* Fills *o with the defaults listed above (no workspace). */
+NSPT_API void nspt_opts_default(nspt_opts* o);
+
+/* One-time per-device set-up (function attributes, device check).  Every entry
+ * point calls it implicitly; call it once before capturing a CUDA graph.
+ * Returns NSPT_ERR_DEVICE when the current device is not sm_103. */
+NSPT_API int nspt_init(void);
+
+/* Bytes of device workspace the call `op` (NSPT_OP_*) needs for these sizes. */
+NSPT_API size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opts);
+
+/*
+ * C = A star B, truncated at order T (Eq. 5), for `batch` independent pairs.
+ *   A, B : [batch][T+1][N][N] complex128 (inputs)
+ *   C    : [batch][T+1][N][N] complex128 (output; must not overlap A or B)
+ * NAIVE: Eq. 5 directly.  FFT: Sec. 2 Steps 1-5 -- zero-pad the order axis to
+ * M, forward transform with w = exp(+2 pi i/M) (Step 2), M mode-wise complex
+ * GEMMs (Step 3), inverse transform with 1/M (Step 4), keep orders 0..T
+ * (Step 5).  N >= 1, T >= 0, batch >= 1.
+ */
+NSPT_API int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int batch,
+                     const nspt_opts* opts, void* stream);
+
+/*
+ * Backward of C = A star B for a real loss L with gC = dL/dRe C + i dL/dIm C
+ * (the truncated correlations obtained by differentiating Eq. 5):
+ *   gA_j = sum_{k=j}^{T} gC_k (B_{k-j})^H,   gB_j = sum_{k=j}^{T} (A_{k-j})^H gC_k.
+ * FFT form: gA~_p = G~_p (B~_p)^H and gB~_p = (A~_p)^H G~_p, inverse
+ * transform, keep 0..T (wrap-free for M >= 2T+1).
+ *   A, B, gC : [batch][T+1][N][N] inputs;  gA, gB : outputs, either may be NULL.
+ */
+NSPT_API int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB,
+                              int N, int T, int batch, const nspt_opts* opts, void* stream);
+
+/*
+ * One NSPT Langevin step of the TEK model for `batch` independent streams of
+ * four link series (Eqs. 1-3 in the rescaled fictitious time):
+ *   z_{mu nu} = exp(2 pi i flux eps_{mu nu}/L), eps = +1 (mu<nu), -1 (mu>nu), N = L^2;
+ *   S_mu = U_mu star sum_{nu != mu} [z_{mu nu} U_nu U_mu^+ U_nu^+ + conj(z_{mu nu}) U_nu^+ U_mu^+ U_nu];
+ *   F^(k) = i[S^(k) - S^(k)^H - Tr(S^(k) - S^(k)^H)/N];
+ *   X^(0) = 0, X^(1) = eps F^(1) + sqrt(2 eps) eta, X^(k>=2) = eps F^(k);
+ *   U <- exp_star(i X) star U   (order 0 of U unchanged).
+ *   U   : [batch][4][T+1][N][N], updated IN PLACE
+ *   eta : [batch][4][N][N] traceless Hermitian Gaussian noise (input, required)
+ *   F   : [batch][4][T+1][N][N] drift of the input links (output, may be NULL)
+ * N must be a perfect square L^2 with gcd(flux, L) = 1; eps > 0.
+ */
+NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int batch, int flux,
+                           double eps, const nspt_opts* opts, void* stream);
+
+/*
+ * Single stages of FFT-CONV, for stage timing and per-stage tests.
+ * nspt_order_fft: Steps 1-2 -- At[b][p] = sum_{k<=T} A[b][k] w^(kp), p = 0..M-1,
+ *   A : [batch][T+1][N][N] -> At : [batch][M][N][N], w = exp(+2 pi i/M).
+ * nspt_order_ifft: Steps 4-5 -- C[b][k] = (1/M) sum_p Ct[b][p] w^(-kp), k = 0..T,
+ *   Ct : [batch][M][N][N] -> C : [batch][T+1][N][N].
+ * M: power of two, 2(T+1) <= M <= 512.  FP64 arithmetic.
+ */
+NSPT_API int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream);
+NSPT_API int nspt_order_ifft(const void* Ct, void* C, int N, int T, int batch, int M, void* stream);
+
+/*
+ * Instrumentation (host side; no effect on results).
+ * nspt_launch_count: kernel launches enqueued by this library since load.
+ * nspt_profile_begin: from now on, bracket every library kernel launch with a
+ *   CUDA event pair recorded on its own stream (up to max_records launches).
+ * nspt_profile_end: wait for those events and sum their durations per stage
+ *   (total_ms[s], launches[s] for s < nstages); returns the records used.
+ * nspt_stage_name: name of stage s (fft_fwd, slice, gemm_mode, fft_inv,
+ *   gemm_conv, tek_elementwise, gemm_tc, other).
+ */
+NSPT_API long long nspt_launch_count(void);
+NSPT_API int nspt_profile_begin(int max_records);
+NSPT_API int nspt_profile_end(int nstages, double* total_ms, long long* launches);
+NSPT_API const char* nspt_stage_name(int stage);
+
+/* Static description of a status code. */
+NSPT_API const char* nspt_status_string(int status);
+/* Name of the last CUDA error seen by this thread ("no error" if none). */
+NSPT_API const char* nspt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSPT_H */

@@ -1,0 +1,539 @@
+// C ABI, planner and orchestration of the NSPT polynomial-matrix library.
+//
+// Every entry point validates its arguments on the host, carves the caller's
+// workspace, and enqueues kernels on the caller's stream; nothing is allocated,
+// synchronised or read back.  The FFT-CONV orchestration follows Sec. 2
+// Steps 1-5; the Langevin step follows Eqs. 1-3 (see include/nspt.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+#include "zgemm64.cuh"
+#include "tek.cuh"
+#include "split.cuh"
+#include "prof.cuh"
+
+namespace {
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+int next_pow2(int x) {
+  int m = 1;
+  while (m < x) m <<= 1;
+  return m;
+}
+
+struct Plan {
+  int N, T, batch;
+  long long E;
+  int algo, prec, M, slices, log2r;
+  bool rescale_auto;
+};
+
+int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p) {
+  nspt_opts d;
+  nspt_opts_default(&d);
+  if (!o) o = &d;
+  if (N < 1 || T < 0 || batch < 1 || N > 4096 || T > 255) return NSPT_ERR_ARG;
+  p->N = N; p->T = T; p->batch = batch; p->E = (long long)N * N;
+  p->algo = o->algo;
+  if (p->algo == NSPT_ALGO_AUTO) p->algo = (T >= 3) ? NSPT_ALGO_FFT : NSPT_ALGO_NAIVE;
+  if (p->algo != NSPT_ALGO_NAIVE && p->algo != NSPT_ALGO_FFT) return NSPT_ERR_ARG;
+  p->prec = o->prec;
+  if (p->prec != NSPT_PREC_FP64 && p->prec != NSPT_PREC_SPLIT) return NSPT_ERR_ARG;
+  p->M = o->fft_len ? o->fft_len : next_pow2(2 * (T + 1));
+  if (ilog2_exact(p->M) < 0 || p->M < 2 * (T + 1) || p->M > 512) return NSPT_ERR_ARG;
+  p->slices = o->slices ? o->slices : 6;
+  if (p->slices < 2 || p->slices > 8) return NSPT_ERR_ARG;
+  if (o->complex_mode != 0 && o->complex_mode != 4) return NSPT_ERR_UNSUPPORTED;
+  p->rescale_auto = (o->rescale_log2r == NSPT_RESCALE_AUTO);
+  p->log2r = p->rescale_auto ? 0 : o->rescale_log2r;
+  if (!p->rescale_auto && (p->log2r < -60 || p->log2r > 60)) return NSPT_ERR_ARG;
+  if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE) return NSPT_ERR_UNSUPPORTED;
+  return NSPT_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  if (!a || !b) return false;
+  const char* x = (const char*)a;
+  const char* y = (const char*)b;
+  return x < y + nb && y < x + na;
+}
+
+// --------------------------------------------------------------------------
+// FP64 building blocks
+// --------------------------------------------------------------------------
+ZgemmParams zg(int kind, const double2* A, long long sA, const double2* B, long long sB, double2* C,
+               long long sC, int N, int nmat, int T) {
+  ZgemmParams P;
+  memset(&P, 0, sizeof(P));
+  P.A = A; P.B = B; P.C = C; P.sA = sA; P.sB = sB; P.sC = sC;
+  P.N = N; P.kind = kind; P.nmat = nmat; P.T = T;
+  P.alpha = make_double2(1.0, 0.0);
+  return P;
+}
+
+__global__ void add_identity_kernel(double2* X, long long stride_mats, int N, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count * N) return;
+  const long long s = i / N;
+  const int d = (int)(i % N);
+  X[s * stride_mats * N * N + (long long)d * N + d].x += 1.0;
+}
+
+cudaError_t add_identity(double2* X, long long stride_mats, int N, long long count, cudaStream_t st) {
+  const long long n = count * N;
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  add_identity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, stride_mats, N, count);
+  return cudaGetLastError();
+}
+
+#define TRY(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) { g_last_cuda = _e; return NSPT_ERR_CUDA; } } while (0)
+
+// --- forward product, FP64 ---
+size_t ws_mul(const Plan& p) {
+  if (p.algo == NSPT_ALGO_NAIVE) return 0;
+  const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
+  if (p.prec == NSPT_PREC_FP64) return 3 * ((spec + 255) & ~(size_t)255);
+  return nspt_split_ws_mul(p.N, p.T, p.batch, p.M, p.slices);
+}
+
+int mul_fp64(const Plan& p, const double2* A, const double2* B, double2* C, void* ws, cudaStream_t st) {
+  const int N = p.N, T = p.T, b = p.batch, M = p.M;
+  if (p.algo == NSPT_ALGO_NAIVE) {
+    ZgemmParams P = zg(ZG_CONV, A, T + 1, B, T + 1, C, T + 1, N, T + 1, T);
+    TRY(nspt_zgemm64(P, b, st));
+    return NSPT_OK;
+  }
+  WsCarver w(ws, SIZE_MAX);
+  double2* At = w.take<double2>((size_t)b * M * p.E);
+  double2* Bt = w.take<double2>((size_t)b * M * p.E);
+  double2* Ct = w.take<double2>((size_t)b * M * p.E);
+  TRY(nspt_fft_fwd64(A, T + 1, At, (int)p.E, T, b, M, 0, 0, st));
+  TRY(nspt_fft_fwd64(B, T + 1, Bt, (int)p.E, T, b, M, 0, 0, st));
+  ZgemmParams P = zg(ZG_MODE, At, M, Bt, M, Ct, M, N, M, T);
+  TRY(nspt_zgemm64(P, b, st));
+  TRY(nspt_fft_inv64(Ct, C, T + 1, (int)p.E, N, T, b, M, 0, 0, 1.0, 0, st));
+  return NSPT_OK;
+}
+
+// --- backward, FP64 ---
+size_t ws_bwd(const Plan& p) {
+  if (p.algo == NSPT_ALGO_NAIVE) return 0;
+  const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
+  if (p.prec == NSPT_PREC_FP64) return 4 * ((spec + 255) & ~(size_t)255);
+  return nspt_split_ws_bwd(p.N, p.T, p.batch, p.M, p.slices);
+}
+
+int bwd_fp64(const Plan& p, const double2* A, const double2* B, const double2* G, double2* gA, double2* gB,
+             void* ws, cudaStream_t st) {
+  const int N = p.N, T = p.T, b = p.batch, M = p.M;
+  if (p.algo == NSPT_ALGO_NAIVE) {
+    if (gA) {
+      ZgemmParams P = zg(ZG_CORR_A, G, T + 1, B, T + 1, gA, T + 1, N, T + 1, T);
+      P.opB = 1;
+      TRY(nspt_zgemm64(P, b, st));
+    }
+    if (gB) {
+      ZgemmParams P = zg(ZG_CORR_B, A, T + 1, G, T + 1, gB, T + 1, N, T + 1, T);
+      P.opA = 1;
+      TRY(nspt_zgemm64(P, b, st));
+    }
+    return NSPT_OK;
+  }
+  WsCarver w(ws, SIZE_MAX);
+  double2* At = w.take<double2>((size_t)b * M * p.E);
+  double2* Bt = w.take<double2>((size_t)b * M * p.E);
+  double2* Gt = w.take<double2>((size_t)b * M * p.E);
+  double2* Xt = w.take<double2>((size_t)b * M * p.E);
+  TRY(nspt_fft_fwd64(G, T + 1, Gt, (int)p.E, T, b, M, 0, 0, st));
+  if (gA) {
+    TRY(nspt_fft_fwd64(B, T + 1, Bt, (int)p.E, T, b, M, 0, 0, st));
+    ZgemmParams P = zg(ZG_MODE, Gt, M, Bt, M, Xt, M, N, M, T);
+    P.opB = 1;
+    TRY(nspt_zgemm64(P, b, st));
+    TRY(nspt_fft_inv64(Xt, gA, T + 1, (int)p.E, N, T, b, M, 0, 0, 1.0, 0, st));
+  }
+  if (gB) {
+    TRY(nspt_fft_fwd64(A, T + 1, At, (int)p.E, T, b, M, 0, 0, st));
+    ZgemmParams P = zg(ZG_MODE, At, M, Gt, M, Xt, M, N, M, T);
+    P.opA = 1;
+    TRY(nspt_zgemm64(P, b, st));
+    TRY(nspt_fft_inv64(Xt, gB, T + 1, (int)p.E, N, T, b, M, 0, 0, 1.0, 0, st));
+  }
+  return NSPT_OK;
+}
+
+// --------------------------------------------------------------------------
+// Langevin step (Eqs. 1-3).  The engine hides the naive / FFT choice behind
+// "operands" (a series for the naive form, a spectrum for the FFT form) and
+// "accumulators" (a series / a spectrum summed over terms).
+// --------------------------------------------------------------------------
+const int kPairs[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+int pair_index(int a, int b) {  // a < b
+  for (int i = 0; i < 6; ++i)
+    if (kPairs[i][0] == a && kPairs[i][1] == b) return i;
+  return -1;
+}
+int ordered_index(int mu, int nu) { return mu * 3 + (nu < mu ? nu : nu - 1); }  // 0..11
+
+size_t ws_langevin(const Plan& p) {
+  const long long E = p.E;
+  const long long T1 = p.T + 1, M = p.M;
+  size_t mats;
+  if (p.algo == NSPT_ALGO_FFT) {
+    // spectra: U(4) PQ(18) Acc(18) In(4); series: tmp(18) S(4) Y(4) R(8); exp spectra Y,R,C (12)
+    mats = (size_t)(4 + 18 + 18 + 4 + 12) * M + (size_t)(18 + 4 + 4 + 8) * T1;
+  } else {
+    // series: P1(6) Q(12) inner(4) S(4) Y(4) R(8) U0(4)
+    mats = (size_t)(6 + 12 + 4 + 4 + 4 + 8 + 4) * T1;
+  }
+  return (size_t)p.batch * mats * E * sizeof(double2) + (size_t)p.batch * 4 * T1 * sizeof(double) + 8 * 256;
+}
+
+int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int flux, double eps, void* ws,
+                  cudaStream_t st) {
+  const int N = p.N, T = p.T, nb = p.batch;
+  const long long E = p.E, T1 = T + 1;
+  int L = (int)llround(sqrt((double)N));
+  // twist phases z[mu][nu] = exp(2 pi i flux eps_{mu nu} / L), computed on the host
+  double2 z[4][4];
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = 0; nu < 4; ++nu) {
+      const double sgn = (mu < nu) ? 1.0 : -1.0;
+      const double ang = 2.0 * M_PI * flux * sgn / L;
+      z[mu][nu] = (mu == nu) ? make_double2(0, 0) : make_double2(cos(ang), sin(ang));
+    }
+  WsCarver w(ws, SIZE_MAX);
+  if (p.algo == NSPT_ALGO_FFT) {
+    const int M = p.M;
+    double2* specU = w.take<double2>((size_t)nb * 4 * M * E);
+    double2* specPQ = w.take<double2>((size_t)nb * 18 * M * E);
+    double2* specAcc = w.take<double2>((size_t)nb * 18 * M * E);
+    double2* specIn = w.take<double2>((size_t)nb * 4 * M * E);
+    double2* serTmp = w.take<double2>((size_t)nb * 18 * T1 * E);
+    double2* serS = w.take<double2>((size_t)nb * 4 * T1 * E);
+    double2* serY = w.take<double2>((size_t)nb * 4 * T1 * E);
+    double2* serR[2] = {w.take<double2>((size_t)nb * 4 * T1 * E), w.take<double2>((size_t)nb * 4 * T1 * E)};
+    double2* spY = w.take<double2>((size_t)nb * 4 * M * E);
+    double2* spR = w.take<double2>((size_t)nb * 4 * M * E);
+    double2* spC = w.take<double2>((size_t)nb * 4 * M * E);
+    double* imtr = w.take<double>((size_t)nb * 4 * T1);
+    const long long sm = (long long)M;  // matrices per spectrum
+    // 1. spectra of the four links
+    TRY(nspt_fft_fwd64(U, T1, specU, (int)E, T, nb * 4, M, 0, 0, st));
+    auto specOf = [&](double2* base, int slot) { return base + (long long)slot * M * E; };
+    // 2. P1(mu,nu) = U_nu * U_mu^+ (mu<nu), Q(mu,nu) = U_mu * U_nu (mu != nu)
+    for (int i = 0; i < 6; ++i) {
+      const int mu = kPairs[i][0], nu = kPairs[i][1];
+      ZgemmParams P = zg(ZG_MODE, specOf(specU, nu), 4 * sm, specOf(specU, mu), 4 * sm, specOf(specAcc, i),
+                         18 * sm, N, M, T);
+      P.opB = 1; P.revB = 1;
+      TRY(nspt_zgemm64(P, nb, st));
+    }
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = 0; nu < 4; ++nu) {
+        if (mu == nu) continue;
+        ZgemmParams P = zg(ZG_MODE, specOf(specU, mu), 4 * sm, specOf(specU, nu), 4 * sm,
+                           specOf(specAcc, 6 + ordered_index(mu, nu)), 18 * sm, N, M, T);
+        TRY(nspt_zgemm64(P, nb, st));
+      }
+    // truncate (Step 5) and return to the frequency domain
+    TRY(nspt_fft_inv64(specAcc, serTmp, T1, (int)E, N, T, nb * 18, M, 0, 0, 1.0, 0, st));
+    TRY(nspt_fft_fwd64(serTmp, T1, specPQ, (int)E, T, nb * 18, M, 0, 0, st));
+    // 3. inner_mu = sum_nu z P1(mu,nu) U_nu^+ + conj(z) P2(mu,nu) U_nu,  P2(mu,nu) = Q(mu,nu)^+
+    for (int mu = 0; mu < 4; ++mu) {
+      bool first = true;
+      for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        {
+          const int pi = (mu < nu) ? pair_index(mu, nu) : pair_index(nu, mu);
+          ZgemmParams P = zg(ZG_MODE, specOf(specPQ, pi), 18 * sm, specOf(specU, nu), 4 * sm, specOf(specIn, mu),
+                             4 * sm, N, M, T);
+          if (mu > nu) { P.opA = 1; P.revA = 1; }
+          P.opB = 1; P.revB = 1;
+          P.alpha = z[mu][nu];
+          P.accumulate = first ? 0 : 1;
+          first = false;
+          TRY(nspt_zgemm64(P, nb, st));
+        }
+        {
+          ZgemmParams P = zg(ZG_MODE, specOf(specPQ, 6 + ordered_index(mu, nu)), 18 * sm, specOf(specU, nu), 4 * sm,
+                             specOf(specIn, mu), 4 * sm, N, M, T);
+          P.opA = 1; P.revA = 1;
+          P.alpha = make_double2(z[mu][nu].x, -z[mu][nu].y);
+          P.accumulate = 1;
+          TRY(nspt_zgemm64(P, nb, st));
+        }
+      }
+    }
+    // truncate inner_mu and return it to the frequency domain (in place in specIn)
+    TRY(nspt_fft_inv64(specIn, serTmp, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st));
+    TRY(nspt_fft_fwd64(serTmp, T1, specIn, (int)E, T, nb * 4, M, 0, 0, st));
+    // 4. S_mu = U_mu * inner_mu
+    for (int mu = 0; mu < 4; ++mu) {
+      ZgemmParams P = zg(ZG_MODE, specOf(specU, mu), 4 * sm, specOf(specIn, mu), 4 * sm, specOf(specAcc, mu), 4 * sm,
+                         N, M, T);
+      TRY(nspt_zgemm64(P, nb, st));
+    }
+    TRY(nspt_fft_inv64(specAcc, serS, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st));
+    // 5. drift and the Langevin increment Y = i X
+    TRY(nspt_tek_drift(serS, imtr, eta, F, serY, N, T, (long long)nb * 4, eps, st));
+    // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
+    TRY(cudaMemsetAsync(serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+    TRY(cudaMemsetAsync(serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+    TRY(add_identity(serR[0], T1, N, (long long)nb * 4, st));
+    int cur = 0;
+    for (int n = T; n >= 1; --n) {
+      const int t = T - n + 1;
+      const int Mt = next_pow2(2 * (t + 1));
+      TRY(nspt_fft_fwd64(serY, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
+      TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, t - 1, nb * 4, Mt, 0, 0, st));
+      ZgemmParams P = zg(ZG_MODE, spY, Mt, spR, Mt, spC, Mt, N, Mt, t);
+      TRY(nspt_zgemm64(P, nb * 4, st));
+      TRY(nspt_fft_inv64(spC, serR[cur ^ 1], T1, (int)E, N, t, nb * 4, Mt, 0, 0, 1.0 / n, 1, st));
+      cur ^= 1;
+    }
+    // 7. U <- exp_star(i X) * U  (spectrum of the old U is still in specU);
+    //    order 0 is exactly U^(0) since X^(0) = 0, so it is not rewritten
+    TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, T, nb * 4, M, 0, 0, st));
+    ZgemmParams P = zg(ZG_MODE, spR, M, specU, M, spC, M, N, M, T);
+    TRY(nspt_zgemm64(P, nb * 4, st));
+    TRY(nspt_fft_inv64(spC, U, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st, /*kmin=*/1));
+    return NSPT_OK;
+  }
+  // ---------------- naive form ----------------
+  double2* serP1 = w.take<double2>((size_t)nb * 6 * T1 * E);
+  double2* serQ = w.take<double2>((size_t)nb * 12 * T1 * E);
+  double2* serIn = w.take<double2>((size_t)nb * 4 * T1 * E);
+  double2* serS = w.take<double2>((size_t)nb * 4 * T1 * E);
+  double2* serY = w.take<double2>((size_t)nb * 4 * T1 * E);
+  double2* serR[2] = {w.take<double2>((size_t)nb * 4 * T1 * E), w.take<double2>((size_t)nb * 4 * T1 * E)};
+  double2* serU0 = w.take<double2>((size_t)nb * 4 * T1 * E);
+  double* imtr = w.take<double>((size_t)nb * 4 * T1);
+  auto link = [&](const double2* base, int mu) { return base + (long long)mu * T1 * E; };
+  auto wlink = [&](double2* base, int mu) { return base + (long long)mu * T1 * E; };
+  for (int i = 0; i < 6; ++i) {
+    const int mu = kPairs[i][0], nu = kPairs[i][1];
+    ZgemmParams P = zg(ZG_CONV, link(U, nu), 4 * T1, link(U, mu), 4 * T1, serP1 + (long long)i * T1 * E, 6 * T1, N,
+                       T + 1, T);
+    P.opB = 1;
+    TRY(nspt_zgemm64(P, nb, st));
+  }
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = 0; nu < 4; ++nu) {
+      if (mu == nu) continue;
+      ZgemmParams P = zg(ZG_CONV, link(U, mu), 4 * T1, link(U, nu), 4 * T1,
+                         serQ + (long long)ordered_index(mu, nu) * T1 * E, 12 * T1, N, T + 1, T);
+      TRY(nspt_zgemm64(P, nb, st));
+    }
+  for (int mu = 0; mu < 4; ++mu) {
+    bool first = true;
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == mu) continue;
+      {
+        const int pi = (mu < nu) ? pair_index(mu, nu) : pair_index(nu, mu);
+        ZgemmParams P = zg(ZG_CONV, serP1 + (long long)pi * T1 * E, 6 * T1, link(U, nu), 4 * T1, wlink(serIn, mu),
+                           4 * T1, N, T + 1, T);
+        if (mu > nu) P.opA = 1;
+        P.opB = 1;
+        P.alpha = z[mu][nu];
+        P.accumulate = first ? 0 : 1;
+        first = false;
+        TRY(nspt_zgemm64(P, nb, st));
+      }
+      {
+        ZgemmParams P = zg(ZG_CONV, serQ + (long long)ordered_index(mu, nu) * T1 * E, 12 * T1, link(U, nu), 4 * T1,
+                           wlink(serIn, mu), 4 * T1, N, T + 1, T);
+        P.opA = 1;
+        P.alpha = make_double2(z[mu][nu].x, -z[mu][nu].y);
+        P.accumulate = 1;
+        TRY(nspt_zgemm64(P, nb, st));
+      }
+    }
+  }
+  {
+    ZgemmParams P = zg(ZG_CONV, U, T1, serIn, T1, serS, T1, N, T + 1, T);
+    TRY(nspt_zgemm64(P, nb * 4, st));
+  }
+  TRY(nspt_tek_drift(serS, imtr, eta, F, serY, N, T, (long long)nb * 4, eps, st));
+  TRY(cudaMemsetAsync(serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+  TRY(cudaMemsetAsync(serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+  TRY(add_identity(serR[0], T1, N, (long long)nb * 4, st));
+  int cur = 0;
+  for (int n = T; n >= 1; --n) {
+    const int t = T - n + 1;
+    ZgemmParams P = zg(ZG_CONV, serY, T1, serR[cur], T1, serR[cur ^ 1], T1, N, t + 1, t);
+    P.alpha = make_double2(1.0 / n, 0.0);
+    TRY(nspt_zgemm64(P, nb * 4, st));
+    TRY(add_identity(serR[cur ^ 1], T1, N, (long long)nb * 4, st));
+    cur ^= 1;
+  }
+  TRY(cudaMemcpyAsync(serU0, U, (size_t)nb * 4 * T1 * E * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+  ZgemmParams P = zg(ZG_CONV, serR[cur], T1, serU0, T1, U, T1, N, T + 1, T);
+  TRY(nspt_zgemm64(P, nb * 4, st));
+  return NSPT_OK;
+}
+
+std::mutex g_init_mu;
+int g_init_dev[64] = {0};
+
+}  // namespace
+
+void nspt_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+
+extern "C" {
+
+void nspt_opts_default(nspt_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->algo = NSPT_ALGO_AUTO;
+  o->prec = NSPT_PREC_FP64;
+  o->rescale_log2r = 0;
+}
+
+int nspt_init(void) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) { g_last_cuda = e; return NSPT_ERR_CUDA; }
+  if (dev < 0 || dev >= 64) return NSPT_ERR_DEVICE;
+  std::lock_guard<std::mutex> lk(g_init_mu);
+  if (g_init_dev[dev] == 1) return NSPT_OK;
+  if (g_init_dev[dev] == -1) return NSPT_ERR_DEVICE;
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) { g_last_cuda = e; return NSPT_ERR_CUDA; }
+  if (!(prop.major == 10 && prop.minor == 3)) { g_init_dev[dev] = -1; return NSPT_ERR_DEVICE; }
+  int rc = nspt_split_init();
+  if (rc != NSPT_OK) return rc;
+  g_init_dev[dev] = 1;
+  return NSPT_OK;
+}
+
+size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opts) {
+  Plan p;
+  if (make_plan(N, T, batch, opts, &p) != NSPT_OK) return 0;
+  switch (op) {
+    case NSPT_OP_MUL: return ws_mul(p);
+    case NSPT_OP_MUL_BACKWARD: return ws_bwd(p);
+    case NSPT_OP_LANGEVIN: return ws_langevin(p);
+    default: return 0;
+  }
+}
+
+static int check_ws(const nspt_opts* o, size_t need) {
+  if (need == 0) return NSPT_OK;
+  if (!o || !o->workspace || o->workspace_bytes < need) return NSPT_ERR_WORKSPACE;
+  if (((uintptr_t)o->workspace) & 255) return NSPT_ERR_WORKSPACE;
+  return NSPT_OK;
+}
+
+int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int batch, const nspt_opts* opts,
+                     void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!A || !B || !C) return NSPT_ERR_ARG;
+  const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
+  if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_mul(p)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.prec == NSPT_PREC_FP64)
+    return mul_fp64(p, (const double2*)A, (const double2*)B, (double2*)C, opts ? opts->workspace : nullptr, st);
+  return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, (const double2*)A,
+                        (const double2*)B, (double2*)C, opts->workspace, st);
+}
+
+int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB, int N, int T,
+                              int batch, const nspt_opts* opts, void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!A || !B || !gC) return NSPT_ERR_ARG;
+  if (!gA && !gB) return NSPT_OK;
+  const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
+  const void* ins[3] = {A, B, gC};
+  for (int i = 0; i < 3; ++i)
+    if (overlaps(gA, bytes, ins[i], bytes) || overlaps(gB, bytes, ins[i], bytes)) return NSPT_ERR_ALIAS;
+  if (overlaps(gA, bytes, gB, bytes)) return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_bwd(p)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.prec == NSPT_PREC_FP64)
+    return bwd_fp64(p, (const double2*)A, (const double2*)B, (const double2*)gC, (double2*)gA, (double2*)gB,
+                    opts ? opts->workspace : nullptr, st);
+  return nspt_split_bwd(p.N, p.T, p.batch, p.M, p.slices, p.log2r, (const double2*)A, (const double2*)B,
+                        (const double2*)gC, (double2*)gA, (double2*)gB, opts->workspace, st);
+}
+
+int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int batch, int flux, double eps,
+                           const nspt_opts* opts, void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!U || !eta) return NSPT_ERR_ARG;
+  const int L = (int)llround(sqrt((double)N));
+  if (L * L != N || flux <= 0) return NSPT_ERR_ARG;
+  int a = flux % L, bb = L;
+  while (a) { int t = bb % a; bb = a; a = t; }
+  if (bb != 1) return NSPT_ERR_ARG;
+  if (!(eps > 0.0) || !std::isfinite(eps)) return NSPT_ERR_ARG;
+  const size_t ubytes = (size_t)batch * 4 * (T + 1) * p.E * sizeof(double2);
+  const size_t ebytes = (size_t)batch * 4 * p.E * sizeof(double2);
+  if (overlaps(U, ubytes, eta, ebytes) || overlaps(F, ubytes, U, ubytes) || overlaps(F, ubytes, eta, ebytes))
+    return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_langevin(p)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  if (p.prec != NSPT_PREC_FP64) {
+    return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, (double2*)U, (const double2*)eta, (double2*)F, flux,
+                               eps, opts->workspace, (cudaStream_t)stream);
+  }
+  return langevin_fp64(p, (double2*)U, (const double2*)eta, (double2*)F, flux, eps, opts ? opts->workspace : nullptr,
+                       (cudaStream_t)stream);
+}
+
+int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {
+  if (!A || !At || N < 1 || T < 0 || batch < 1) return NSPT_ERR_ARG;
+  if (ilog2_exact(M) < 0 || M < 2 * (T + 1) || M > 512) return NSPT_ERR_ARG;
+  const long long E = (long long)N * N;
+  if (overlaps(A, (size_t)batch * (T + 1) * E * 16, At, (size_t)batch * M * E * 16)) return NSPT_ERR_ALIAS;
+  int rc = nspt_init();
+  if (rc) return rc;
+  cudaError_t e = nspt_fft_fwd64((const double2*)A, T + 1, (double2*)At, (int)E, T, batch, M, 0, 0, (cudaStream_t)stream);
+  if (e != cudaSuccess) { g_last_cuda = e; return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+int nspt_order_ifft(const void* Ct, void* C, int N, int T, int batch, int M, void* stream) {
+  if (!Ct || !C || N < 1 || T < 0 || batch < 1) return NSPT_ERR_ARG;
+  if (ilog2_exact(M) < 0 || M < 2 * (T + 1) || M > 512) return NSPT_ERR_ARG;
+  const long long E = (long long)N * N;
+  if (overlaps(C, (size_t)batch * (T + 1) * E * 16, Ct, (size_t)batch * M * E * 16)) return NSPT_ERR_ALIAS;
+  int rc = nspt_init();
+  if (rc) return rc;
+  cudaError_t e = nspt_fft_inv64((const double2*)Ct, (double2*)C, T + 1, (int)E, N, T, batch, M, 0, 0, 1.0, 0,
+                                 (cudaStream_t)stream);
+  if (e != cudaSuccess) { g_last_cuda = e; return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+const char* nspt_status_string(int s) {
+  switch (s) {
+    case NSPT_OK: return "ok";
+    case NSPT_ERR_ARG: return "invalid argument";
+    case NSPT_ERR_ALIAS: return "output overlaps an input";
+    case NSPT_ERR_UNSUPPORTED: return "unsupported option combination";
+    case NSPT_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case NSPT_ERR_CUDA: return "CUDA error";
+    case NSPT_ERR_TIMEOUT: return "device-side wait timed out";
+    case NSPT_ERR_DEVICE: return "device is not sm_103 (B300)";
+    default: return "unknown status";
+  }
+}
+
+const char* nspt_last_error(void) { return cudaGetErrorString(g_last_cuda); }
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+// Shared device/host helpers of the NSPT polynomial-matrix library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/nspt.h"
+
+#define NSPT_CUDA_TRY(expr)                                        \
+  do {                                                             \
+    cudaError_t _e = (expr);                                       \
+    if (_e != cudaSuccess) { nspt_set_last_cuda_error(_e); return NSPT_ERR_CUDA; } \
+  } while (0)
+
+void nspt_set_last_cuda_error(cudaError_t e);
+
+// ---------------------------------------------------------------------------
+// complex double helpers (interleaved re, im = double2)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__host__ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+
+// Workspace carving: 256-byte aligned bump allocator over a caller-owned buffer.
+struct WsCarver {
+  char* base;
+  size_t off;
+  size_t cap;
+  __host__ WsCarver(void* b, size_t c) : base((char*)b), off(0), cap(c) {}
+  template <typename T>
+  __host__ T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  }
+  __host__ bool fits() const { return off <= cap; }
+};
+
+static inline int ilog2_exact(int M) {
+  int s = 0;
+  while ((1 << s) < M) ++s;
+  return ((1 << s) == M) ? s : -1;
+}

@@ -1,0 +1,101 @@
+// Elementwise kernels of the TEK Langevin step (Eqs. 2-3 in rescaled time).
+//
+// From the staple series S_mu (Eq. 3, plus sign on the second term) of every
+// link of every stream:
+//   F^(k) = i [S^(k) - S^(k)^H - Tr(S^(k) - S^(k)^H)/N]            (drift)
+//   X^(0) = 0, X^(1) = eps F^(1) + sqrt(2 eps) eta, X^(k>=2) = eps F^(k)
+//   Y = i X                                         (argument of exp_star)
+// With s = sum_i Im S_ii, Tr(S - S^H) = 2 i s, so F = i (S - S^H) + (2 s/N) 1.
+// A 32x32 tile of S and its mirror tile are staged in shared memory so that
+// both the direct and the transposed reads are coalesced.
+#include "common.cuh"
+#include "tek.cuh"
+#include "prof.cuh"
+
+namespace {
+
+// one warp per matrix: out[m] = sum_i Im S_m[i][i]
+__global__ void imag_trace_kernel(const double2* __restrict__ S, double* __restrict__ out, int N, long long nmat) {
+  const long long m = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (m >= nmat) return;
+  const double2* Sm = S + m * N * N;
+  double acc = 0.0;
+  for (int i = lane; i < N; i += 32) acc += Sm[(long long)i * N + i].y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) out[m] = acc;
+}
+
+// grid: (tiles_j, tiles_i, nmat); block (32, 8)
+__global__ void drift_kernel(const double2* __restrict__ S, const double* __restrict__ imtr,
+                             const double2* __restrict__ eta, double2* __restrict__ F,
+                             double2* __restrict__ Y, int N, int T, double eps, double noise_amp) {
+  __shared__ double2 tA[32][33];   // S[i0+r][j0+c]
+  __shared__ double2 tB[32][33];   // S[j0+r][i0+c]
+  const long long m = blockIdx.z;  // matrix index = series*(T+1) + k
+  const int k = (int)(m % (T + 1));
+  const long long series = m / (T + 1);
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const double2* Sm = S + m * N * N;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = threadIdx.x;
+    tA[r][c] = (i0 + r < N && j0 + c < N) ? Sm[(long long)(i0 + r) * N + j0 + c] : make_double2(0, 0);
+    tB[r][c] = (j0 + r < N && i0 + c < N) ? Sm[(long long)(j0 + r) * N + i0 + c] : make_double2(0, 0);
+  }
+  __syncthreads();
+  const double diag = 2.0 * imtr[m] / (double)N;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int c = threadIdx.x;
+    const int i = i0 + r, j = j0 + c;
+    if (i >= N || j >= N) continue;
+    const double2 a = tA[r][c];       // S_ij
+    const double2 bt = tB[c][r];      // S_ji
+    // D = S_ij - conj(S_ji);  F = i D + diag * delta_ij
+    const double dr = a.x - bt.x, di = a.y + bt.y;
+    double2 f = make_double2(-di, dr);
+    if (i == j) f.x += diag;
+    const long long off = m * N * N + (long long)i * N + j;
+    if (F) F[off] = f;
+    // X = eps F (+ noise at order 1), X^(0) = 0; Y = i X
+    double2 x = make_double2(eps * f.x, eps * f.y);
+    if (k == 0) x = make_double2(0.0, 0.0);
+    if (k == 1) {
+      const double2 e = eta[series * N * N + (long long)i * N + j];
+      x.x += noise_amp * e.x;
+      x.y += noise_amp * e.y;
+    }
+    Y[off] = make_double2(-x.y, x.x);
+  }
+}
+
+}  // namespace
+
+cudaError_t nspt_tek_drift(const double2* S, double* imtr_ws, const double2* eta, double2* F, double2* Y,
+                           int N, int T, long long nseries, double eps, cudaStream_t st) {
+  const long long nmat = nseries * (T + 1);
+  if (nmat == 0) return cudaSuccess;
+  const int wpb = 8;
+  ProfScope ps(NSPT_STAGE_TEK, st, 1 + (int)((nmat + 65534) / 65535));
+  imag_trace_kernel<<<(unsigned)((nmat + wpb - 1) / wpb), wpb * 32, 0, st>>>(S, imtr_ws, N, nmat);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int tiles = (N + 31) / 32;
+  if (nmat > 65535) {
+    // chunk over matrices (grid z limit)
+    for (long long m0 = 0; m0 < nmat; m0 += 65535 / (T + 1) * (T + 1)) {
+      const long long chunk = std::min<long long>(65535 / (T + 1) * (T + 1), nmat - m0);
+      const long long s0 = m0 / (T + 1);
+      dim3 grid(tiles, tiles, (unsigned)chunk);
+      drift_kernel<<<grid, dim3(32, 8), 0, st>>>(S + m0 * N * N, imtr_ws + m0, eta + s0 * N * N,
+                                                 F ? F + m0 * N * N : nullptr, Y + m0 * N * N, N, T, eps,
+                                                 sqrt(2.0 * eps));
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  dim3 grid(tiles, tiles, (unsigned)nmat);
+  drift_kernel<<<grid, dim3(32, 8), 0, st>>>(S, imtr_ws, eta, F, Y, N, T, eps, sqrt(2.0 * eps));
+  return cudaGetLastError();
+}

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every symbol include/nspt.h declares;
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "nspt.h")).read()
+    return sorted(set(re.findall(r"NSPT_API\s+[\w\s\*]+?\b(nspt_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2001_02835_b300 as n
+    return n.lib()
+
+
+def test_every_declared_symbol_is_exported(L):
+    syms = _declared_symbols()
+    assert len(syms) >= 10
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_status_strings(L):
+    assert L.nspt_status_string(0) == b"ok"
+    assert b"workspace" in L.nspt_status_string(-4)
+    assert L.nspt_status_string(-99) == b"unknown status"
+
+
+def test_argument_checks_need_no_gpu(L):
+    import paper_2001_02835_b300 as n
+    o = n.make_opts()
+    # NULL pointers / bad sizes are rejected on the host before any CUDA call
+    assert L.nspt_polymat_mul(None, None, None, 4, 3, 1, ctypes.byref(o), None) == -1
+    assert L.nspt_polymat_mul(1 << 20, 2 << 20, 3 << 20, 0, 3, 1, ctypes.byref(o), None) == -1
+    assert L.nspt_polymat_mul(1 << 20, 2 << 20, 3 << 20, 4, -1, 1, ctypes.byref(o), None) == -1
+    # output overlapping an input
+    assert L.nspt_polymat_mul(1 << 20, 1 << 24, (1 << 20) + 16, 4, 3, 1, ctypes.byref(o), None) == -2
+    # FFT length not a power of two / too short for wrap-free convolution
+    o2 = n.make_opts(algo="fft", fft_len=12)
+    assert L.nspt_polymat_mul(1 << 20, 1 << 24, 1 << 28, 4, 3, 1, ctypes.byref(o2), None) == -1
+    o3 = n.make_opts(algo="fft", fft_len=4)
+    assert L.nspt_polymat_mul(1 << 20, 1 << 24, 1 << 28, 4, 3, 1, ctypes.byref(o3), None) == -1
+    # FFT form without a workspace
+    o4 = n.make_opts(algo="fft")
+    assert L.nspt_polymat_mul(1 << 20, 1 << 24, 1 << 28, 4, 3, 1, ctypes.byref(o4), None) == -4
+    # Langevin: N must be L^2 with gcd(flux, L) = 1, eps > 0
+    assert L.nspt_tek_langevin_step(1 << 20, 1 << 30, None, 10, 2, 1, 1, 0.01, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_langevin_step(1 << 20, 1 << 30, None, 9, 2, 1, 3, 0.01, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_langevin_step(1 << 20, 1 << 30, None, 9, 2, 1, 1, -0.01, ctypes.byref(o), None) == -1
+
+
+def test_workspace_sizes(L):
+    import paper_2001_02835_b300 as n
+    naive = n.make_opts(algo="naive")
+    assert n.workspace_size(0, 225, 31, 4, naive) == 0
+    fft = n.make_opts(algo="fft")
+    spec = 4 * 64 * 225 * 225 * 16
+    assert n.workspace_size(0, 225, 31, 4, fft) >= 3 * spec
+    assert n.workspace_size(1, 225, 31, 4, fft) >= 4 * spec
+    assert n.workspace_size(0, 225, 31, 4, n.make_opts(algo="fft", fft_len=128)) >= 6 * spec

@@ -1,0 +1,58 @@
+"""GPU parity of the NSPT Langevin step (FP64 form) against the oracle."""
+import numpy as np
+import pytest
+
+import nspt_synth as syn
+from oracle import polymat as pm
+from oracle import tek
+
+from tests.gpu_util import dev, host, max_order_rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def nspt():
+    import paper_2001_02835_b300 as n
+    assert n.lib().nspt_init() == 0
+    return n
+
+
+@pytest.mark.parametrize("algo", ["naive", "fft"])
+@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 8, 1), (3, 1, 2, 2), (2, 1, 5, 1), (5, 2, 4, 2)])
+def test_langevin_step_matches_oracle(nspt, algo, L, flux, T, streams):
+    g = syn.rng(syn.SEED_BASE + 10 * L + T)
+    N = L * L
+    U = syn.link_series(g, L, flux, T, streams)
+    eta = syn.hermitian_noise(g, N, streams * 4).reshape(streams, 4, N, N)
+    eps = 0.01
+    z = tek.twist_phases(L, flux)
+    refU = np.empty_like(U)
+    refF = np.empty_like(U)
+    for s in range(streams):
+        refU[s], refF[s] = tek.langevin_step(U[s], eta[s], z, eps)
+    tU = dev(U)
+    _, F = nspt.tek_langevin_step(tU, dev(eta), flux, eps, want_drift=True, algo=algo)
+    gotU = host(tU)
+    gotF = host(F)
+    # F^(0) vanishes at the twist-eater vacuum: compare with an absolute floor
+    assert np.abs(gotF - refF).max() <= 1e-12 * max(1.0, np.abs(refF).max())
+    assert max_order_rel(gotU, refU) <= TOL
+    np.testing.assert_array_equal(gotU[:, :, 0], U[:, :, 0])
+
+
+def test_langevin_generic_vacuum_drift(nspt):
+    """A non-vacuum order 0 (Haar links): the drift is nonzero at every order."""
+    g = syn.rng(4100)
+    L, flux, T = 3, 1, 4
+    N = L * L
+    U = syn.link_series(g, L, flux, T, 1)
+    U[0, :, 0] = syn.haar_sun(g, N, 4)
+    eta = syn.hermitian_noise(g, N, 4).reshape(1, 4, N, N)
+    z = tek.twist_phases(L, flux)
+    refU, refF = tek.langevin_step(U[0], eta[0], z, 0.02)
+    tU = dev(U)
+    _, F = nspt.tek_langevin_step(tU, dev(eta), flux, 0.02, want_drift=True, algo="fft")
+    assert max_order_rel(host(F)[0], refF) <= TOL
+    assert max_order_rel(host(tU)[0], refU) <= TOL
