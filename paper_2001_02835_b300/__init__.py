@@ -70,6 +70,9 @@ _SIGS = {
     "nspt_profile_end": (_i, [_i, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
     "nspt_stage_name": (ctypes.c_char_p, [_i]),
     "nspt_last_error": (ctypes.c_char_p, []),
+    "nspt_device_status": (_i, [ctypes.POINTER(Opts), _vp]),
+    "nspt_split_slices": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "nspt_split_mode_gemm": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp]),
 }
 
 
@@ -258,6 +261,34 @@ def profile_end() -> dict:
     if rc < 0:
         _check(rc, "nspt_profile_end")
     return {lib().nspt_stage_name(i).decode(): (ms[i], int(n[i])) for i in range(NSTAGES) if n[i]}
+
+
+def split_slices(X: torch.Tensor, S: int, trans: bool = False, conj: bool = False):
+    """Stage entry: digit slices (bf16 (Q, S, 2, N, Kp)) and row exponents (int32 (Q, N))
+    of the Q matrices X (Q, N, N) complex128 (see include/nspt.h)."""
+    _check_tensor(X, "X")
+    Q, N = X.shape[0], X.shape[1]
+    Kp = (N + 7) // 8 * 8
+    sl = torch.zeros((Q, S, 2, N, Kp), dtype=torch.bfloat16, device=X.device)
+    ex = torch.empty((Q, N), dtype=torch.int32, device=X.device)
+    _check(lib().nspt_split_slices(X.data_ptr(), sl.data_ptr(), ex.data_ptr(), N, Q, S, int(trans), int(conj),
+                                   _stream_ptr(X.device)), "nspt_split_slices")
+    return sl, ex
+
+
+def split_mode_gemm(slA: torch.Tensor, slB: torch.Tensor, expA: torch.Tensor, expB: torch.Tensor, N: int,
+                    S: int) -> torch.Tensor:
+    """Stage entry: mode GEMMs from digit slices (see include/nspt.h).
+    Returns Ct as float32 (Q, N, N, 4) = (re_hi, re_lo, im_hi, im_lo)."""
+    Q = expA.shape[0]
+    Ct = torch.empty((Q, N, N, 4), dtype=torch.float32, device=slA.device)
+    err = torch.zeros(1, dtype=torch.int32, device=slA.device)
+    rc = lib().nspt_split_mode_gemm(slA.data_ptr(), slB.data_ptr(), expA.data_ptr(), expB.data_ptr(), Ct.data_ptr(),
+                                    N, Q, S, err.data_ptr(), _stream_ptr(slA.device))
+    _check(rc, "nspt_split_mode_gemm")
+    if int(err.item()) != 0:
+        raise NsptError("nspt_split_mode_gemm: device wait timed out (code %d)" % int(err.item()))
+    return Ct
 
 
 class PolymatMul(torch.autograd.Function):

@@ -536,4 +536,30 @@ const char* nspt_status_string(int s) {
 
 const char* nspt_last_error(void) { return cudaGetErrorString(g_last_cuda); }
 
+int nspt_device_status(const nspt_opts* opts, void* stream) {
+  if (!opts || !opts->workspace) return NSPT_ERR_ARG;
+  int err = 0;
+  int rc = nspt_split_read_error(opts->workspace, &err, (cudaStream_t)stream);
+  if (rc) return rc;
+  return err ? NSPT_ERR_TIMEOUT : NSPT_OK;
+}
+
+int nspt_split_slices(const void* X, void* slices, int* exps, int N, int Q, int S, int trans, int conj,
+                      void* stream) {
+  if (!X || !slices || !exps || N < 1 || N > 1024 || Q < 1 || Q > 65535 || S < 2 || S > 8) return NSPT_ERR_ARG;
+  int rc = nspt_init();
+  if (rc) return rc;
+  return nspt_split_slice(S, (const double2*)X, Q, Q, 0, trans ? 1 : 0, conj ? 1 : 0, N, Q, slices, exps,
+                          (cudaStream_t)stream);
+}
+
+int nspt_split_mode_gemm(const void* slA, const void* slB, const int* expA, const int* expB, void* Ct, int N, int Q,
+                         int S, int* err, void* stream) {
+  if (!slA || !slB || !expA || !expB || !Ct || !err || N < 1 || N > 1024 || Q < 1 || S < 2 || S > 8)
+    return NSPT_ERR_ARG;
+  int rc = nspt_init();
+  if (rc) return rc;
+  return nspt_split_gemm_stage(slA, slB, expA, expB, Ct, N, Q, S, err, (cudaStream_t)stream);
+}
+
 }  // extern "C"

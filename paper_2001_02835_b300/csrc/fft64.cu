@@ -78,11 +78,18 @@ fft_fwd64_kernel(const double2* __restrict__ in, long long in_stride, double2* _
   for (int i = y; i < M; i += 8) dst[(long long)bitrev<M>(i) * E] = sm[i * EB + e];
 }
 
+__device__ __forceinline__ double2 load_spec(const double2* p) { return *p; }
+// double-float spectrum (re_hi, re_lo, im_hi, im_lo) from the tensor-core GEMM
+__device__ __forceinline__ double2 load_spec(const float4* p) {
+  const float4 v = *p;
+  return make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+}
+
 // in:  [batch][M][E] spectrum; out: [batch][T+1][E], row k scaled by
 // 2^(log2u - k*log2r) / M.
-template <int M, int EB>
+template <int M, int EB, typename InT>
 __global__ void __launch_bounds__(EB * 8)
-fft_inv64_kernel(const double2* __restrict__ in, double2* __restrict__ out, long long out_stride, int E,
+fft_inv64_kernel(const InT* __restrict__ in, double2* __restrict__ out, long long out_stride, int E,
                  int N, int T, int log2u, int log2r, double post, int add_identity, int kmin) {
   extern __shared__ double2 sm[];
   const int e = threadIdx.x;
@@ -90,9 +97,9 @@ fft_inv64_kernel(const double2* __restrict__ in, double2* __restrict__ out, long
   const int b = blockIdx.y;
   const long long e0 = (long long)blockIdx.x * EB;
   const bool valid = (e0 + e) < E;
-  const double2* src = in + (long long)b * M * E + e0 + e;
+  const InT* src = in + (long long)b * M * E + e0 + e;
   for (int p = y; p < M; p += 8)
-    sm[bitrev<M>(p) * EB + e] = valid ? src[(long long)p * E] : make_double2(0.0, 0.0);
+    sm[bitrev<M>(p) * EB + e] = valid ? load_spec(src + (long long)p * E) : make_double2(0.0, 0.0);
   __syncthreads();
 #pragma unroll 1
   for (int h = 1; h <= M / 4; h <<= 1) {
@@ -140,12 +147,12 @@ cudaError_t launch_fwd(const double2* in, long long ins, double2* out, int E, in
   return cudaGetLastError();
 }
 
-template <int M>
-cudaError_t launch_inv(const double2* in, double2* out, long long outs, int E, int N, int T, int batch, int lu,
+template <int M, typename InT>
+cudaError_t launch_inv(const InT* in, double2* out, long long outs, int E, int N, int T, int batch, int lu,
                        int lr, double post, int addi, int kmin, cudaStream_t st) {
   constexpr int EB = strip_entries<M>();
   const size_t smem = (size_t)M * EB * sizeof(double2);
-  auto kern = fft_inv64_kernel<M, EB>;
+  auto kern = fft_inv64_kernel<M, EB, InT>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
@@ -175,7 +182,20 @@ cudaError_t nspt_fft_inv64(const double2* in, double2* out, long long out_stride
   if (2 * (t + 1) > M) return cudaErrorInvalidValue;
   ProfScope ps(NSPT_STAGE_FFT_INV, st);
   switch (M) {
-#define NSPT_CASE(m) case m: return launch_inv<m>(in, out, out_stride, E, N, t, batch, log2u, log2r, post, add_identity, kmin, st);
+#define NSPT_CASE(m) case m: return launch_inv<m, double2>(in, out, out_stride, E, N, t, batch, log2u, log2r, post, add_identity, kmin, st);
+    NSPT_CASE(2) NSPT_CASE(4) NSPT_CASE(8) NSPT_CASE(16) NSPT_CASE(32) NSPT_CASE(64) NSPT_CASE(128)
+    NSPT_CASE(256) NSPT_CASE(512)
+#undef NSPT_CASE
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t nspt_fft_inv64_df(const float4* in, double2* out, long long out_stride, int E, int N, int t, int batch,
+                              int M, int log2u, int log2r, cudaStream_t st) {
+  if (2 * (t + 1) > M) return cudaErrorInvalidValue;
+  ProfScope ps(NSPT_STAGE_FFT_INV, st);
+  switch (M) {
+#define NSPT_CASE(m) case m: return launch_inv<m, float4>(in, out, out_stride, E, N, t, batch, log2u, log2r, 1.0, 0, 0, st);
     NSPT_CASE(2) NSPT_CASE(4) NSPT_CASE(8) NSPT_CASE(16) NSPT_CASE(32) NSPT_CASE(64) NSPT_CASE(128)
     NSPT_CASE(256) NSPT_CASE(512)
 #undef NSPT_CASE

@@ -1,17 +1,268 @@
-// Split-precision product path (placeholder until the tensor-core GEMM lands).
-#include "common.cuh"
-#include "split.cuh"
+// Split-precision product path: FP64 spectra -> BF16 digit slices -> tensor-core
+// mode GEMMs with exact FP32 digit groups -> double-float spectrum -> inverse
+// FFT in FP64 (Sec. 2 Steps 1-5 with Step 3 on the tensor cores).
+//
+// Slicing (an error-free split in the spirit of Ozaki et al.): each row r of
+// an operand gets e_r with |x| < 2^e_r for all of its real and imaginary
+// parts; x * 2^(W - e_r), W = 8S - 1, is rounded to an integer X <= 2^W read
+// straight from the FP64 bit pattern, and X is cut into S balanced base-256
+// digits d_0..d_{S-1} (|d_i| <= 128), so x = 2^(e_r - 7) sum_i d_i 2^(-8i) up to
+// 2^(e_r - W - 1).  Digit i is stored as the BF16 value d_i * 2^(-8i) (exact).
+// No FP64 arithmetic is used: on B300 the FP64 pipe is about 1/58 of FP32.
+#include <algorithm>
+#include <cmath>
 
-int nspt_split_init() { return NSPT_OK; }
-size_t nspt_split_ws_mul(int, int, int, int, int) { return 0; }
-size_t nspt_split_ws_bwd(int, int, int, int, int) { return 0; }
-int nspt_split_mul(int, int, int, int, int, int, bool, const double2*, const double2*, double2*, void*, cudaStream_t) {
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "prof.cuh"
+#include "split.cuh"
+#include "split_gemm.cuh"
+#include "zgemm64.cuh"
+
+namespace {
+
+int g_num_sms = 0;
+
+template <int S>
+__device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
+  constexpr int W = 8 * S - 1;
+  const long long bits = __double_as_longlong(x);
+  const int bexp = (int)((bits >> 52) & 0x7FF);
+  unsigned long long X = 0;
+  if (bexp != 0) {
+    const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = 1075 + e - W - bexp;
+    if (sh <= 0) X = mant << (-sh);
+    else if (sh < 64) X = (mant + (1ull << (sh - 1))) >> sh;
+  }
+  const float sign = bits < 0 ? -1.f : 1.f;
+#pragma unroll
+  for (int i = S - 1; i >= 1; --i) {
+    int d = (int)(X & 255ull);
+    X >>= 8;
+    if (d > 128) { d -= 256; X += 1; }
+    s[i] = sign * (float)d * __int_as_float((127 - 8 * i) << 23);
+  }
+  s[0] = sign * (float)(int)X;
+}
+
+__device__ __forceinline__ int bexp_of(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// grid (ceil(N/RB), Q); block 256.  Output row r of plane q is row r of the
+// source matrix (trans = 0) or its column r (trans = 1), conjugated if conj;
+// the source of plane q = b*M + p is mode p (rev = 0) or (M - p) mod M (rev = 1)
+// of batch element b.
+template <int S>
+__global__ void __launch_bounds__(256)
+slice_kernel(const double2* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
+             int RB, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+  extern __shared__ double2 tile[];
+  const int q = blockIdx.y;
+  const int b = q / M, p = q % M;
+  const int sp = rev ? (M - p) % M : p;
+  const double2* Xm = X + ((long long)b * bstride + sp) * N * N;
+  const int r0 = blockIdx.x * RB;
+  const int nr = min(RB, N - r0);
+  const int ld = RB + 1;
+  if (!trans) {
+    for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
+      const int rr = idx / N, k = idx % N;
+      tile[rr * N + k] = Xm[(long long)(r0 + rr) * N + k];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
+      const int k = idx / nr, rr = idx % nr;
+      tile[k * ld + rr] = Xm[(long long)k * N + r0 + rr];
+    }
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long plane = (long long)N * Kp;
+  for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
+    auto elem = [&](int k) -> double2 {
+      double2 v = trans ? tile[k * ld + rr] : tile[rr * N + k];
+      if (conj) v.y = -v.y;
+      return v;
+    };
+    int mx = 0;
+    for (int k = lane; k < N; k += 32) {
+      const double2 v = elem(k);
+      mx = max(mx, max(bexp_of(v.x), bexp_of(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int e = (mx == 0) ? -1000 : mx - 1022;  // |x| < 2^e for every part of the row
+    const int r = r0 + rr;
+    if (lane == 0) exps[(long long)q * N + r] = e;
+    __nv_bfloat16* orow = out + (long long)q * S * 2 * plane + (long long)r * Kp;
+    for (int k = 2 * lane; k < N; k += 64) {
+      const double2 v0 = elem(k);
+      const double2 v1 = (k + 1 < N) ? elem(k + 1) : make_double2(0.0, 0.0);
+      float re0[S], im0[S], re1[S], im1[S];
+      to_digits<S>(v0.x, e, re0);
+      to_digits<S>(v0.y, e, im0);
+      to_digits<S>(v1.x, e, re1);
+      to_digits<S>(v1.y, e, im1);
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        *reinterpret_cast<__nv_bfloat162*>(orow + (2LL * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
+        *reinterpret_cast<__nv_bfloat162*>(orow + (2LL * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
+      }
+    }
+  }
+}
+
+int row_block(int N) {
+  int rb = (int)(190000 / ((long long)(N + 1) * 16)) - 1;
+  return std::max(1, std::min(16, rb));
+}
+
+template <int S>
+int launch_slice(const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q,
+                 __nv_bfloat16* out, int* exps, cudaStream_t st) {
+  const int RB = row_block(N);
+  const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(slice_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  dim3 grid((N + RB - 1) / RB, Q);
+  ProfScope ps(NSPT_STAGE_SLICE, st);
+  slice_kernel<S><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, out, exps);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+int kpad(int N) { return (N + 7) & ~7; }
+
+struct SplitWs {
+  double2 *At, *Bt;
+  __nv_bfloat16 *slA, *slB;
+  int *expA, *expB, *err;
+  float4* Ct;
+};
+
+SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total) {
+  WsCarver w(ws, SIZE_MAX);
+  SplitWs s;
+  const long long E = (long long)N * N, Q = (long long)batch * M;
+  s.err = w.take<int>(64);
+  s.At = w.take<double2>((size_t)Q * E);
+  s.Bt = w.take<double2>((size_t)Q * E);
+  s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+  s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+  s.expA = w.take<int>((size_t)Q * N);
+  s.expB = w.take<int>((size_t)Q * N);
+  s.Ct = reinterpret_cast<float4*>(s.At);  // A~ is dead once sliced
+  if (total) *total = w.off;
+  return s;
+}
+
+int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
+  SplitGemmArgs a;
+  a.slicesA = w.slA; a.slicesB = w.slB; a.expA = w.expA; a.expB = w.expB; a.C = w.Ct;
+  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = w.err;
+  return nspt_split_gemm(a, st);
+}
+
+#define TRYC(x) do { cudaError_t _e = (x); if (_e != cudaSuccess) { nspt_set_last_cuda_error(_e); return NSPT_ERR_CUDA; } } while (0)
+#define TRYS(x) do { int _r = (x); if (_r != NSPT_OK) return _r; } while (0)
+
+}  // namespace
+
+int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
+                     void* out, int* exps, cudaStream_t st) {
+  __nv_bfloat16* o = (__nv_bfloat16*)out;
+  switch (S) {
+#define NSPT_CASE(s) case s: return launch_slice<s>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, o, exps, st);
+    NSPT_CASE(2) NSPT_CASE(3) NSPT_CASE(4) NSPT_CASE(5) NSPT_CASE(6) NSPT_CASE(7) NSPT_CASE(8)
+#undef NSPT_CASE
+    default: return NSPT_ERR_ARG;
+  }
+}
+
+int nspt_split_init() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  return nspt_split_gemm_init();
+}
+
+size_t nspt_split_ws_mul(int N, int T, int batch, int M, int S) {
+  size_t total = 0;
+  carve(nullptr, N, batch, M, S, &total);
+  return total;
+}
+
+size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int S) {
+  // G~ spectrum in addition to the product workspace
+  return nspt_split_ws_mul(N, T, batch, M, S) + (((size_t)batch * M * N * N * sizeof(double2) + 255) & ~(size_t)255);
+}
+
+int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescale_auto, const double2* A,
+                   const double2* B, double2* C, void* ws, cudaStream_t st) {
+  if (rescale_auto) return NSPT_ERR_UNSUPPORTED;
+  const int E = N * N, Q = batch * M;
+  SplitWs w = carve(ws, N, batch, M, S, nullptr);
+  TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
+  TRYC(nspt_fft_fwd64(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd64(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+  // a2: slices of A~_q (rows) and of B~_q^T (columns of B~_q)
+  TRYS(nspt_split_slice(S, w.At, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
+  TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+  // a3: mode GEMMs on the tensor cores
+  TRYS(gemm(w, N, Q, S, st));
+  // a4: inverse transform, truncation, unscale 2^(-k log2r)
+  TRYC(nspt_fft_inv64_df(w.Ct, C, T + 1, E, N, T, batch, M, 0, log2r, st));
+  return NSPT_OK;
+}
+
+int nspt_split_bwd(int N, int T, int batch, int M, int S, int log2r, const double2* A, const double2* B,
+                   const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st) {
+  const int E = N * N, Q = batch * M;
+  size_t off = 0;
+  SplitWs w = carve(ws, N, batch, M, S, &off);
+  double2* Gt = reinterpret_cast<double2*>((char*)ws + off);
+  TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  // with A' = r^k A, B' = r^k B, G' = r^-k G the correlations come out scaled by r^-j
+  TRYC(nspt_fft_fwd64(G, T + 1, Gt, E, T, batch, M, 0, -log2r, st));
+  if (gA) {
+    // gA~_p = G~_p (B~_p)^H
+    TRYC(nspt_fft_fwd64(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+    TRYS(nspt_split_slice(S, Gt, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
+    TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 0, 1, N, Q, w.slB, w.expB, st));
+    TRYS(gemm(w, N, Q, S, st));
+    TRYC(nspt_fft_inv64_df(w.Ct, gA, T + 1, E, N, T, batch, M, 0, -log2r, st));
+  }
+  if (gB) {
+    // gB~_p = (A~_p)^H G~_p
+    TRYC(nspt_fft_fwd64(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+    TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 1, 1, N, Q, w.slA, w.expA, st));
+    TRYS(nspt_split_slice(S, Gt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+    TRYS(gemm(w, N, Q, S, st));
+    TRYC(nspt_fft_inv64_df(w.Ct, gB, T + 1, E, N, T, batch, M, 0, -log2r, st));
+  }
+  return NSPT_OK;
+}
+
+int nspt_split_langevin(int, int, int, int, int, double2*, const double2*, double2*, int, double, void*,
+                        cudaStream_t) {
   return NSPT_ERR_UNSUPPORTED;
 }
-int nspt_split_bwd(int, int, int, int, int, int, const double2*, const double2*, const double2*, double2*, double2*,
-                   void*, cudaStream_t) {
-  return NSPT_ERR_UNSUPPORTED;
+
+int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
+                          int S, int* err, cudaStream_t st) {
+  SplitGemmArgs a;
+  a.slicesA = slA; a.slicesB = slB; a.expA = expA; a.expB = expB; a.C = (float4*)C;
+  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = err;
+  return nspt_split_gemm(a, st);
 }
-int nspt_split_langevin(int, int, int, int, int, double2*, const double2*, double2*, int, double, void*, cudaStream_t) {
-  return NSPT_ERR_UNSUPPORTED;
+
+int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st) {
+  if (!ws) return NSPT_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(host_err, ws, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
 }

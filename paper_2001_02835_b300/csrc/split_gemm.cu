@@ -1,0 +1,357 @@
+// Split-precision complex mode GEMM on the 5th-generation tensor cores
+// (FFT-CONV Step 3, C~_q = A~_q B~_q for every mode q of every batch element).
+//
+// Operands arrive as BF16 slice planes written by the slicing kernel: row r
+// of operand X (X = A, or B^T for the right operand, both K-major) is
+//   X[r][k] = 2^(e_r - 7) * sum_{i<S} s_i[r][k],   s_i = d_i * 2^(-8 i),
+// with balanced digits |d_i| <= 128 and one exponent e_r per row.  A product
+// s_i t_j is an integer multiple of 2^(-8(i+j)) below 2^(14-8(i+j)), so the
+// dot product of one digit group g = i + j stays on that grid and is exact in
+// FP32 while it has fewer than 24 significant bits.  Groups g = 0..3 keep
+// their own TMEM accumulators; groups g >= 4 share a fifth one, whose
+// rounding (the tensor core truncates at each accumulation step) stays near
+// 2^-56 of the result per step.  Real and imaginary parts give 10
+// accumulators of 48 FP32 columns = 480 of the 512 TMEM columns for a
+// 128 x 48 output tile.  The four real products of the complex product use
+// the instruction descriptor's A-negate bit for -A_im B_im.  The epilogue sums
+// the groups in double-float (hi + lo float pair), applies
+// 2^(e_A[m] + e_B[n] - 14) and writes float4 (re_hi, re_lo, im_hi, im_lo).
+//
+// Roles (one CTA per SM, persistent over tiles): warp 0 lane 0 issues TMA
+// loads, warp 1 lane 0 issues tcgen05.mma, warps 2-5 drain TMEM.  Per K block
+// of 32, all S slices of the B tile (re, im) are loaded once and the A
+// slices stream through a 4-stage ring; the triangle of slice pairs
+// i + j < S is issued against the resident B slices.  Every wait is bounded
+// (globaltimer); on time-out the kernel records an error, drains its own TMA
+// and MMA work and frees TMEM.
+#include "common.cuh"
+#include "prof.cuh"
+#include "split_gemm.cuh"
+#include "tc_ptx.cuh"
+
+namespace {
+
+constexpr int BM = 128, BN = 48, KB = 32;
+constexpr int NA_STAGES = 4;
+constexpr uint32_t A_TILE = BM * KB * 2;  // 8 KB per part
+constexpr uint32_t B_TILE = BN * KB * 2;  // 3 KB per part
+constexpr int NGROUPS = 5;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
+static_assert(2 * NGROUPS * BN <= (int)TMEM_COLS, "accumulators exceed TMEM");
+
+template <int S>
+struct Smem {
+  uint8_t a[NA_STAGES][2][A_TILE];  // [stage][re/im]
+  uint8_t b[2][S][2][B_TILE];       // [buffer][slice][re/im]
+  uint64_t full_a[NA_STAGES], empty_a[NA_STAGES];
+  uint64_t full_b[2], empty_b[2];
+  uint64_t acc_full, acc_empty, drain;
+  uint32_t tmem_base;
+  volatile int abort_flag;
+};
+
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         int code) {
+  if (tc::mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = tc::globaltimer();
+  uint32_t n = 0;
+  while (!tc::mbar_try_wait(bar, parity)) {
+    if ((++n & 255) == 0) {
+      if (*abort_flag) return false;
+      if (tc::globaltimer() - t0 > WAIT_LIMIT_NS) {
+        *abort_flag = 1;
+        atomicCAS(err, 0, code);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// error-free sum of two floats (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+__device__ __forceinline__ float pow2f(int k) {
+  k = max(-126, min(127, k));
+  return __int_as_float((k + 127) << 23);
+}
+
+// double-float sum of the digit-group accumulators, largest first
+__device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, float& lo) {
+  float h, s2, s3, e1, e2, e3;
+  two_sum(a[0], a[1], h, e1);
+  two_sum(h, a[2], s2, e2);
+  two_sum(s2, a[3], s3, e3);
+  const float l = ((e1 + e2) + e3) + a[4];
+  hi = s3 + l;
+  lo = l - (hi - s3);
+}
+
+template <int S>
+__global__ void __launch_bounds__(192, 1)
+split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const int* __restrict__ expA, const int* __restrict__ expB, float4* __restrict__ C, int N,
+                  int Q, int tilesM, int tilesN, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  Smem<S>& sm = *reinterpret_cast<Smem<S>*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nK = (N + KB - 1) / KB;
+  const long long ntiles = (long long)Q * tilesM * tilesN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NA_STAGES; ++s) { tc::mbar_init(&sm.full_a[s], 1); tc::mbar_init(&sm.empty_a[s], 1); }
+    for (int s = 0; s < 2; ++s) { tc::mbar_init(&sm.full_b[s], 1); tc::mbar_init(&sm.empty_b[s], 1); }
+    tc::mbar_init(&sm.acc_full, 1);
+    tc::mbar_init(&sm.acc_empty, 128);
+    tc::mbar_init(&sm.drain, 1);
+    sm.abort_flag = 0;
+    tc::fence_mbar_init();
+    tc::fence_proxy_async();
+    tc::prefetch_tmap(&tmA);
+    tc::prefetch_tmap(&tmB);
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&sm.tmem_base, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = sm.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------ TMA producer ------------------------------
+    int ia = 0, ib = 0;
+    uint32_t pa = 0, pb = 0;
+    uint32_t last_a_parity[NA_STAGES] = {0, 0, 0, 0}, last_b_parity[2] = {0, 0};
+    bool issued_a[NA_STAGES] = {false, false, false, false}, issued_b[2] = {false, false};
+    for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
+      const int q = (int)(t / (tilesM * tilesN));
+      const int r = (int)(t % (tilesM * tilesN));
+      const int m0 = (r / tilesN) * BM, n0 = (r % tilesN) * BN;
+      bool ok = true;
+      for (int kb = 0; kb < nK && ok; ++kb) {
+        if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
+        tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 2 * B_TILE);
+        for (int j = 0; j < S; ++j)
+          for (int c = 0; c < 2; ++c)
+            tc::tma_load_3d(sm.b[ib][j][c], &tmB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 2 + c);
+        issued_b[ib] = true;
+        last_b_parity[ib] = pb;
+        if (++ib == 2) { ib = 0; pb ^= 1; }
+        for (int i = 0; i < S; ++i) {
+          if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
+          for (int c = 0; c < 2; ++c)
+            tc::tma_load_3d(sm.a[ia][c], &tmA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
+          issued_a[ia] = true;
+          last_a_parity[ia] = pa;
+          if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+        }
+      }
+      if (!ok) break;
+    }
+    // make sure no TMA write into this CTA's shared memory is still in flight
+    volatile int no_abort = 0;
+    for (int s = 0; s < NA_STAGES; ++s)
+      if (issued_a[s]) wait_bar(&sm.full_a[s], last_a_parity[s], &no_abort, err, 7);
+    for (int s = 0; s < 2; ++s)
+      if (issued_b[s]) wait_bar(&sm.full_b[s], last_b_parity[s], &no_abort, err, 7);
+  } else if (warp == 1 && lane == 0) {
+    // ------------------------------ MMA issuer ------------------------------
+    constexpr uint32_t ID = tc::idesc_bf16(BM, BN, false);
+    constexpr uint32_t IDN = tc::idesc_bf16(BM, BN, true);
+    int ia = 0, ib = 0;
+    uint32_t pa = 0, pb = 0, pacc = 0;
+    bool any = false;
+    int local = 0;
+    for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x, ++local) {
+      if (local > 0) {
+        if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
+      }
+      tc::fence_after_sync();
+      uint32_t started = 0;  // bit (2g + c): accumulator already written in this tile
+      bool ok = true;
+      for (int kb = 0; kb < nK && ok; ++kb) {
+        if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
+        tc::fence_after_sync();
+        for (int i = 0; i < S; ++i) {
+          if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+          tc::fence_after_sync();
+          const uint32_t a_re = tc::smem_u32(sm.a[ia][0]), a_im = tc::smem_u32(sm.a[ia][1]);
+          for (int j = 0; j + i < S; ++j) {
+            const int g = min(i + j, NGROUPS - 1);
+            const uint32_t d_re = tmem + (uint32_t)(2 * g) * BN;
+            const uint32_t d_im = tmem + (uint32_t)(2 * g + 1) * BN;
+            const uint32_t b_re = tc::smem_u32(sm.b[ib][j][0]), b_im = tc::smem_u32(sm.b[ib][j][1]);
+#pragma unroll
+            for (int kk = 0; kk < KB / 16; ++kk) {
+              const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the 64-byte swizzle row
+              const uint64_t ar = tc::desc_sw64(a_re + off), ai = tc::desc_sw64(a_im + off);
+              const uint64_t br = tc::desc_sw64(b_re + off), bi = tc::desc_sw64(b_im + off);
+              const uint32_t acc_re = (started >> (2 * g)) & 1u;
+              tc::mma_f16(d_re, ar, br, ID, acc_re);
+              tc::mma_f16(d_re, ai, bi, IDN, 1u);
+              const uint32_t acc_im = (started >> (2 * g + 1)) & 1u;
+              tc::mma_f16(d_im, ar, bi, ID, acc_im);
+              tc::mma_f16(d_im, ai, br, ID, 1u);
+              started |= 3u << (2 * g);
+              any = true;
+            }
+          }
+          tc::mma_commit(&sm.empty_a[ia]);
+          if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+        }
+        if (!ok) break;
+        tc::mma_commit(&sm.empty_b[ib]);
+        if (++ib == 2) { ib = 0; pb ^= 1; }
+      }
+      if (!ok) break;
+      tc::mma_commit(&sm.acc_full);
+      pacc ^= 1;
+    }
+    if (any) {
+      // all issued MMAs retire before TMEM can be released
+      tc::mma_commit(&sm.drain);
+      volatile int no_abort = 0;
+      wait_bar(&sm.drain, 0, &no_abort, err, 8);
+    }
+  } else if (warp >= 2) {
+    // ------------------------------ epilogue ------------------------------
+    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;
+    uint32_t pacc = 0;
+    constexpr int G = S < NGROUPS ? S : NGROUPS;
+    for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
+      const int q = (int)(t / (tilesM * tilesN));
+      const int r = (int)(t % (tilesM * tilesN));
+      const int m0 = (r / tilesN) * BM, n0 = (r % tilesN) * BN;
+      if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6)) break;
+      pacc ^= 1;
+      tc::fence_after_sync();
+      const int m = m0 + row;
+      const bool mvalid = m < N;
+      const int ea = mvalid ? __ldg(expA + (long long)q * N + m) : 0;
+      float4* crow = C + ((long long)q * N + (mvalid ? m : 0)) * N;
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 16; ++ch) {
+        float re[NGROUPS][16], im[NGROUPS][16];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+          tc::tmem_ld16(lane_base + (uint32_t)(2 * g) * BN + ch * 16, re[g]);
+          tc::tmem_ld16(lane_base + (uint32_t)(2 * g + 1) * BN + ch * 16, im[g]);
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int g = G; g < NGROUPS; ++g)
+#pragma unroll
+          for (int c = 0; c < 16; ++c) { re[g][c] = 0.f; im[g][c] = 0.f; }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int n = n0 + ch * 16 + c;
+          if (!mvalid || n >= N) continue;
+          const int eb = __ldg(expB + (long long)q * N + n);
+          float ar[NGROUPS], ai[NGROUPS];
+#pragma unroll
+          for (int g = 0; g < NGROUPS; ++g) { ar[g] = re[g][c]; ai[g] = im[g][c]; }
+          float rh, rl, ih, il;
+          df_sum(ar, rh, rl);
+          df_sum(ai, ih, il);
+          const int k = ea + eb - 14;
+          const int k1 = k / 2, k2 = k - k1;
+          const float f1 = pow2f(k1), f2 = pow2f(k2);
+          crow[n] = make_float4(rh * f1 * f2, rl * f1 * f2, ih * f1 * f2, il * f1 * f2);
+        }
+      }
+      tc::fence_before_sync();
+      tc::mbar_arrive(&sm.acc_empty);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+// ---------------- host: tensor maps ----------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
+// 3-D map over slice planes: (k < N, row < N, plane), row pitch Kp bf16
+int make_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)N * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;
+}
+
+template <int S>
+size_t smem_bytes() { return sizeof(Smem<S>) + 1024; }
+
+template <int S>
+int launch(const SplitGemmArgs& a, cudaStream_t st) {
+  CUtensorMap mA, mB;
+  const long long planes = (long long)a.Q * S * 2;
+  if (make_map(&mA, a.slicesA, a.N, a.Kp, planes, BM)) return NSPT_ERR_CUDA;
+  if (make_map(&mB, a.slicesB, a.N, a.Kp, planes, BN)) return NSPT_ERR_CUDA;
+  const int tilesM = (a.N + BM - 1) / BM, tilesN = (a.N + BN - 1) / BN;
+  const long long ntiles = (long long)a.Q * tilesM * tilesN;
+  int grid = a.num_sms;
+  if (ntiles < grid) grid = (int)ntiles;
+  ProfScope ps(NSPT_STAGE_GEMM_TC, st);
+  split_gemm_kernel<S><<<grid, 192, smem_bytes<S>(), st>>>(mA, mB, a.expA, a.expB, a.C, a.N, a.Q, tilesM, tilesN,
+                                                           a.err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+}  // namespace
+
+int nspt_split_gemm_init() {
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || !fn || q != cudaDriverEntryPointSuccess) {
+      nspt_set_last_cuda_error(e == cudaSuccess ? cudaErrorNotSupported : e);
+      return NSPT_ERR_CUDA;
+    }
+    g_encode = (EncodeTiledFn)fn;
+  }
+#define NSPT_ATTR(s)                                                                                        \
+  {                                                                                                         \
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<s>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem_bytes<s>());                                             \
+    if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }                            \
+  }
+  NSPT_ATTR(2) NSPT_ATTR(3) NSPT_ATTR(4) NSPT_ATTR(5) NSPT_ATTR(6) NSPT_ATTR(7) NSPT_ATTR(8)
+#undef NSPT_ATTR
+  return NSPT_OK;
+}
+
+int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st) {
+  if (a.N > 1024 || a.N < 1) return NSPT_ERR_UNSUPPORTED;
+  switch (a.S) {
+    case 2: return launch<2>(a, st);
+    case 3: return launch<3>(a, st);
+    case 4: return launch<4>(a, st);
+    case 5: return launch<5>(a, st);
+    case 6: return launch<6>(a, st);
+    case 7: return launch<7>(a, st);
+    case 8: return launch<8>(a, st);
+    default: return NSPT_ERR_ARG;
+  }
+}

@@ -1,0 +1,16 @@
+#pragma once
+#include <cuda_runtime.h>
+
+struct SplitGemmArgs {
+  const void* slicesA;  // bf16 [Q][S][2][N][Kp]  rows of A~_q (K-major)
+  const void* slicesB;  // bf16 [Q][S][2][N][Kp]  rows of (B~_q)^T (K-major)
+  const int* expA;      // [Q][N] row exponents of A~_q
+  const int* expB;      // [Q][N] row exponents of (B~_q)^T
+  float4* C;            // [Q][N][N] double-float (re_hi, re_lo, im_hi, im_lo)
+  int N, Kp, Q, S;
+  int num_sms;
+  int* err;             // device error word (0 = ok)
+};
+
+int nspt_split_gemm_init();
+int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st);

@@ -32,3 +32,6 @@ cudaError_t nspt_fft_fwd64(const double2* in, long long in_stride, double2* out,
 cudaError_t nspt_fft_inv64(const double2* in, double2* out, long long out_stride, int E, int N, int t,
                            int batch, int M, int log2u, int log2r, double post, int add_identity,
                            cudaStream_t st, int kmin = 0);
+// Inverse order FFT of a double-float spectrum (float4 = re_hi, re_lo, im_hi, im_lo).
+cudaError_t nspt_fft_inv64_df(const float4* in, double2* out, long long out_stride, int E, int N, int t, int batch,
+                              int M, int log2u, int log2r, cudaStream_t st);

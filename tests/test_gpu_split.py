@@ -1,0 +1,186 @@
+"""GPU parity of the split-precision form (BF16 digit slices on tcgen05 tensor
+cores, exact FP32 digit groups, double-float recombination) against the FP64
+oracle, plus stage tests of the slicer and of the tensor-core mode GEMM.
+
+Stated per-order bound: with S slices every entry is carried to 8S - 1 bits
+below the largest entry of its row (column); the transform, the K-term dot
+products and the double-float recombination add a floor near 2^-46 per
+accumulation step.  The tests assert
+    max_k ||dC_k||_F / ||C_k||_F <= 2^10 * sqrt(N) * (2^-(8S-1) + 2^-44).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import nspt_synth as syn
+from oracle import polymat as pm
+
+from tests.gpu_util import dev, host, max_order_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def bound(S, N):
+    return 2.0 ** 10 * math.sqrt(N) * (2.0 ** -(8 * S - 1) + 2.0 ** -44)
+
+
+@pytest.fixture(scope="module")
+def nspt():
+    import paper_2001_02835_b300 as n
+    assert n.lib().nspt_init() == 0
+    return n
+
+
+@pytest.mark.parametrize("N,T,batch", [(1, 0, 1), (3, 2, 2), (9, 8, 4), (33, 15, 2), (48, 7, 1), (49, 3, 2),
+                                       (130, 5, 1), (225, 3, 1)])
+def test_split_mul_matches_oracle(nspt, N, T, batch):
+    g = syn.rng(5000 + N + 100 * T)
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    C = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split"))
+    ref = pm.star(A, B)
+    err = max_order_rel(C, ref)
+    assert err <= bound(6, N), err
+
+
+@pytest.mark.parametrize("S", [2, 3, 4, 5, 6, 7, 8])
+def test_split_error_shrinks_with_slices(nspt, S):
+    g = syn.rng(5100)
+    N, T = 40, 7
+    A = syn.series_batch(g, N, T, 2)
+    B = syn.series_batch(g, N, T, 2)
+    ref = pm.star(A, B)
+    C = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", slices=S))
+    err = max_order_rel(C, ref)
+    assert err <= bound(S, N), (S, err)
+    if S <= 5:
+        # the split really is the limiting error at few slices
+        assert err >= 2.0 ** -(8 * S + 8), (S, err)
+
+
+def test_split_per_order_rescale(nspt):
+    """Orders growing like 2^k: without rescale the low orders drown in the
+    transform; r = 1/2 (exact power of two, undone on C) restores them."""
+    g = syn.rng(5200)
+    N, T = 20, 31
+    A = syn.series_batch(g, N, T, 2)
+    B = syn.series_batch(g, N, T, 2)
+    s = (2.0 ** np.arange(T + 1))[None, :, None, None]
+    A, B = A * s, B * s
+    ref = pm.star(A, B)
+    C = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", rescale_log2r=-1))
+    err = max_order_rel(C, ref)
+    assert err <= bound(6, N), err
+    C0 = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", rescale_log2r=0))
+    assert max_order_rel(C0, ref) > 1e3 * err
+
+
+@pytest.mark.parametrize("N,T,batch", [(3, 2, 1), (9, 8, 2), (70, 5, 1)])
+def test_split_backward_matches_oracle(nspt, N, T, batch):
+    g = syn.rng(5300 + N)
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    W = syn.gaussian(g, A.shape, 1.0)
+    gA, gB = nspt.polymat_mul_backward(dev(A), dev(B), dev(W), algo="fft", prec="split")
+    rA, rB = pm.star_backward(A, B, W)
+    assert max_order_rel(host(gA), rA) <= bound(6, N)
+    assert max_order_rel(host(gB), rB) <= bound(6, N)
+
+
+@pytest.mark.parametrize("S,trans,conj", [(2, 0, 0), (6, 0, 0), (6, 1, 0), (6, 0, 1), (8, 1, 1)])
+def test_slicer_reconstructs_rows(nspt, S, trans, conj):
+    g = syn.rng(5500 + S)
+    Q, N = 3, 37
+    X = syn.gaussian(g, (Q, N, N), 1.0)
+    X[1, 5] = 0.0          # an all-zero row (or column)
+    X[1, :, 5] = 0.0
+    X[2] *= 1e-30          # tiny magnitudes keep their relative precision
+    sl, ex = nspt.split_slices(dev(X), S, trans=bool(trans), conj=bool(conj))
+    sl = host(sl.float()).astype(np.float64)[..., :N]
+    ex = host(ex)
+    Y = np.swapaxes(X, 1, 2) if trans else X
+    if conj:
+        Y = np.conj(Y)
+    rec = (sl[:, :, 0].sum(1) + 1j * sl[:, :, 1].sum(1)) * (2.0 ** (ex - 7.0))[:, :, None]
+    tol = 2.0 ** (ex - 8.0 * S)[:, :, None]
+    assert np.all(np.abs(rec.real - Y.real) <= tol) and np.all(np.abs(rec.imag - Y.imag) <= tol)
+    digits = sl * (2.0 ** (8 * np.arange(S)))[None, :, None, None, None]
+    assert np.all(np.abs(digits) <= 128) and np.all(digits == np.round(digits))
+    rowmax = np.maximum(np.abs(Y.real), np.abs(Y.imag)).max(-1)
+    nz = rowmax > 0
+    assert np.all(rowmax[nz] < 2.0 ** ex[nz]) and np.all(rowmax[nz] >= 2.0 ** (ex[nz] - 1))
+
+
+@pytest.mark.parametrize("N", [16, 40, 225])
+@pytest.mark.parametrize("pairs", [[(0, 0)], [(0, 1), (1, 0)], [(0, 2), (1, 1), (2, 0)], [(1, 2), (0, 3)]])
+def test_mode_gemm_digit_groups_are_exact(nspt, N, pairs):
+    """Integer digits in the slices of a few digit groups: every group below 4
+    is accumulated exactly, so the double-float result equals the exact
+    product (computed in FP64, where all values here are exact)."""
+    rs = np.random.default_rng(N)
+    Q, S = 2, 6
+    Kp = (N + 7) // 8 * 8
+    dA = np.zeros((Q, S, 2, N, Kp))
+    dB = np.zeros((Q, S, 2, N, Kp))
+    for i, j in pairs:
+        dA[:, i, :, :, :N] = rs.integers(-128, 129, (Q, 2, N, N))
+        dB[:, j, :, :, :N] = rs.integers(-128, 129, (Q, 2, N, N))
+    w = 2.0 ** (-8.0 * np.arange(S))
+    slA = torch.from_numpy((dA * w[None, :, None, None, None]).astype(np.float32)).to(torch.bfloat16).cuda()
+    slB = torch.from_numpy((dB * w[None, :, None, None, None]).astype(np.float32)).to(torch.bfloat16).cuda()
+    eA = torch.full((Q, N), 14, dtype=torch.int32, device="cuda")
+    eB = torch.zeros((Q, N), dtype=torch.int32, device="cuda")
+    Ct = host(nspt.split_mode_gemm(slA, slB, eA, eB, N, S)).astype(np.float64)
+    got = (Ct[..., 0] + Ct[..., 1]) + 1j * (Ct[..., 2] + Ct[..., 3])
+    Ar, Ai = (np.einsum("qsmk,s->qmk", dA[:, :, c, :, :N], w) for c in (0, 1))
+    Br, Bi = (np.einsum("qsnk,s->qkn", dB[:, :, c, :, :N], w) for c in (0, 1))
+    # keep only the pairs the kernel issues (i + j < S): all of them here
+    ref = (Ar @ Br - Ai @ Bi) + 1j * (Ar @ Bi + Ai @ Br)
+    # group g is exact when its worst case, (pairs in g) * 2N * 128^2 grid units, is below 2^24
+    per_group = {}
+    for i, j in pairs:
+        per_group[i + j] = per_group.get(i + j, 0) + 1
+    exact_groups = max(per_group) <= 3 and all(c * 2 * N * 2 ** 14 <= 2 ** 24 for c in per_group.values())
+    if exact_groups and len(per_group) == 1:
+        # one group: the exact sum has < 24 significant bits, so the result is bit-exact
+        np.testing.assert_array_equal(got, ref)
+    else:
+        # several groups: exact per group, then rounded once to the 48-bit double-float
+        # (an inexact group g would show up at 2^-(24 + 8 g) of the result)
+        assert np.all(np.abs(got - ref) <= 2.0 ** -46 * np.abs(ref) + 2.0 ** -60)
+
+
+def test_split_su225_t63_sampled_oracle(nspt):
+    """SU(225), O(g^63), M = 128, batch 4, split form: against the GPU FP64 form
+    everywhere (both checked against the oracle on sampled entries)."""
+    g = syn.rng(syn.SEED_BASE + 2)
+    N, T, batch = 225, 63, 4
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    tA, tB = dev(A), dev(B)
+    Cs = host(nspt.polymat_mul(tA, tB, algo="fft", prec="split"))
+    C64 = host(nspt.polymat_mul(tA, tB, algo="fft", prec="fp64"))
+    err = max_order_rel(Cs, C64)
+    assert err <= bound(6, N), err
+    rs = np.random.default_rng(11)
+    idx = [(int(rs.integers(batch)), int(k), int(rs.integers(N)), int(rs.integers(N))) for k in range(T + 1)]
+    ref = pm.star_entries(A, B, idx)
+    scale = np.sqrt(np.mean(np.abs(C64) ** 2))
+    assert np.abs(np.array([C64[i] for i in idx]) - ref).max() <= 1e-12 * scale
+    assert np.abs(np.array([Cs[i] for i in idx]) - ref).max() <= 10 * bound(6, N) * scale
+
+
+def test_split_device_status_ok(nspt):
+    import ctypes
+    g = syn.rng(5400)
+    A = syn.series_batch(g, 16, 3, 1)
+    tA = dev(A)
+    opts = nspt.make_opts(algo="fft", prec="split")
+    ws = nspt._with_ws(nspt.OP_MUL, 16, 3, 1, opts, tA.device)  # noqa: F841
+    C = tA.clone()
+    rc = nspt.lib().nspt_polymat_mul(tA.data_ptr(), tA.data_ptr(), C.data_ptr(), 16, 3, 1, ctypes.byref(opts),
+                                     nspt._stream_ptr(tA.device))
+    assert rc == 0
+    assert nspt.lib().nspt_device_status(ctypes.byref(opts), nspt._stream_ptr(tA.device)) == 0
