@@ -138,10 +138,15 @@ def test_mode_gemm_digit_groups_are_exact(nspt, N, pairs):
     Br, Bi = (np.einsum("qsnk,s->qkn", dB[:, :, c, :, :N], w) for c in (0, 1))
     # keep only the pairs the kernel issues (i + j < S): all of them here
     ref = (Ar @ Br - Ai @ Bi) + 1j * (Ar @ Bi + Ai @ Br)
+    # the kernel issues every pair (i, j) of non-zero A and B slices with i + j < S;
     # group g is exact when its worst case, (pairs in g) * 2N * 128^2 grid units, is below 2^24
+    a_sl = {i for i, _ in pairs}
+    b_sl = {j for _, j in pairs}
     per_group = {}
-    for i, j in pairs:
-        per_group[i + j] = per_group.get(i + j, 0) + 1
+    for i in a_sl:
+        for j in b_sl:
+            if i + j < S:
+                per_group[i + j] = per_group.get(i + j, 0) + 1
     exact_groups = max(per_group) <= 3 and all(c * 2 * N * 2 ** 14 <= 2 ** 24 for c in per_group.values())
     if exact_groups and len(per_group) == 1:
         # one group: the exact sum has < 24 significant bits, so the result is bit-exact
