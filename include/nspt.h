@@ -189,6 +189,25 @@ NSPT_API int nspt_split_slices(const void* X, void* slices, int* exps, int N, in
 NSPT_API int nspt_split_mode_gemm(const void* slA, const void* slB, const int* expA, const int* expB, void* Ct, int N,
                                   int Q, int S, int* err, void* stream);
 
+/*
+ * Allocation-free FFT-CONV product (no counterpart in the paper): the same
+ * result as nspt_polymat_mul with NSPT_ALGO_FFT, NSPT_PREC_FP64 and the default
+ * M, for callers that cannot allocate device memory (code in host callbacks or
+ * allocator hooks, processes whose device memory another framework owns, or
+ * plug-in hosts that pass only input and output buffers).  Its scratch -- the
+ * three spectra, 3 * batch * M * N^2 * 16 bytes -- lives in one fixed 32 MiB
+ * device array inside the library, which every GPU that loads the library
+ * holds until the process exits; larger problems return NSPT_ERR_WORKSPACE.
+ *   A, B : [batch][T+1][N][N] complex128 device inputs;  C : output, no overlap.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array, which keeps the last call's contents (each call
+ * overwrites every entry it reads): calls that can overlap on the GPU -- on
+ * different streams without ordering -- race and must not be issued.
+ */
+NSPT_API int nspt_polymat_mul_fft_noalloc(const void* A, const void* B, void* C, int N, int T, int batch,
+                                          void* stream);
+
 /* Static description of a status code. */
 NSPT_API const char* nspt_status_string(int status);
 /* Name of the last CUDA error seen by this thread ("no error" if none). */

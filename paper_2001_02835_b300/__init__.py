@@ -73,6 +73,7 @@ _SIGS = {
     "nspt_device_status": (_i, [ctypes.POINTER(Opts), _vp]),
     "nspt_split_slices": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
     "nspt_split_mode_gemm": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp]),
+    "nspt_polymat_mul_fft_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
 }
 
 
