@@ -1,0 +1,120 @@
+// Double-float ("double-word") arithmetic on FP32 pairs for the transforms of
+// the split form.  A value is hi + lo with |lo| <= ulp(hi)/2 (about 48
+// significant bits).  Sums use Knuth's TwoSum and Dekker's FastTwoSum,
+// products the FMA residual a*b - fl(a*b); see Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic" (ACM TOMS 2017).  Conversions to and from FP64 work on the bit
+// patterns with integer operations, because the FP64 pipe of B300 runs at
+// about 1/58 of the FP32 rate.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+struct dfl {
+  float h, l;
+};
+struct cdf {
+  dfl re, im;
+};
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ dfl df_fast(float s, float e) {
+  const float h = s + e;
+  return dfl{h, e - (h - s)};
+}
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  float s, e;
+  df_two_sum(a.h, b.h, s, e);
+  e += a.l + b.l;
+  return df_fast(s, e);
+}
+__device__ __forceinline__ dfl df_neg(dfl a) { return dfl{-a.h, -a.l}; }
+__device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ dfl df_scale(dfl a, float p2) { return dfl{a.h * p2, a.l * p2}; }
+
+__device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+
+// a * w with w = (c, s) given as double-float pairs (a twiddle factor)
+__device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
+  // re = a.re c - a.im s
+  float p1 = a.re.h * c.h, e1 = fmaf(a.re.h, c.h, -p1);
+  float p2 = a.im.h * s.h, e2 = fmaf(a.im.h, s.h, -p2);
+  float sr, e3;
+  df_two_sum(p1, -p2, sr, e3);
+  float lo = (e1 - e2) + e3;
+  lo = fmaf(a.re.h, c.l, lo);
+  lo = fmaf(a.re.l, c.h, lo);
+  lo = fmaf(-a.im.h, s.l, lo);
+  lo = fmaf(-a.im.l, s.h, lo);
+  const dfl re = df_fast(sr, lo);
+  // im = a.re s + a.im c
+  float q1 = a.re.h * s.h, f1 = fmaf(a.re.h, s.h, -q1);
+  float q2 = a.im.h * c.h, f2 = fmaf(a.im.h, c.h, -q2);
+  float si, f3;
+  df_two_sum(q1, q2, si, f3);
+  float lo2 = (f1 + f2) + f3;
+  lo2 = fmaf(a.re.h, s.l, lo2);
+  lo2 = fmaf(a.re.l, s.h, lo2);
+  lo2 = fmaf(a.im.h, c.l, lo2);
+  lo2 = fmaf(a.im.l, c.h, lo2);
+  return cdf{re, df_fast(si, lo2)};
+}
+
+// 2^k as a float for -252 <= k <= 254 (two factors keep it exact)
+__device__ __forceinline__ void pow2_pair(int k, float& f1, float& f2) {
+  const int k1 = k / 2, k2 = k - k1;
+  f1 = __int_as_float((max(-126, min(127, k1)) + 127) << 23);
+  f2 = __int_as_float((max(-126, min(127, k2)) + 127) << 23);
+}
+
+// FP64 -> double-float: hi keeps the top 24 significant bits, lo the next 29
+// bits rounded to 24.  Zero and FP64 denormals map to 0.
+__device__ __forceinline__ dfl df_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return dfl{0.f, 0.f};
+  const int fe = e - 1023 + 127;
+  if (fe < 1 || fe > 254) {  // outside the FP32 exponent range: saturate through the slow path
+    const float h = __double2float_rz(x);
+    return dfl{h, 0.f};
+  }
+  const unsigned sign = (unsigned)(b >> 63) << 31;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  const float h = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)(m >> 29));
+  float f1, f2;
+  pow2_pair(e - 1075, f1, f2);
+  float l = (float)(unsigned)(m & 0x1FFFFFFFull) * f1 * f2;
+  if (sign) l = -l;
+  return dfl{h, l};
+}
+
+// float -> FP64 by bit assembly (normal floats; zero and denormals exactly)
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xFF;
+  if (ef == 0 || ef == 255) return (double)f;
+  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                                  ((unsigned long long)(ef - 127 + 1023) << 52) |
+                                  ((unsigned long long)(u & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return f2d(a.h) + f2d(a.l); }
+
+// round(x * 2^sh) for x = hi + lo as a signed 64-bit integer (|result| < 2^63)
+__device__ __forceinline__ long long f_scaled_int(float f, int sh_base) {
+  const unsigned u = __float_as_uint(f);
+  const int ef = (int)((u >> 23) & 0xFF);
+  if (ef == 0) return 0;
+  const long long m = (long long)((u & 0x7FFFFF) | 0x800000);
+  const int sh = ef - 150 + sh_base;
+  long long v;
+  if (sh >= 0) v = m << sh;
+  else if (sh > -63) v = (m + (1LL << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (u >> 31) ? -v : v;
+}

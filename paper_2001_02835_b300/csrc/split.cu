@@ -19,6 +19,7 @@
 #include "split.cuh"
 #include "split_gemm.cuh"
 #include "zgemm64.cuh"
+#include "dfloat.cuh"
 
 namespace {
 
@@ -47,21 +48,65 @@ __device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
   s[0] = sign * (float)(int)X;
 }
 
-__device__ __forceinline__ int bexp_of(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+// digits of a double-float value x = hi + lo (|x| < 2^e), same representation as above
+template <int S>
+__device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
+  constexpr int W = 8 * S - 1;
+  constexpr int W1 = W < 62 ? W : 62;  // signed 64-bit headroom; the rest is an exact shift
+  const long long Xs = f_scaled_int(x.h, W1 - e) + f_scaled_int(x.l, W1 - e);
+  const float sign = Xs < 0 ? -1.f : 1.f;
+  unsigned long long X = (unsigned long long)(Xs < 0 ? -Xs : Xs) << (W - W1);
+#pragma unroll
+  for (int i = S - 1; i >= 1; --i) {
+    int d = (int)(X & 255ull);
+    X >>= 8;
+    if (d > 128) { d -= 256; X += 1; }
+    s[i] = sign * (float)d * __int_as_float((127 - 8 * i) << 23);
+  }
+  s[0] = sign * (float)(int)X;
+}
+
+// smallest e with |x| < 2^e for every part, from the exponent field
+__device__ __forceinline__ int exp_bound(double2 v) {
+  const int a = (int)((__double_as_longlong(v.x) >> 52) & 0x7FF), b = (int)((__double_as_longlong(v.y) >> 52) & 0x7FF);
+  const int m = max(a, b);
+  return m == 0 ? -100000 : m - 1022;
+}
+__device__ __forceinline__ int exp_bound(float4 v) {
+  // |hi + lo| < 2^(exponent(hi) + 1) since |lo| <= ulp(hi)/2
+  const int a = (int)((__float_as_uint(v.x) >> 23) & 0xFF), b = (int)((__float_as_uint(v.z) >> 23) & 0xFF);
+  const int m = max(a, b);
+  return m == 0 ? -100000 : m - 126;
+}
+__device__ __forceinline__ double2 conj_of(double2 v) { return make_double2(v.x, -v.y); }
+__device__ __forceinline__ float4 conj_of(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
+__device__ __forceinline__ double2 zero_of(double2) { return make_double2(0.0, 0.0); }
+__device__ __forceinline__ float4 zero_of(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <int S>
+__device__ __forceinline__ void digits_re_im(double2 v, int e, float (&re)[S], float (&im)[S]) {
+  to_digits<S>(v.x, e, re);
+  to_digits<S>(v.y, e, im);
+}
+template <int S>
+__device__ __forceinline__ void digits_re_im(float4 v, int e, float (&re)[S], float (&im)[S]) {
+  to_digits<S>(dfl{v.x, v.y}, e, re);
+  to_digits<S>(dfl{v.z, v.w}, e, im);
+}
 
 // grid (ceil(N/RB), Q); block 256.  Output row r of plane q is row r of the
 // source matrix (trans = 0) or its column r (trans = 1), conjugated if conj;
 // the source of plane q = b*M + p is mode p (rev = 0) or (M - p) mod M (rev = 1)
 // of batch element b.
-template <int S>
+template <int S, typename InT>
 __global__ void __launch_bounds__(256)
-slice_kernel(const double2* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
+slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
              int RB, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
-  extern __shared__ double2 tile[];
+  extern __shared__ __align__(16) unsigned char tile_raw[];
+  InT* tile = reinterpret_cast<InT*>(tile_raw);
   const int q = blockIdx.y;
   const int b = q / M, p = q % M;
   const int sp = rev ? (M - p) % M : p;
-  const double2* Xm = X + ((long long)b * bstride + sp) * N * N;
+  const InT* Xm = X + ((long long)b * bstride + sp) * N * N;
   const int r0 = blockIdx.x * RB;
   const int nr = min(RB, N - r0);
   const int ld = RB + 1;
@@ -80,30 +125,24 @@ slice_kernel(const double2* __restrict__ X, long long bstride, int M, int rev, i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long plane = (long long)N * Kp;
   for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
-    auto elem = [&](int k) -> double2 {
-      double2 v = trans ? tile[k * ld + rr] : tile[rr * N + k];
-      if (conj) v.y = -v.y;
-      return v;
+    auto elem = [&](int k) -> InT {
+      const InT v = trans ? tile[k * ld + rr] : tile[rr * N + k];
+      return conj ? conj_of(v) : v;
     };
-    int mx = 0;
-    for (int k = lane; k < N; k += 32) {
-      const double2 v = elem(k);
-      mx = max(mx, max(bexp_of(v.x), bexp_of(v.y)));
-    }
+    int mx = -100000;
+    for (int k = lane; k < N; k += 32) mx = max(mx, exp_bound(elem(k)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    const int e = (mx == 0) ? -1000 : mx - 1022;  // |x| < 2^e for every part of the row
+    const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
     const int r = r0 + rr;
     if (lane == 0) exps[(long long)q * N + r] = e;
     __nv_bfloat16* orow = out + (long long)q * S * 2 * plane + (long long)r * Kp;
     for (int k = 2 * lane; k < N; k += 64) {
-      const double2 v0 = elem(k);
-      const double2 v1 = (k + 1 < N) ? elem(k + 1) : make_double2(0.0, 0.0);
+      const InT v0 = elem(k);
+      const InT v1 = (k + 1 < N) ? elem(k + 1) : zero_of(v0);
       float re0[S], im0[S], re1[S], im1[S];
-      to_digits<S>(v0.x, e, re0);
-      to_digits<S>(v0.y, e, im0);
-      to_digits<S>(v1.x, e, re1);
-      to_digits<S>(v1.y, e, im1);
+      digits_re_im<S>(v0, e, re0, im0);
+      digits_re_im<S>(v1, e, re1, im1);
 #pragma unroll
       for (int i = 0; i < S; ++i) {
         *reinterpret_cast<__nv_bfloat162*>(orow + (2LL * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
@@ -118,16 +157,16 @@ int row_block(int N) {
   return std::max(1, std::min(16, rb));
 }
 
-template <int S>
-int launch_slice(const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q,
+template <int S, typename InT>
+int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q,
                  __nv_bfloat16* out, int* exps, cudaStream_t st) {
   const int RB = row_block(N);
-  const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(double2);
-  cudaError_t e = cudaFuncSetAttribute(slice_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
+  cudaError_t e = cudaFuncSetAttribute(slice_kernel<S, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_kernel<S><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, out, exps);
+  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, out, exps);
   e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
@@ -136,7 +175,7 @@ int launch_slice(const double2* X, long long bstride, int M, int rev, int trans,
 int kpad(int N) { return (N + 7) & ~7; }
 
 struct SplitWs {
-  double2 *At, *Bt;
+  float4 *At, *Bt;
   __nv_bfloat16 *slA, *slB;
   int *expA, *expB, *err;
   float4* Ct;
@@ -147,13 +186,13 @@ SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total) {
   SplitWs s;
   const long long E = (long long)N * N, Q = (long long)batch * M;
   s.err = w.take<int>(64);
-  s.At = w.take<double2>((size_t)Q * E);
-  s.Bt = w.take<double2>((size_t)Q * E);
+  s.At = w.take<float4>((size_t)Q * E);
+  s.Bt = w.take<float4>((size_t)Q * E);
   s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
   s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
   s.expA = w.take<int>((size_t)Q * N);
   s.expB = w.take<int>((size_t)Q * N);
-  s.Ct = reinterpret_cast<float4*>(s.At);  // A~ is dead once sliced
+  s.Ct = s.At;  // A~ is dead once sliced
   if (total) *total = w.off;
   return s;
 }
@@ -170,15 +209,26 @@ int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
 
 }  // namespace
 
-int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                     void* out, int* exps, cudaStream_t st) {
+template <typename InT>
+int slice_any(int S, const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q, void* out,
+              int* exps, cudaStream_t st) {
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   switch (S) {
-#define NSPT_CASE(s) case s: return launch_slice<s>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, o, exps, st);
+#define NSPT_CASE(s) case s: return launch_slice<s, InT>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, o, exps, st);
     NSPT_CASE(2) NSPT_CASE(3) NSPT_CASE(4) NSPT_CASE(5) NSPT_CASE(6) NSPT_CASE(7) NSPT_CASE(8)
 #undef NSPT_CASE
     default: return NSPT_ERR_ARG;
   }
+}
+
+int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
+                     void* out, int* exps, cudaStream_t st) {
+  return slice_any<double2>(S, X, bstride, M, rev, trans, conj, N, Q, out, exps, st);
+}
+
+int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
+                        void* out, int* exps, cudaStream_t st) {
+  return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, out, exps, st);
 }
 
 int nspt_split_init() {
@@ -206,15 +256,15 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
   SplitWs w = carve(ws, N, batch, M, S, nullptr);
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
-  TRYC(nspt_fft_fwd64(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
-  TRYC(nspt_fft_fwd64(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
   // a2: slices of A~_q (rows) and of B~_q^T (columns of B~_q)
-  TRYS(nspt_split_slice(S, w.At, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
-  TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+  TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
+  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
   // a3: mode GEMMs on the tensor cores
   TRYS(gemm(w, N, Q, S, st));
   // a4: inverse transform, truncation, unscale 2^(-k log2r)
-  TRYC(nspt_fft_inv64_df(w.Ct, C, T + 1, E, N, T, batch, M, 0, log2r, st));
+  TRYC(nspt_fft_inv_df(w.Ct, C, T + 1, E, T, batch, M, 0, log2r, st));
   return NSPT_OK;
 }
 
@@ -223,25 +273,25 @@ int nspt_split_bwd(int N, int T, int batch, int M, int S, int log2r, const doubl
   const int E = N * N, Q = batch * M;
   size_t off = 0;
   SplitWs w = carve(ws, N, batch, M, S, &off);
-  double2* Gt = reinterpret_cast<double2*>((char*)ws + off);
+  float4* Gt = reinterpret_cast<float4*>((char*)ws + off);
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // with A' = r^k A, B' = r^k B, G' = r^-k G the correlations come out scaled by r^-j
-  TRYC(nspt_fft_fwd64(G, T + 1, Gt, E, T, batch, M, 0, -log2r, st));
+  TRYC(nspt_fft_fwd_df(G, T + 1, Gt, E, T, batch, M, 0, -log2r, st));
   if (gA) {
     // gA~_p = G~_p (B~_p)^H
-    TRYC(nspt_fft_fwd64(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-    TRYS(nspt_split_slice(S, Gt, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
-    TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 0, 1, N, Q, w.slB, w.expB, st));
+    TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 1, N, Q, w.slB, w.expB, st));
     TRYS(gemm(w, N, Q, S, st));
-    TRYC(nspt_fft_inv64_df(w.Ct, gA, T + 1, E, N, T, batch, M, 0, -log2r, st));
+    TRYC(nspt_fft_inv_df(w.Ct, gA, T + 1, E, T, batch, M, 0, -log2r, st));
   }
   if (gB) {
     // gB~_p = (A~_p)^H G~_p
-    TRYC(nspt_fft_fwd64(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-    TRYS(nspt_split_slice(S, w.Bt, M, M, 0, 1, 1, N, Q, w.slA, w.expA, st));
-    TRYS(nspt_split_slice(S, Gt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+    TRYC(nspt_fft_fwd_df(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 1, N, Q, w.slA, w.expA, st));
+    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
     TRYS(gemm(w, N, Q, S, st));
-    TRYC(nspt_fft_inv64_df(w.Ct, gB, T + 1, E, N, T, batch, M, 0, -log2r, st));
+    TRYC(nspt_fft_inv_df(w.Ct, gB, T + 1, E, T, batch, M, 0, -log2r, st));
   }
   return NSPT_OK;
 }
