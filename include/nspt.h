@@ -171,21 +171,23 @@ NSPT_API int nspt_device_status(const nspt_opts* opts, void* stream);
  * nspt_split_slices (FFT-CONV Step 3 operand preparation): cuts each of the Q
  * N x N complex128 matrices X[q] into S BF16 digit planes.  Output row r is
  * row r of X[q] (trans = 0) or column r (trans = 1), conjugated if conj.
- *   slices : bf16 [Q][S][2][N][Kp], Kp = N rounded up to a multiple of 8;
- *            plane (q, i, c) holds digit i of the real (c = 0) / imaginary
- *            (c = 1) parts, stored as d * 2^(-8 i) with |d| <= 128;
+ *   slices : bf16 [Q][S][P][N][Kp], Kp = N rounded up to a multiple of 8,
+ *            P = 2 for a left operand (right = 0) and P = 3 for a right
+ *            operand (right = 1); plane (q, i, c) holds digit i of the real
+ *            (c = 0) / imaginary (c = 1) parts, and for P = 3 plane c = 2 holds
+ *            the negated real part; digits are stored as d * 2^(-8 i), |d| <= 128;
  *   exps   : int [Q][N]; row r satisfies
  *            row[k] = 2^(exps[q][r] - 7) sum_i plane(q, i, ., r, k)
  *            up to 2^(exps[q][r] - 8S).
  *
  * nspt_split_mode_gemm (FFT-CONV Step 3, Sec. 2): Ct_q = A_q B_q for q < Q
- * from the slices of A_q (trans = 0) and of B_q (trans = 1), on the tensor
- * cores.  Ct : [Q][N][N] float4 (re_hi, re_lo, im_hi, im_lo), the double-float
- * result; err : device int, set non-zero if a bounded wait gave up.
- * 2 <= S <= 8, N <= 1024, Q <= 65535 (slicing).
+ * from the slices of A_q (trans = 0, right = 0) and of B_q (trans = 1,
+ * right = 1), on the tensor cores.  Ct : [Q][N][N] float4 (re_hi, re_lo,
+ * im_hi, im_lo), the double-float result; err : device int, set non-zero if a
+ * bounded wait gave up.  2 <= S <= 8, N <= 1024, Q <= 65535 (slicing).
  */
 NSPT_API int nspt_split_slices(const void* X, void* slices, int* exps, int N, int Q, int S, int trans, int conj,
-                               void* stream);
+                               int right, void* stream);
 NSPT_API int nspt_split_mode_gemm(const void* slA, const void* slB, const int* expA, const int* expB, void* Ct, int N,
                                   int Q, int S, int* err, void* stream);
 

@@ -71,7 +71,7 @@ _SIGS = {
     "nspt_stage_name": (ctypes.c_char_p, [_i]),
     "nspt_last_error": (ctypes.c_char_p, []),
     "nspt_device_status": (_i, [ctypes.POINTER(Opts), _vp]),
-    "nspt_split_slices": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp]),
+    "nspt_split_slices": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp]),
     "nspt_split_mode_gemm": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp]),
     "nspt_polymat_mul_fft_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
 }
@@ -264,16 +264,16 @@ def profile_end() -> dict:
     return {lib().nspt_stage_name(i).decode(): (ms[i], int(n[i])) for i in range(NSTAGES) if n[i]}
 
 
-def split_slices(X: torch.Tensor, S: int, trans: bool = False, conj: bool = False):
-    """Stage entry: digit slices (bf16 (Q, S, 2, N, Kp)) and row exponents (int32 (Q, N))
-    of the Q matrices X (Q, N, N) complex128 (see include/nspt.h)."""
+def split_slices(X: torch.Tensor, S: int, trans: bool = False, conj: bool = False, right: bool = False):
+    """Stage entry: digit slices (bf16 (Q, S, P, N, Kp), P = 3 for a right operand, else 2)
+    and row exponents (int32 (Q, N)) of the Q matrices X (Q, N, N) complex128 (see include/nspt.h)."""
     _check_tensor(X, "X")
     Q, N = X.shape[0], X.shape[1]
     Kp = (N + 7) // 8 * 8
-    sl = torch.zeros((Q, S, 2, N, Kp), dtype=torch.bfloat16, device=X.device)
+    sl = torch.zeros((Q, S, 3 if right else 2, N, Kp), dtype=torch.bfloat16, device=X.device)
     ex = torch.empty((Q, N), dtype=torch.int32, device=X.device)
     _check(lib().nspt_split_slices(X.data_ptr(), sl.data_ptr(), ex.data_ptr(), N, Q, S, int(trans), int(conj),
-                                   _stream_ptr(X.device)), "nspt_split_slices")
+                                   int(right), _stream_ptr(X.device)), "nspt_split_slices")
     return sl, ex
 
 

@@ -544,13 +544,13 @@ int nspt_device_status(const nspt_opts* opts, void* stream) {
   return err ? NSPT_ERR_TIMEOUT : NSPT_OK;
 }
 
-int nspt_split_slices(const void* X, void* slices, int* exps, int N, int Q, int S, int trans, int conj,
+int nspt_split_slices(const void* X, void* slices, int* exps, int N, int Q, int S, int trans, int conj, int right,
                       void* stream) {
   if (!X || !slices || !exps || N < 1 || N > 1024 || Q < 1 || Q > 65535 || S < 2 || S > 8) return NSPT_ERR_ARG;
   int rc = nspt_init();
   if (rc) return rc;
-  return nspt_split_slice(S, (const double2*)X, Q, Q, 0, trans ? 1 : 0, conj ? 1 : 0, N, Q, slices, exps,
-                          (cudaStream_t)stream);
+  return nspt_split_slice(S, (const double2*)X, Q, Q, 0, trans ? 1 : 0, conj ? 1 : 0, N, Q, right ? 3 : 2, slices,
+                          exps, (cudaStream_t)stream);
 }
 
 int nspt_split_mode_gemm(const void* slA, const void* slB, const int* expA, const int* expB, void* Ct, int N, int Q,

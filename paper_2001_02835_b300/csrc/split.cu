@@ -25,6 +25,12 @@ namespace {
 
 int g_num_sms = 0;
 
+// exact int -> float for |d| < 2^22 without a conversion instruction
+// (1.5 * 2^23 + d has d in its low mantissa bits)
+__device__ __forceinline__ float small_int_to_float(int d) {
+  return __int_as_float(0x4B400000 + d) - 12582912.0f;
+}
+
 template <int S>
 __device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
   constexpr int W = 8 * S - 1;
@@ -43,9 +49,9 @@ __device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
     int d = (int)(X & 255ull);
     X >>= 8;
     if (d > 128) { d -= 256; X += 1; }
-    s[i] = sign * (float)d * __int_as_float((127 - 8 * i) << 23);
+    s[i] = sign * small_int_to_float(d) * __int_as_float((127 - 8 * i) << 23);
   }
-  s[0] = sign * (float)(int)X;
+  s[0] = sign * small_int_to_float((int)X);
 }
 
 // digits of a double-float value x = hi + lo (|x| < 2^e), same representation as above
@@ -61,9 +67,9 @@ __device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
     int d = (int)(X & 255ull);
     X >>= 8;
     if (d > 128) { d -= 256; X += 1; }
-    s[i] = sign * (float)d * __int_as_float((127 - 8 * i) << 23);
+    s[i] = sign * small_int_to_float(d) * __int_as_float((127 - 8 * i) << 23);
   }
-  s[0] = sign * (float)(int)X;
+  s[0] = sign * small_int_to_float((int)X);
 }
 
 // smallest e with |x| < 2^e for every part, from the exponent field
@@ -95,12 +101,14 @@ __device__ __forceinline__ void digits_re_im(float4 v, int e, float (&re)[S], fl
 
 // grid (ceil(N/RB), Q); block 256.  Output row r of plane q is row r of the
 // source matrix (trans = 0) or its column r (trans = 1), conjugated if conj;
+// P = 2 planes per digit (re, im) for a left operand, P = 3 (re, im, -re) for a
+// right operand of the tensor-core GEMM;
 // the source of plane q = b*M + p is mode p (rev = 0) or (M - p) mod M (rev = 1)
 // of batch element b.
 template <int S, typename InT>
 __global__ void __launch_bounds__(256)
 slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
-             int RB, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+             int RB, int P, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   extern __shared__ __align__(16) unsigned char tile_raw[];
   InT* tile = reinterpret_cast<InT*>(tile_raw);
   const int q = blockIdx.y;
@@ -136,7 +144,7 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
     const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
     const int r = r0 + rr;
     if (lane == 0) exps[(long long)q * N + r] = e;
-    __nv_bfloat16* orow = out + (long long)q * S * 2 * plane + (long long)r * Kp;
+    __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
     for (int k = 2 * lane; k < N; k += 64) {
       const InT v0 = elem(k);
       const InT v1 = (k + 1 < N) ? elem(k + 1) : zero_of(v0);
@@ -145,8 +153,11 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
       digits_re_im<S>(v1, e, re1, im1);
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        *reinterpret_cast<__nv_bfloat162*>(orow + (2LL * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
-        *reinterpret_cast<__nv_bfloat162*>(orow + (2LL * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
+        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
+        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
+        if (P == 3)
+          *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 2) * plane + k) =
+              __floats2bfloat162_rn(-re0[i], -re1[i]);
       }
     }
   }
@@ -158,7 +169,7 @@ int row_block(int N) {
 }
 
 template <int S, typename InT>
-int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q,
+int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q, int P,
                  __nv_bfloat16* out, int* exps, cudaStream_t st) {
   const int RB = row_block(N);
   const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
@@ -166,7 +177,7 @@ int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, out, exps);
+  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, P, out, exps);
   e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
@@ -189,7 +200,7 @@ SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total) {
   s.At = w.take<float4>((size_t)Q * E);
   s.Bt = w.take<float4>((size_t)Q * E);
   s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
-  s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+  s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 3 * N * kpad(N));
   s.expA = w.take<int>((size_t)Q * N);
   s.expB = w.take<int>((size_t)Q * N);
   s.Ct = s.At;  // A~ is dead once sliced
@@ -210,11 +221,11 @@ int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
 }  // namespace
 
 template <typename InT>
-int slice_any(int S, const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q, void* out,
-              int* exps, cudaStream_t st) {
+int slice_any(int S, const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q, int P,
+              void* out, int* exps, cudaStream_t st) {
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   switch (S) {
-#define NSPT_CASE(s) case s: return launch_slice<s, InT>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, o, exps, st);
+#define NSPT_CASE(s) case s: return launch_slice<s, InT>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, P, o, exps, st);
     NSPT_CASE(2) NSPT_CASE(3) NSPT_CASE(4) NSPT_CASE(5) NSPT_CASE(6) NSPT_CASE(7) NSPT_CASE(8)
 #undef NSPT_CASE
     default: return NSPT_ERR_ARG;
@@ -222,13 +233,13 @@ int slice_any(int S, const InT* X, long long bstride, int M, int rev, int trans,
 }
 
 int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                     void* out, int* exps, cudaStream_t st) {
-  return slice_any<double2>(S, X, bstride, M, rev, trans, conj, N, Q, out, exps, st);
+                     int P, void* out, int* exps, cudaStream_t st) {
+  return slice_any<double2>(S, X, bstride, M, rev, trans, conj, N, Q, P, out, exps, st);
 }
 
 int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                        void* out, int* exps, cudaStream_t st) {
-  return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, out, exps, st);
+                        int P, void* out, int* exps, cudaStream_t st) {
+  return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, P, out, exps, st);
 }
 
 int nspt_split_init() {
@@ -259,8 +270,8 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
   TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
   TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
   // a2: slices of A~_q (rows) and of B~_q^T (columns of B~_q)
-  TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
-  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+  TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
+  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
   // a3: mode GEMMs on the tensor cores
   TRYS(gemm(w, N, Q, S, st));
   // a4: inverse transform, truncation, unscale 2^(-k log2r)
@@ -280,16 +291,16 @@ int nspt_split_bwd(int N, int T, int batch, int M, int S, int log2r, const doubl
   if (gA) {
     // gA~_p = G~_p (B~_p)^H
     TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 0, 0, N, Q, w.slA, w.expA, st));
-    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 1, N, Q, w.slB, w.expB, st));
+    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 1, N, Q, 3, w.slB, w.expB, st));
     TRYS(gemm(w, N, Q, S, st));
     TRYC(nspt_fft_inv_df(w.Ct, gA, T + 1, E, T, batch, M, 0, -log2r, st));
   }
   if (gB) {
     // gB~_p = (A~_p)^H G~_p
     TRYC(nspt_fft_fwd_df(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 1, N, Q, w.slA, w.expA, st));
-    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 1, 0, N, Q, w.slB, w.expB, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 1, N, Q, 2, w.slA, w.expA, st));
+    TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
     TRYS(gemm(w, N, Q, S, st));
     TRYC(nspt_fft_inv_df(w.Ct, gB, T + 1, E, T, batch, M, 0, -log2r, st));
   }

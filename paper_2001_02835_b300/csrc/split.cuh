@@ -14,9 +14,9 @@ int nspt_split_langevin(int N, int T, int batch, int M, int slices, double2* U, 
                         int flux, double eps, void* ws, cudaStream_t st);
 // slices of Q planes of X (see slice_kernel): out bf16 [Q][S][2][N][Kp], exps [Q][N]
 int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                     void* out, int* exps, cudaStream_t st);
+                     int P, void* out, int* exps, cudaStream_t st);
 int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                        void* out, int* exps, cudaStream_t st);
+                        int P, void* out, int* exps, cudaStream_t st);
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st);
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st);

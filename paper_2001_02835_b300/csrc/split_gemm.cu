@@ -10,16 +10,20 @@
 // FP32 while it has fewer than 24 significant bits.  Groups g = 0..3 keep
 // their own TMEM accumulators; groups g >= 4 share a fifth one, whose
 // rounding (the tensor core truncates at each accumulation step) stays near
-// 2^-56 of the result per step.  Real and imaginary parts give 10
-// accumulators of 48 FP32 columns = 480 of the 512 TMEM columns for a
-// 128 x 48 output tile.  The four real products of the complex product use
-// the instruction descriptor's A-negate bit for -A_im B_im.  The epilogue sums
+// 2^-56 of the result per step.  The complex product is embedded in two real
+// MMAs of N = 96 per slice pair: the right operand's tile holds the rows
+// [B_re; B_im; -B_re] (48 each), and
+//     D_g[:, 0:96] += A_re [B_re; B_im]^T      -> (A_re B_re | A_re B_im)
+//     D_g[:, 0:96] += (-A_im) [B_im; -B_re]^T  -> (-A_im B_im | A_im B_re)
+// (A-negate bit of the instruction descriptor), so one accumulator of 96 FP32
+// columns per group holds (re | im); 5 groups use 480 of the 512 TMEM columns
+// for a 128 x 48 output tile.  The epilogue sums
 // the groups in double-float (hi + lo float pair), applies
 // 2^(e_A[m] + e_B[n] - 14) and writes float4 (re_hi, re_lo, im_hi, im_lo).
 //
 // Roles (one CTA per SM, persistent over tiles): warp 0 lane 0 issues TMA
 // loads, warp 1 lane 0 issues tcgen05.mma, warps 2-5 drain TMEM.  Per K block
-// of 32, all S slices of the B tile (re, im) are loaded once and the A
+// of 32, all S slices of the B tile (re, im, -re) are loaded once and the A
 // slices stream through a 4-stage ring; the triangle of slice pairs
 // i + j < S is issued against the resident B slices.  Every wait is bounded
 // (globaltimer); on time-out the kernel records an error, drains its own TMA
@@ -38,12 +42,13 @@ constexpr uint32_t B_TILE = BN * KB * 2;  // 3 KB per part
 constexpr int NGROUPS = 5;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
-static_assert(2 * NGROUPS * BN <= (int)TMEM_COLS, "accumulators exceed TMEM");
+constexpr int NACC = 2 * BN;  // accumulator columns per group: (re | im)
+static_assert(NGROUPS * NACC <= (int)TMEM_COLS, "accumulators exceed TMEM");
 
 template <int S>
 struct Smem {
   uint8_t a[NA_STAGES][2][A_TILE];  // [stage][re/im]
-  uint8_t b[2][S][2][B_TILE];       // [buffer][slice][re/im]
+  uint8_t b[2][S][3][B_TILE];       // [buffer][slice][re, im, -re]
   uint64_t full_a[NA_STAGES], empty_a[NA_STAGES];
   uint64_t full_b[2], empty_b[2];
   uint64_t acc_full, acc_empty, drain;
@@ -137,10 +142,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
-        tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 2 * B_TILE);
+        tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
         for (int j = 0; j < S; ++j)
-          for (int c = 0; c < 2; ++c)
-            tc::tma_load_3d(sm.b[ib][j][c], &tmB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 2 + c);
+          for (int c = 0; c < 3; ++c)
+            tc::tma_load_3d(sm.b[ib][j][c], &tmB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
         issued_b[ib] = true;
         last_b_parity[ib] = pb;
         if (++ib == 2) { ib = 0; pb ^= 1; }
@@ -164,8 +169,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
       if (issued_b[s]) wait_bar(&sm.full_b[s], last_b_parity[s], &no_abort, err, 7);
   } else if (warp == 1 && lane == 0) {
     // ------------------------------ MMA issuer ------------------------------
-    constexpr uint32_t ID = tc::idesc_bf16(BM, BN, false);
-    constexpr uint32_t IDN = tc::idesc_bf16(BM, BN, true);
+    constexpr uint32_t ID = tc::idesc_bf16(BM, NACC, false);
+    constexpr uint32_t IDN = tc::idesc_bf16(BM, NACC, true);
     int ia = 0, ib = 0;
     uint32_t pa = 0, pb = 0, pacc = 0;
     bool any = false;
@@ -175,7 +180,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
       }
       tc::fence_after_sync();
-      uint32_t started = 0;  // bit (2g + c): accumulator already written in this tile
+      uint32_t started = 0;  // bit g: accumulator of group g already written in this tile
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
@@ -186,21 +191,16 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           const uint32_t a_re = tc::smem_u32(sm.a[ia][0]), a_im = tc::smem_u32(sm.a[ia][1]);
           for (int j = 0; j + i < S; ++j) {
             const int g = min(i + j, NGROUPS - 1);
-            const uint32_t d_re = tmem + (uint32_t)(2 * g) * BN;
-            const uint32_t d_im = tmem + (uint32_t)(2 * g + 1) * BN;
-            const uint32_t b_re = tc::smem_u32(sm.b[ib][j][0]), b_im = tc::smem_u32(sm.b[ib][j][1]);
+            const uint32_t d = tmem + (uint32_t)(g * NACC);
+            const uint32_t b_re = tc::smem_u32(sm.b[ib][j][0]);  // rows [re; im]
+            const uint32_t b_im = tc::smem_u32(sm.b[ib][j][1]);  // rows [im; -re]
 #pragma unroll
             for (int kk = 0; kk < KB / 16; ++kk) {
               const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the 64-byte swizzle row
-              const uint64_t ar = tc::desc_sw64(a_re + off), ai = tc::desc_sw64(a_im + off);
-              const uint64_t br = tc::desc_sw64(b_re + off), bi = tc::desc_sw64(b_im + off);
-              const uint32_t acc_re = (started >> (2 * g)) & 1u;
-              tc::mma_f16(d_re, ar, br, ID, acc_re);
-              tc::mma_f16(d_re, ai, bi, IDN, 1u);
-              const uint32_t acc_im = (started >> (2 * g + 1)) & 1u;
-              tc::mma_f16(d_im, ar, bi, ID, acc_im);
-              tc::mma_f16(d_im, ai, br, ID, 1u);
-              started |= 3u << (2 * g);
+              const uint32_t acc = (started >> g) & 1u;
+              tc::mma_f16(d, tc::desc_sw64(a_re + off), tc::desc_sw64(b_re + off), ID, acc);
+              tc::mma_f16(d, tc::desc_sw64(a_im + off), tc::desc_sw64(b_im + off), IDN, 1u);
+              started |= 1u << g;
               any = true;
             }
           }
@@ -244,8 +244,8 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         float re[NGROUPS][16], im[NGROUPS][16];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          tc::tmem_ld16(lane_base + (uint32_t)(2 * g) * BN + ch * 16, re[g]);
-          tc::tmem_ld16(lane_base + (uint32_t)(2 * g + 1) * BN + ch * 16, im[g]);
+          tc::tmem_ld16(lane_base + (uint32_t)(g * NACC) + ch * 16, re[g]);
+          tc::tmem_ld16(lane_base + (uint32_t)(g * NACC + BN) + ch * 16, im[g]);
         }
         tc::tmem_wait_ld();
 #pragma unroll
@@ -303,9 +303,9 @@ size_t smem_bytes() { return sizeof(Smem<S>) + 1024; }
 template <int S>
 int launch(const SplitGemmArgs& a, cudaStream_t st) {
   CUtensorMap mA, mB;
-  const long long planes = (long long)a.Q * S * 2;
-  if (make_map(&mA, a.slicesA, a.N, a.Kp, planes, BM)) return NSPT_ERR_CUDA;
-  if (make_map(&mB, a.slicesB, a.N, a.Kp, planes, BN)) return NSPT_ERR_CUDA;
+  // left operand: planes (re, im) per digit; right operand: (re, im, -re)
+  if (make_map(&mA, a.slicesA, a.N, a.Kp, (long long)a.Q * S * 2, BM)) return NSPT_ERR_CUDA;
+  if (make_map(&mB, a.slicesB, a.N, a.Kp, (long long)a.Q * S * 3, BN)) return NSPT_ERR_CUDA;
   const int tilesM = (a.N + BM - 1) / BM, tilesN = (a.N + BN - 1) / BN;
   const long long ntiles = (long long)a.Q * tilesM * tilesN;
   int grid = a.num_sms;

@@ -3,7 +3,7 @@
 
 struct SplitGemmArgs {
   const void* slicesA;  // bf16 [Q][S][2][N][Kp]  rows of A~_q (K-major)
-  const void* slicesB;  // bf16 [Q][S][2][N][Kp]  rows of (B~_q)^T (K-major)
+  const void* slicesB;  // bf16 [Q][S][3][N][Kp]  rows of (B~_q)^T (K-major): re, im, -re
   const int* expA;      // [Q][N] row exponents of A~_q
   const int* expB;      // [Q][N] row exponents of (B~_q)^T
   float4* C;            // [Q][N][N] double-float (re_hi, re_lo, im_hi, im_lo)

@@ -89,16 +89,18 @@ def test_split_backward_matches_oracle(nspt, N, T, batch):
     assert max_order_rel(host(gB), rB) <= bound(6, N)
 
 
-@pytest.mark.parametrize("S,trans,conj", [(2, 0, 0), (6, 0, 0), (6, 1, 0), (6, 0, 1), (8, 1, 1)])
-def test_slicer_reconstructs_rows(nspt, S, trans, conj):
+@pytest.mark.parametrize("S,trans,conj,right", [(2, 0, 0, 0), (6, 0, 0, 0), (6, 1, 0, 1), (6, 0, 1, 0), (8, 1, 1, 1)])
+def test_slicer_reconstructs_rows(nspt, S, trans, conj, right):
     g = syn.rng(5500 + S)
     Q, N = 3, 37
     X = syn.gaussian(g, (Q, N, N), 1.0)
     X[1, 5] = 0.0          # an all-zero row (or column)
     X[1, :, 5] = 0.0
     X[2] *= 1e-30          # tiny magnitudes keep their relative precision
-    sl, ex = nspt.split_slices(dev(X), S, trans=bool(trans), conj=bool(conj))
+    sl, ex = nspt.split_slices(dev(X), S, trans=bool(trans), conj=bool(conj), right=bool(right))
     sl = host(sl.float()).astype(np.float64)[..., :N]
+    if right:
+        np.testing.assert_array_equal(sl[:, :, 2], -sl[:, :, 0])
     ex = host(ex)
     Y = np.swapaxes(X, 1, 2) if trans else X
     if conj:
@@ -123,10 +125,11 @@ def test_mode_gemm_digit_groups_are_exact(nspt, N, pairs):
     Q, S = 2, 6
     Kp = (N + 7) // 8 * 8
     dA = np.zeros((Q, S, 2, N, Kp))
-    dB = np.zeros((Q, S, 2, N, Kp))
+    dB = np.zeros((Q, S, 3, N, Kp))
     for i, j in pairs:
         dA[:, i, :, :, :N] = rs.integers(-128, 129, (Q, 2, N, N))
-        dB[:, j, :, :, :N] = rs.integers(-128, 129, (Q, 2, N, N))
+        dB[:, j, :2, :, :N] = rs.integers(-128, 129, (Q, 2, N, N))
+    dB[:, :, 2] = -dB[:, :, 0]
     w = 2.0 ** (-8.0 * np.arange(S))
     slA = torch.from_numpy((dA * w[None, :, None, None, None]).astype(np.float32)).to(torch.bfloat16).cuda()
     slB = torch.from_numpy((dB * w[None, :, None, None, None]).astype(np.float32)).to(torch.bfloat16).cuda()
