@@ -54,22 +54,26 @@ __device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
   s[0] = sign * small_int_to_float((int)X);
 }
 
-// digits of a double-float value x = hi + lo (|x| < 2^e), same representation as above
+// digits of a double-float value x = hi + lo (|x| < 2^e) in FP32 arithmetic:
+// with v = x 2^-e (|v| < 1) and sigma_i = 1.5 * 2^(16 - 8i), t = (v + sigma_i) -
+// sigma_i rounds v to the nearest multiple of 2^(-7-8i) exactly, v - t is
+// exact, and t * 2^7 = d_i 2^(-8i) is the stored slice value.  Digits 0..2
+// come from hi alone (|lo| < 2^-25 lies below their grid); lo joins the
+// residual before digit 3, so |d_i| <= 128 for i < 3 and <= 192 after.
 template <int S>
 __device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
-  constexpr int W = 8 * S - 1;
-  constexpr int W1 = W < 62 ? W : 62;  // signed 64-bit headroom; the rest is an exact shift
-  const long long Xs = f_scaled_int(x.h, W1 - e) + f_scaled_int(x.l, W1 - e);
-  const float sign = Xs < 0 ? -1.f : 1.f;
-  unsigned long long X = (unsigned long long)(Xs < 0 ? -Xs : Xs) << (W - W1);
+  float f1, f2;
+  pow2_pair(-e, f1, f2);
+  float v = (x.h * f1) * f2;
+  const float lo = (x.l * f1) * f2;
 #pragma unroll
-  for (int i = S - 1; i >= 1; --i) {
-    int d = (int)(X & 255ull);
-    X >>= 8;
-    if (d > 128) { d -= 256; X += 1; }
-    s[i] = sign * small_int_to_float(d) * __int_as_float((127 - 8 * i) << 23);
+  for (int i = 0; i < S; ++i) {
+    if (i == 3) v = v + lo;
+    const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
+    const float t = (v + sig) - sig;
+    v = v - t;
+    s[i] = t * 128.f;
   }
-  s[0] = sign * small_int_to_float((int)X);
 }
 
 // smallest e with |x| < 2^e for every part, from the exponent field
