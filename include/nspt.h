@@ -130,6 +130,42 @@ NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, in
                            double eps, const nspt_opts* opts, void* stream);
 
 /*
+ * Grouped products: `count` (<= 64) independent products of uneven sizes,
+ * C_i = A_i star B_i with N_i, T_i and batch_i each, by FFT-CONV with
+ * M_i = smallest power of two >= 2(T_i + 1) (opts->fft_len must be 0).
+ * Split form: the mode GEMMs of all products run in ONE persistent
+ * tensor-core launch whose per-product tensor maps travel in the kernel
+ * parameters, so the call needs no device-side table and can be captured in
+ * a CUDA graph (after nspt_init).  FP64 form: the products run one after
+ * another.  `descs` is a HOST array; pointers inside are device pointers with
+ * the layout of nspt_polymat_mul.  Workspace: nspt_workspace_size_grouped().
+ */
+typedef struct nspt_polymat_desc {
+  const void* A;
+  const void* B;
+  void* C;
+  int N, T, batch;
+} nspt_polymat_desc;
+
+NSPT_API size_t nspt_workspace_size_grouped(const nspt_polymat_desc* descs, int count, const nspt_opts* opts);
+NSPT_API int nspt_polymat_mul_grouped(const nspt_polymat_desc* descs, int count, const nspt_opts* opts,
+                                      void* stream);
+
+/*
+ * Autotuner of the split form's tensor-core tile width (128 x 32 or 128 x 48
+ * output tiles, i.e. 64- or 96-column MMAs): times the grouped mode-GEMM
+ * launch of this group signature (every product's N and M x batch, slices)
+ * with each width on the caller's workspace (sized as for
+ * nspt_polymat_mul_grouped, contents overwritten), keeps the fastest for
+ * later calls with the same signature (a single product is a group of one),
+ * and writes it to *chosen_bn.  cache_path (may be NULL): a text file of
+ * "signature width" lines read before timing and appended after.  Synchronises
+ * `stream`; call it before any graph capture.
+ */
+NSPT_API int nspt_autotune_grouped(const nspt_polymat_desc* descs, int count, const nspt_opts* opts,
+                                   const char* cache_path, int* chosen_bn, void* stream);
+
+/*
  * Single stages of FFT-CONV, for stage timing and per-stage tests.
  * nspt_order_fft: Steps 1-2 -- At[b][p] = sum_{k<=T} A[b][k] w^(kp), p = 0..M-1,
  *   A : [batch][T+1][N][N] -> At : [batch][M][N][N], w = exp(+2 pi i/M).

@@ -41,6 +41,11 @@ class NsptError(RuntimeError):
     """A libnspt call returned a negative status."""
 
 
+class PolymatDesc(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("N", ctypes.c_int), ("T", ctypes.c_int), ("batch", ctypes.c_int)]
+
+
 class Opts(ctypes.Structure):
     _fields_ = [
         ("algo", ctypes.c_int),
@@ -74,6 +79,9 @@ _SIGS = {
     "nspt_split_slices": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp]),
     "nspt_split_mode_gemm": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, _vp, _vp]),
     "nspt_polymat_mul_fft_noalloc": (_i, [_vp, _vp, _vp, _i, _i, _i, _vp]),
+    "nspt_workspace_size_grouped": (_sz, [_vp, _i, ctypes.POINTER(Opts)]),
+    "nspt_polymat_mul_grouped": (_i, [_vp, _i, ctypes.POINTER(Opts), _vp]),
+    "nspt_autotune_grouped": (_i, [_vp, _i, ctypes.POINTER(Opts), ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), _vp]),
 }
 
 
@@ -290,6 +298,56 @@ def split_mode_gemm(slA: torch.Tensor, slB: torch.Tensor, expA: torch.Tensor, ex
     if int(err.item()) != 0:
         raise NsptError("nspt_split_mode_gemm: device wait timed out (code %d)" % int(err.item()))
     return Ct
+
+
+def _group_descs(As, Bs, Cs):
+    if not (len(As) == len(Bs) == len(Cs)) or not As:
+        raise ValueError("need equally many A, B, C tensors")
+    arr = (PolymatDesc * len(As))()
+    for i, (A, B, C) in enumerate(zip(As, Bs, Cs)):
+        for X, n in ((A, "A"), (B, "B"), (C, "C")):
+            _check_tensor(X, n)
+        if A.shape != B.shape or A.shape != C.shape:
+            raise ValueError("product %d: A, B, C shapes differ" % i)
+        batch, T, N = _series_dims(A)
+        arr[i] = PolymatDesc(A.data_ptr(), B.data_ptr(), C.data_ptr(), N, T, batch)
+    return arr
+
+
+def _group_ws(arr, count, opts, device):
+    nbytes = int(lib().nspt_workspace_size_grouped(arr, count, ctypes.byref(opts)))
+    ws = _workspace(nbytes, device)
+    if ws is not None:
+        opts.workspace = ws.data_ptr()
+        opts.workspace_bytes = ws.numel()
+    return ws
+
+
+def polymat_mul_grouped(As, Bs, Cs=None, **kw):
+    """C_i = A_i star B_i for a list of products of uneven (N, T) (nspt_polymat_mul_grouped);
+    kw: prec ('split' runs all mode GEMMs in one persistent tensor-core launch), slices, rescale_log2r."""
+    if Cs is None:
+        Cs = [torch.empty_like(A) for A in As]
+    arr = _group_descs(As, Bs, Cs)
+    opts = make_opts(algo="fft", **kw)
+    ws = _group_ws(arr, len(As), opts, As[0].device)  # noqa: F841
+    _check(lib().nspt_polymat_mul_grouped(arr, len(As), ctypes.byref(opts), _stream_ptr(As[0].device)),
+           "nspt_polymat_mul_grouped")
+    return Cs
+
+
+def autotune_grouped(As, Bs, cache_path=None, **kw) -> int:
+    """Times the tile widths of the split form's grouped GEMM for this group and keeps the
+    fastest for later calls with the same signature; returns the chosen width."""
+    Cs = [torch.empty_like(A) for A in As]
+    arr = _group_descs(As, Bs, Cs)
+    opts = make_opts(algo="fft", prec="split", **kw)
+    ws = _group_ws(arr, len(As), opts, As[0].device)  # noqa: F841
+    chosen = ctypes.c_int(0)
+    path = cache_path.encode() if cache_path else None
+    _check(lib().nspt_autotune_grouped(arr, len(As), ctypes.byref(opts), path, ctypes.byref(chosen),
+                                       _stream_ptr(As[0].device)), "nspt_autotune_grouped")
+    return int(chosen.value)
 
 
 class PolymatMul(torch.autograd.Function):

@@ -14,6 +14,8 @@
 #include "tek.cuh"
 #include "split.cuh"
 #include "prof.cuh"
+#include "split_gemm.cuh"
+#include <algorithm>
 
 namespace {
 thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -493,6 +495,71 @@ int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int 
   }
   return langevin_fp64(p, (double2*)U, (const double2*)eta, (double2*)F, flux, eps, opts ? opts->workspace : nullptr,
                        (cudaStream_t)stream);
+}
+
+static int check_group(const nspt_polymat_desc* d, int count, const nspt_opts* o, Plan* first) {
+  if (!d || count < 1 || count > NSPT_SPLIT_MAX_PROBLEMS) return NSPT_ERR_ARG;
+  if (o && o->fft_len != 0) return NSPT_ERR_ARG;
+  for (int i = 0; i < count; ++i) {
+    Plan p;
+    int rc = make_plan(d[i].N, d[i].T, d[i].batch, o, &p);
+    if (rc) return rc;
+    if (p.algo != NSPT_ALGO_FFT && p.prec == NSPT_PREC_SPLIT) return NSPT_ERR_UNSUPPORTED;
+    if (!d[i].A || !d[i].B || !d[i].C) return NSPT_ERR_ARG;
+    const size_t bytes = (size_t)d[i].batch * (d[i].T + 1) * p.E * sizeof(double2);
+    for (int j = 0; j < count; ++j) {
+      const size_t bj = (size_t)d[j].batch * (d[j].T + 1) * (size_t)d[j].N * d[j].N * sizeof(double2);
+      if (overlaps(d[i].C, bytes, d[j].A, bj) || overlaps(d[i].C, bytes, d[j].B, bj)) return NSPT_ERR_ALIAS;
+      if (j != i && overlaps(d[i].C, bytes, d[j].C, bj)) return NSPT_ERR_ALIAS;
+    }
+    if (i == 0) *first = p;
+  }
+  return NSPT_OK;
+}
+
+size_t nspt_workspace_size_grouped(const nspt_polymat_desc* d, int count, const nspt_opts* o) {
+  Plan p;
+  if (check_group(d, count, o, &p)) return 0;
+  if (p.prec == NSPT_PREC_SPLIT) return nspt_split_ws_grouped(d, count, p.slices);
+  size_t mx = 0;
+  for (int i = 0; i < count; ++i) {
+    Plan q;
+    make_plan(d[i].N, d[i].T, d[i].batch, o, &q);
+    mx = std::max(mx, ws_mul(q));
+  }
+  return mx;
+}
+
+int nspt_polymat_mul_grouped(const nspt_polymat_desc* d, int count, const nspt_opts* o, void* stream) {
+  Plan p;
+  int rc = check_group(d, count, o, &p);
+  if (rc) return rc;
+  if ((rc = check_ws(o, nspt_workspace_size_grouped(d, count, o)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (p.prec == NSPT_PREC_SPLIT) {
+    if (p.rescale_auto) return NSPT_ERR_UNSUPPORTED;
+    return nspt_split_mul_grouped(d, count, p.slices, p.log2r, o->workspace, st);
+  }
+  for (int i = 0; i < count; ++i) {
+    Plan q;
+    make_plan(d[i].N, d[i].T, d[i].batch, o, &q);
+    rc = mul_fp64(q, (const double2*)d[i].A, (const double2*)d[i].B, (double2*)d[i].C, o ? o->workspace : nullptr,
+                  st);
+    if (rc) return rc;
+  }
+  return NSPT_OK;
+}
+
+int nspt_autotune_grouped(const nspt_polymat_desc* d, int count, const nspt_opts* o, const char* cache_path,
+                          int* chosen_bn, void* stream) {
+  Plan p;
+  int rc = check_group(d, count, o, &p);
+  if (rc) return rc;
+  if (!chosen_bn || p.prec != NSPT_PREC_SPLIT) return NSPT_ERR_ARG;
+  if ((rc = check_ws(o, nspt_workspace_size_grouped(d, count, o)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  return nspt_split_autotune_grouped(d, count, p.slices, o->workspace, cache_path, chosen_bn, (cudaStream_t)stream);
 }
 
 int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {

@@ -11,6 +11,11 @@
 // No FP64 arithmetic is used: on B300 the FP64 pipe is about 1/58 of FP32.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include <cuda_bf16.h>
 
@@ -212,10 +217,32 @@ SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total) {
   return s;
 }
 
-int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
+// ---------------- tile-width table filled by the autotuner ----------------
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tuned_bn;
+
+std::string signature(int S, const std::vector<std::pair<int, int>>& nq) {
+  std::string sig = "S" + std::to_string(S);
+  for (auto& x : nq) sig += ";" + std::to_string(x.first) + "x" + std::to_string(x.second);
+  return sig;
+}
+
+int choose_bn(const std::string& sig) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_bn.find(sig);
+  return it == g_tuned_bn.end() ? 48 : it->second;
+}
+
+SplitGemmArgs gemm_args(const SplitWs& w, int N, int Q, int S) {
   SplitGemmArgs a;
   a.slicesA = w.slA; a.slicesB = w.slB; a.expA = w.expA; a.expB = w.expB; a.C = w.Ct;
-  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = w.err;
+  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
+  return a;
+}
+
+int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
+  SplitGemmArgs a = gemm_args(w, N, Q, S);
+  a.bn = choose_bn(signature(S, {{N, Q}}));
   return nspt_split_gemm(a, st);
 }
 
@@ -329,5 +356,146 @@ int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(host_err, ws, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Grouped products: independent products of uneven (N, T) whose mode GEMMs
+// run in one persistent tensor-core launch.
+// ---------------------------------------------------------------------------
+namespace {
+
+int pow2_at_least(int x) {
+  int m = 1;
+  while (m < x) m <<= 1;
+  return m;
+}
+
+struct GroupLayout {
+  int* err;
+  std::vector<SplitWs> ws;
+  size_t total;
+};
+
+GroupLayout carve_group(void* base, const nspt_polymat_desc* d, int count, int S) {
+  GroupLayout g;
+  WsCarver w(base, SIZE_MAX);
+  g.err = w.take<int>(64);
+  for (int i = 0; i < count; ++i) {
+    const int N = d[i].N, M = pow2_at_least(2 * (d[i].T + 1));
+    const long long E = (long long)N * N, Q = (long long)d[i].batch * M;
+    SplitWs s;
+    s.err = g.err;
+    s.At = w.take<float4>((size_t)Q * E);
+    s.Bt = w.take<float4>((size_t)Q * E);
+    s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+    s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 3 * N * kpad(N));
+    s.expA = w.take<int>((size_t)Q * N);
+    s.expB = w.take<int>((size_t)Q * N);
+    s.Ct = s.At;
+    g.ws.push_back(s);
+  }
+  g.total = w.off;
+  return g;
+}
+
+std::string group_signature(const nspt_polymat_desc* d, int count, int S) {
+  std::vector<std::pair<int, int>> nq;
+  for (int i = 0; i < count; ++i) nq.push_back({d[i].N, d[i].batch * pow2_at_least(2 * (d[i].T + 1))});
+  return signature(S, nq);
+}
+
+int group_prepare(const nspt_polymat_desc* d, int count, int S, int log2r, const GroupLayout& g,
+                  std::vector<SplitGemmArgs>& args, cudaStream_t st) {
+  TRYC(cudaMemsetAsync(g.err, 0, sizeof(int), st));
+  args.clear();
+  for (int i = 0; i < count; ++i) {
+    const int N = d[i].N, T = d[i].T, b = d[i].batch, M = pow2_at_least(2 * (T + 1));
+    const int E = N * N, Q = b * M;
+    const SplitWs& w = g.ws[i];
+    TRYC(nspt_fft_fwd_df((const double2*)d[i].A, T + 1, w.At, E, T, b, M, 0, log2r, st));
+    TRYC(nspt_fft_fwd_df((const double2*)d[i].B, T + 1, w.Bt, E, T, b, M, 0, log2r, st));
+    TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
+    args.push_back(gemm_args(w, N, Q, S));
+  }
+  return NSPT_OK;
+}
+
+}  // namespace
+
+size_t nspt_split_ws_grouped(const nspt_polymat_desc* d, int count, int S) {
+  return carve_group(nullptr, d, count, S).total;
+}
+
+int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log2r, void* ws, cudaStream_t st) {
+  GroupLayout g = carve_group(ws, d, count, S);
+  std::vector<SplitGemmArgs> args;
+  TRYS(group_prepare(d, count, S, log2r, g, args, st));
+  TRYS(nspt_split_gemm_batch(args.data(), count, S, choose_bn(group_signature(d, count, S)), g_num_sms, st));
+  for (int i = 0; i < count; ++i) {
+    const int N = d[i].N, T = d[i].T, M = pow2_at_least(2 * (T + 1));
+    TRYC(nspt_fft_inv_df(g.ws[i].Ct, (double2*)d[i].C, T + 1, N * N, T, d[i].batch, M, 0, log2r, st));
+  }
+  return NSPT_OK;
+}
+
+int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,
+                                int* chosen, cudaStream_t st) {
+  const std::string sig = group_signature(d, count, S);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char key[8192];
+      int bn = 0;
+      while (fscanf(f, "%8191s %d", key, &bn) == 2) {
+        if (sig == key && (bn == 32 || bn == 48)) {
+          std::lock_guard<std::mutex> lk(g_tune_mu);
+          g_tuned_bn[sig] = bn;
+        }
+      }
+      fclose(f);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_bn.find(sig);
+    if (it != g_tuned_bn.end()) { *chosen = it->second; return NSPT_OK; }
+  }
+  GroupLayout g = carve_group(ws, d, count, S);
+  std::vector<SplitGemmArgs> args;
+  TRYS(group_prepare(d, count, S, 0, g, args, st));
+  const int cands[2] = {32, 48};
+  float best = 1e30f;
+  int best_bn = 48;
+  cudaEvent_t e0, e1;
+  TRYC(cudaEventCreate(&e0));
+  TRYC(cudaEventCreate(&e1));
+  for (int bn : cands) {
+    int rc = nspt_split_gemm_batch(args.data(), count, S, bn, g_num_sms, st);  // warm-up
+    for (int r = 0; r < 3 && rc == NSPT_OK; ++r) {
+      if (r == 0) cudaEventRecord(e0, st);
+      rc = nspt_split_gemm_batch(args.data(), count, S, bn, g_num_sms, st);
+    }
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || rc != NSPT_OK) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return rc ? rc : NSPT_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) { best = ms; best_bn = bn; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned_bn[sig] = best_bn;
+  }
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "%s %d\n", sig.c_str(), best_bn);
+      fclose(f);
+    }
+  }
+  *chosen = best_bn;
   return NSPT_OK;
 }

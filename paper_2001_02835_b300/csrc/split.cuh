@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "../../include/nspt.h"
+
 int nspt_split_init();
 size_t nspt_split_ws_mul(int N, int T, int batch, int M, int slices);
 size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int slices);
@@ -20,3 +22,7 @@ int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int re
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st);
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st);
+size_t nspt_split_ws_grouped(const nspt_polymat_desc* d, int count, int S);
+int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log2r, void* ws, cudaStream_t st);
+int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,
+                                int* chosen, cudaStream_t st);

@@ -33,20 +33,39 @@
 #include "split_gemm.cuh"
 #include "tc_ptx.cuh"
 
+#include <cstring>
+#include <memory>
+
 namespace {
 
-constexpr int BM = 128, BN = 48, KB = 32;
+constexpr int BM = 128, KB = 32;
 constexpr int NA_STAGES = 4;
 constexpr uint32_t A_TILE = BM * KB * 2;  // 8 KB per part
-constexpr uint32_t B_TILE = BN * KB * 2;  // 3 KB per part
 constexpr int NGROUPS = 5;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
-constexpr int NACC = 2 * BN;  // accumulator columns per group: (re | im)
-static_assert(NGROUPS * NACC <= (int)TMEM_COLS, "accumulators exceed TMEM");
 
-template <int S>
+// One problem of a (possibly grouped) launch; all of them travel in the kernel
+// parameters, so a launch needs no device-side table and can be captured.
+struct alignas(64) GemmProblem {
+  CUtensorMap mA, mB;    // slice planes of the left / right operand
+  const int* expA;
+  const int* expB;
+  float4* C;
+  int N, Q, tilesM, tilesN;
+  long long tile_begin;  // first global tile index of this problem
+};
+
+template <int MAXP>
+struct GemmBatch {
+  GemmProblem p[MAXP];
+  int count;
+  long long total_tiles;
+};
+
+template <int S, int BN>
 struct Smem {
+  static constexpr uint32_t B_TILE = BN * KB * 2;  // per part
   uint8_t a[NA_STAGES][2][A_TILE];  // [stage][re/im]
   uint8_t b[2][S][3][B_TILE];       // [buffer][slice][re, im, -re]
   uint64_t full_a[NA_STAGES], empty_a[NA_STAGES];
@@ -97,16 +116,17 @@ __device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, flo
   lo = l - (hi - s3);
 }
 
-template <int S>
+template <int S, int BN, int MAXP>
 __global__ void __launch_bounds__(192, 1)
-split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                  const int* __restrict__ expA, const int* __restrict__ expB, float4* __restrict__ C, int N,
-                  int Q, int tilesM, int tilesN, int* err) {
+split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
+  constexpr int NACC = 2 * BN;  // accumulator columns per group: (re | im)
+  static_assert(NGROUPS * NACC <= (int)TMEM_COLS, "accumulators exceed TMEM");
+  static_assert(BN % 16 == 0 && (BN / 8) * 8 == BN, "tile width");
+  constexpr uint32_t B_TILE = Smem<S, BN>::B_TILE;
   extern __shared__ uint8_t smem_raw[];
-  Smem<S>& sm = *reinterpret_cast<Smem<S>*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
+  Smem<S, BN>& sm = *reinterpret_cast<Smem<S, BN>*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nK = (N + KB - 1) / KB;
-  const long long ntiles = (long long)Q * tilesM * tilesN;
+  const long long ntiles = gb.total_tiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NA_STAGES; ++s) { tc::mbar_init(&sm.full_a[s], 1); tc::mbar_init(&sm.empty_a[s], 1); }
@@ -117,8 +137,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     sm.abort_flag = 0;
     tc::fence_mbar_init();
     tc::fence_proxy_async();
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
+    for (int p = 0; p < gb.count; ++p) {
+      tc::prefetch_tmap(&gb.p[p].mA);
+      tc::prefetch_tmap(&gb.p[p].mB);
+    }
   }
   if (warp == 1) {
     tc::tmem_alloc(&sm.tmem_base, TMEM_COLS);
@@ -135,17 +157,22 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     uint32_t pa = 0, pb = 0;
     uint32_t last_a_parity[NA_STAGES] = {0, 0, 0, 0}, last_b_parity[2] = {0, 0};
     bool issued_a[NA_STAGES] = {false, false, false, false}, issued_b[2] = {false, false};
+    int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
-      const int q = (int)(t / (tilesM * tilesN));
-      const int r = (int)(t % (tilesM * tilesN));
-      const int m0 = (r / tilesN) * BM, n0 = (r % tilesN) * BN;
+      while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
+      const GemmProblem& P = gb.p[pi];
+      const long long lt = t - P.tile_begin;
+      const int q = (int)(lt / (P.tilesM * P.tilesN));
+      const int r = (int)(lt % (P.tilesM * P.tilesN));
+      const int m0 = (r / P.tilesN) * BM, n0 = (r % P.tilesN) * BN;
+      const int nK = (P.N + KB - 1) / KB;
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
         tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
         for (int j = 0; j < S; ++j)
           for (int c = 0; c < 3; ++c)
-            tc::tma_load_3d(sm.b[ib][j][c], &tmB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
+            tc::tma_load_3d(sm.b[ib][j][c], &P.mB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
         issued_b[ib] = true;
         last_b_parity[ib] = pb;
         if (++ib == 2) { ib = 0; pb ^= 1; }
@@ -153,7 +180,7 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
           if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
           for (int c = 0; c < 2; ++c)
-            tc::tma_load_3d(sm.a[ia][c], &tmA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
+            tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
           issued_a[ia] = true;
           last_a_parity[ia] = pa;
           if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
@@ -174,8 +201,10 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     int ia = 0, ib = 0;
     uint32_t pa = 0, pb = 0, pacc = 0;
     bool any = false;
-    int local = 0;
+    int local = 0, pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x, ++local) {
+      while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
+      const int nK = (gb.p[pi].N + KB - 1) / KB;
       if (local > 0) {
         if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
       }
@@ -227,17 +256,24 @@ split_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const int row = quarter * 32 + lane;
     uint32_t pacc = 0;
     constexpr int G = S < NGROUPS ? S : NGROUPS;
+    int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
-      const int q = (int)(t / (tilesM * tilesN));
-      const int r = (int)(t % (tilesM * tilesN));
-      const int m0 = (r / tilesN) * BM, n0 = (r % tilesN) * BN;
+      while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
+      const GemmProblem& P = gb.p[pi];
+      const int N = P.N;
+      const long long lt = t - P.tile_begin;
+      const int q = (int)(lt / (P.tilesM * P.tilesN));
+      const int r = (int)(lt % (P.tilesM * P.tilesN));
+      const int m0 = (r / P.tilesN) * BM, n0 = (r % P.tilesN) * BN;
+      const int* __restrict__ expA = P.expA;
+      const int* __restrict__ expB = P.expB;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6)) break;
       pacc ^= 1;
       tc::fence_after_sync();
       const int m = m0 + row;
       const bool mvalid = m < N;
       const int ea = mvalid ? __ldg(expA + (long long)q * N + m) : 0;
-      float4* crow = C + ((long long)q * N + (mvalid ? m : 0)) * N;
+      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
       for (int ch = 0; ch < BN / 16; ++ch) {
@@ -297,25 +333,66 @@ int make_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes
   return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;
 }
 
-template <int S>
-size_t smem_bytes() { return sizeof(Smem<S>) + 1024; }
+template <int S, int BN>
+size_t smem_bytes() { return sizeof(Smem<S, BN>) + 1024; }
 
-template <int S>
-int launch(const SplitGemmArgs& a, cudaStream_t st) {
-  CUtensorMap mA, mB;
-  // left operand: planes (re, im) per digit; right operand: (re, im, -re)
-  if (make_map(&mA, a.slicesA, a.N, a.Kp, (long long)a.Q * S * 2, BM)) return NSPT_ERR_CUDA;
-  if (make_map(&mB, a.slicesB, a.N, a.Kp, (long long)a.Q * S * 3, BN)) return NSPT_ERR_CUDA;
-  const int tilesM = (a.N + BM - 1) / BM, tilesN = (a.N + BN - 1) / BN;
-  const long long ntiles = (long long)a.Q * tilesM * tilesN;
-  int grid = a.num_sms;
-  if (ntiles < grid) grid = (int)ntiles;
+template <int S, int BN, int MAXP>
+int launch(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
+  std::unique_ptr<GemmBatch<MAXP>> gb(new GemmBatch<MAXP>());
+  memset(gb.get(), 0, sizeof(GemmBatch<MAXP>));
+  long long tiles = 0;
+  for (int i = 0; i < count; ++i) {
+    GemmProblem& P = gb->p[i];
+    // left operand: planes (re, im) per digit; right operand: (re, im, -re)
+    if (make_map(&P.mA, a[i].slicesA, a[i].N, a[i].Kp, (long long)a[i].Q * S * 2, BM)) return NSPT_ERR_CUDA;
+    if (make_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, (long long)a[i].Q * S * 3, BN)) return NSPT_ERR_CUDA;
+    P.expA = a[i].expA; P.expB = a[i].expB; P.C = a[i].C;
+    P.N = a[i].N; P.Q = a[i].Q;
+    P.tilesM = (a[i].N + BM - 1) / BM;
+    P.tilesN = (a[i].N + BN - 1) / BN;
+    P.tile_begin = tiles;
+    tiles += (long long)a[i].Q * P.tilesM * P.tilesN;
+  }
+  gb->count = count;
+  gb->total_tiles = tiles;
+  int grid = num_sms;
+  if (tiles < grid) grid = (int)tiles;
+  if (grid < 1) return NSPT_OK;
   ProfScope ps(NSPT_STAGE_GEMM_TC, st);
-  split_gemm_kernel<S><<<grid, 192, smem_bytes<S>(), st>>>(mA, mB, a.expA, a.expB, a.C, a.N, a.Q, tilesM, tilesN,
-                                                           a.err);
+  split_gemm_kernel<S, BN, MAXP><<<grid, 192, smem_bytes<S, BN>(), st>>>(*gb, a[0].err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
+}
+
+template <int S, int BN>
+int launch_any(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
+  if (count == 1) return launch<S, BN, 1>(a, count, st, num_sms);
+  if (count <= NSPT_SPLIT_MAX_PROBLEMS) return launch<S, BN, NSPT_SPLIT_MAX_PROBLEMS>(a, count, st, num_sms);
+  return NSPT_ERR_ARG;
+}
+
+template <int S>
+int launch_bn(const SplitGemmArgs* a, int count, int bn, cudaStream_t st, int num_sms) {
+  if (bn == 32) return launch_any<S, 32>(a, count, st, num_sms);
+  return launch_any<S, 48>(a, count, st, num_sms);
+}
+
+template <int S, int BN, int MAXP>
+int set_attr() {
+  cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<S, BN, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem_bytes<S, BN>());
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
+template <int S>
+int set_attrs() {
+  int rc = set_attr<S, 32, 1>();
+  if (!rc) rc = set_attr<S, 48, 1>();
+  if (!rc) rc = set_attr<S, 32, NSPT_SPLIT_MAX_PROBLEMS>();
+  if (!rc) rc = set_attr<S, 48, NSPT_SPLIT_MAX_PROBLEMS>();
+  return rc;
 }
 
 }  // namespace
@@ -331,27 +408,33 @@ int nspt_split_gemm_init() {
     }
     g_encode = (EncodeTiledFn)fn;
   }
-#define NSPT_ATTR(s)                                                                                        \
-  {                                                                                                         \
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<s>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                         (int)smem_bytes<s>());                                             \
-    if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }                            \
-  }
-  NSPT_ATTR(2) NSPT_ATTR(3) NSPT_ATTR(4) NSPT_ATTR(5) NSPT_ATTR(6) NSPT_ATTR(7) NSPT_ATTR(8)
-#undef NSPT_ATTR
+  int rc = set_attrs<2>();
+  if (!rc) rc = set_attrs<3>();
+  if (!rc) rc = set_attrs<4>();
+  if (!rc) rc = set_attrs<5>();
+  if (!rc) rc = set_attrs<6>();
+  if (!rc) rc = set_attrs<7>();
+  if (!rc) rc = set_attrs<8>();
+  if (rc) return rc;
   return NSPT_OK;
 }
 
-int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st) {
-  if (a.N > 1024 || a.N < 1) return NSPT_ERR_UNSUPPORTED;
-  switch (a.S) {
-    case 2: return launch<2>(a, st);
-    case 3: return launch<3>(a, st);
-    case 4: return launch<4>(a, st);
-    case 5: return launch<5>(a, st);
-    case 6: return launch<6>(a, st);
-    case 7: return launch<7>(a, st);
-    case 8: return launch<8>(a, st);
+int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int num_sms, cudaStream_t st) {
+  if (count < 1) return NSPT_OK;
+  for (int i = 0; i < count; ++i)
+    if (a[i].N > 1024 || a[i].N < 1 || a[i].S != S) return NSPT_ERR_UNSUPPORTED;
+  switch (S) {
+    case 2: return launch_bn<2>(a, count, bn, st, num_sms);
+    case 3: return launch_bn<3>(a, count, bn, st, num_sms);
+    case 4: return launch_bn<4>(a, count, bn, st, num_sms);
+    case 5: return launch_bn<5>(a, count, bn, st, num_sms);
+    case 6: return launch_bn<6>(a, count, bn, st, num_sms);
+    case 7: return launch_bn<7>(a, count, bn, st, num_sms);
+    case 8: return launch_bn<8>(a, count, bn, st, num_sms);
     default: return NSPT_ERR_ARG;
   }
+}
+
+int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st) {
+  return nspt_split_gemm_batch(&a, 1, a.S, a.bn ? a.bn : 48, a.num_sms, st);
 }

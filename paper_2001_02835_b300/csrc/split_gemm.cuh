@@ -10,7 +10,13 @@ struct SplitGemmArgs {
   int N, Kp, Q, S;
   int num_sms;
   int* err;             // device error word (0 = ok)
+  int bn;               // output tile width (32 or 48; 0 = default 48)
 };
+
+// problems per grouped launch (their tensor maps travel in the kernel parameters)
+#define NSPT_SPLIT_MAX_PROBLEMS 64
 
 int nspt_split_gemm_init();
 int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st);
+// one persistent launch over the tiles of `count` problems (same S); err of a[0] is used
+int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int num_sms, cudaStream_t st);

@@ -1,0 +1,124 @@
+"""Grouped products of uneven (N, T): one persistent tensor-core launch for all
+mode GEMMs (split form), CUDA-graph capture, and the tile-width autotuner."""
+import ctypes
+import math
+import os
+import tempfile
+
+import numpy as np
+import pytest
+import torch
+
+import nspt_synth as syn
+from oracle import polymat as pm
+
+from tests.gpu_util import dev, host, max_order_rel
+
+pytestmark = pytest.mark.gpu
+
+
+def bound(S, N):
+    return 2.0 ** 10 * math.sqrt(N) * (2.0 ** -(8 * S - 1) + 2.0 ** -44)
+
+
+@pytest.fixture(scope="module")
+def nspt():
+    import paper_2001_02835_b300 as n
+    assert n.lib().nspt_init() == 0
+    return n
+
+
+def make_group(seed, sizes):
+    g = syn.rng(seed)
+    As, Bs = [], []
+    for N, T, b in sizes:
+        As.append(syn.series_batch(g, N, T, b))
+        Bs.append(syn.series_batch(g, N, T, b))
+    return As, Bs
+
+
+SIZES = [(9, 8, 2), (49, 15, 1), (17, 3, 3), (64, 7, 1), (33, 31, 1), (5, 0, 2)]
+
+
+def test_grouped_split_matches_oracle_and_single_calls(nspt):
+    As, Bs = make_group(6000, SIZES)
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    Cs = nspt.polymat_mul_grouped(dA, dB, prec="split")
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        got = host(Cs[i])
+        assert max_order_rel(got, pm.star(A, B)) <= bound(6, A.shape[-1]), SIZES[i]
+        single = host(nspt.polymat_mul(dA[i], dB[i], algo="fft", prec="split"))
+        np.testing.assert_array_equal(got, single)   # same tiles, same accumulation order
+
+
+def test_grouped_fp64_matches_single_calls(nspt):
+    As, Bs = make_group(6100, SIZES[:4])
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    Cs = nspt.polymat_mul_grouped(dA, dB, prec="fp64")
+    for i in range(len(As)):
+        np.testing.assert_array_equal(host(Cs[i]), host(nspt.polymat_mul(dA[i], dB[i], algo="fft", prec="fp64")))
+        assert max_order_rel(host(Cs[i]), pm.star(As[i], Bs[i])) <= 1e-12
+
+
+def test_grouped_split_cuda_graph_replay(nspt):
+    As, Bs = make_group(6200, SIZES)
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    eager = [host(c) for c in nspt.polymat_mul_grouped(dA, dB, prec="split")]
+    Cs = [torch.empty_like(a) for a in dA]
+    nspt.polymat_mul_grouped(dA, dB, Cs, prec="split")       # workspace cached before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        nspt.polymat_mul_grouped(dA, dB, Cs, prec="split")
+    for C in Cs:
+        C.zero_()
+    graph.replay()
+    graph.replay()
+    for i in range(len(Cs)):
+        np.testing.assert_array_equal(host(Cs[i]), eager[i])
+
+
+def test_autotuner_picks_a_width_and_caches_it(nspt):
+    As, Bs = make_group(6300, [(121, 15, 1), (49, 31, 1), (169, 15, 1)])
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    path = os.path.join(tempfile.mkdtemp(), "nspt_tiles.txt")
+    bn = nspt.autotune_grouped(dA, dB, cache_path=path)
+    assert bn in (32, 48)
+    lines = open(path).read().split("\n")
+    assert any(l.endswith(" %d" % bn) for l in lines)
+    assert nspt.autotune_grouped(dA, dB, cache_path=path) == bn   # read back from the cache
+    assert len([l for l in open(path).read().split("\n") if l]) == 1
+    Cs = nspt.polymat_mul_grouped(dA, dB, prec="split")
+    for i in range(3):
+        assert max_order_rel(host(Cs[i]), pm.star(As[i], Bs[i])) <= bound(6, As[i].shape[-1])
+
+
+@pytest.mark.parametrize("bn_first", [32, 48])
+def test_both_tile_widths_are_correct(nspt, bn_first):
+    """Force each width through the autotuner's table (cache file) and check parity."""
+    sizes = [(47, 7, 1), (100, 3, 2)]
+    As, Bs = make_group(6400 + bn_first, sizes)
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    arr = nspt._group_descs(dA, dB, [torch.empty_like(a) for a in dA])
+    path = os.path.join(tempfile.mkdtemp(), "forced.txt")
+    # signature of this group with 6 slices: "S6;N x (batch*M)..."
+    sig = "S6" + "".join(";%dx%d" % (N, b * (1 << math.ceil(math.log2(2 * (T + 1))))) for N, T, b in sizes)
+    open(path, "w").write("%s %d\n" % (sig, bn_first))
+    assert nspt.autotune_grouped(dA, dB, cache_path=path) == bn_first
+    Cs = nspt.polymat_mul_grouped(dA, dB, prec="split")
+    for i in range(len(sizes)):
+        assert max_order_rel(host(Cs[i]), pm.star(As[i], Bs[i])) <= bound(6, sizes[i][0])
+    del arr
+
+
+def test_grouped_argument_checks(nspt):
+    L = nspt.lib()
+    x = torch.zeros((1, 2, 3, 3), dtype=torch.complex128, device="cuda")
+    y, z = torch.zeros_like(x), torch.zeros_like(x)
+    arr = nspt._group_descs([x], [y], [z])
+    o = nspt.make_opts(algo="fft", prec="split", fft_len=8)
+    assert L.nspt_polymat_mul_grouped(arr, 1, ctypes.byref(o), None) == -1      # per-product M only
+    o = nspt.make_opts(algo="fft", prec="split")
+    assert L.nspt_polymat_mul_grouped(arr, 65, ctypes.byref(o), None) == -1     # more than 64 products
+    arr2 = nspt._group_descs([x], [y], [x])
+    assert L.nspt_polymat_mul_grouped(arr2, 1, ctypes.byref(o), None) == -2     # C overlaps A
