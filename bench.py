@@ -231,6 +231,37 @@ def fp64_peak_tflops(torch):
     return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
+GROUP_N = (49, 121, 169, 225, 289)
+GROUP_T = (15, 31, 63)
+
+
+def grouped_leg(torch, nspt, barrier, count=64, reps=5):
+    """64 independent products, N from {49,121,169,225,289}, T from {15,31,63} (seeded),
+    split form, tile width from the autotuner, one CUDA graph replayed per step."""
+    g = syn.rng(syn.SEED_BASE + 3)
+    Ns = g.choice(GROUP_N, count)
+    Ts = g.choice(GROUP_T, count)
+    As, Bs = [], []
+    for N, T in zip(Ns, Ts):
+        A, B = inputs(int(N), int(T), 1, int(g.integers(1 << 30)))
+        As.append(torch.from_numpy(A).cuda())
+        Bs.append(torch.from_numpy(B).cuda())
+    Cs = [torch.empty_like(A) for A in As]
+    bn = nspt.autotune_grouped(As, Bs, cache_path=os.path.join(tempfile.gettempdir(), "nspt_tiles.txt"))
+    nspt.polymat_mul_grouped(As, Bs, Cs, prec="split")
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        nspt.polymat_mul_grouped(As, Bs, Cs, prec="split")
+    ms_graph = time_steps(torch, graph.replay, reps, 2, barrier) / reps
+    ms_eager = time_steps(torch, lambda: nspt.polymat_mul_grouped(As, Bs, Cs, prec="split"), reps, 1, barrier) / reps
+    flops = sum(fft_flops(int(N), 1 << math.ceil(math.log2(2 * (int(T) + 1)))) for N, T in zip(Ns, Ts))
+    del graph, As, Bs, Cs
+    return {"products": count, "tile_width": bn, "ms_per_group_graph": ms_graph, "ms_per_group_eager": ms_eager,
+            "products_per_s": count / (ms_graph * 1e-3), "eff_tflops": flops / (ms_graph * 1e-3) / 1e12,
+            "sizes": "N ~ U{49,121,169,225,289}, T ~ U{15,31,63}, seed 200102838"}
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -369,6 +400,7 @@ def run_ours(args):
             ms31 = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="fft", prec=p), 3, 1, barrier)
             extras["%s_fft_T31" % p] = {"products_per_s": BATCH * 3 / (ms31 * 1e-3), "ms_per_step": ms31 / 3,
                                         "eff_tflops": fft_flops(N, 64) * BATCH * 3 / (ms31 * 1e-3) / 1e12}
+        extras["grouped_64_uneven"] = grouped_leg(torch, nspt, barrier)
         msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
         extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
