@@ -182,6 +182,7 @@ int pair_index(int a, int b) {  // a < b
 int ordered_index(int mu, int nu) { return mu * 3 + (nu < mu ? nu : nu - 1); }  // 0..11
 
 size_t ws_langevin(const Plan& p) {
+  if (p.prec == NSPT_PREC_SPLIT) return nspt_split_ws_langevin(p.N, p.T, p.batch, p.M, p.slices);
   const long long E = p.E;
   const long long T1 = p.T + 1, M = p.M;
   size_t mats;

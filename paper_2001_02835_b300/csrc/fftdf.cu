@@ -95,10 +95,20 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
 
 // in: [batch][M][E] float4 spectrum; out: FP64 orders 0..T at out + b*out_stride*E,
 // row k scaled by 2^(log2u - k*log2r) / M
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  const float p = a.h * b.h;
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  return df_fast(p, e);
+}
+
+// post: extra real double-float factor (1/n of Horner); add_identity: + 1 on the
+// diagonal of order 0 (entry e is (e / N, e % N)); orders below kmin are not stored
 template <int M, int EB>
 __global__ void __launch_bounds__(EB * 8)
 fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long long out_stride, int E, int T,
-                  int log2u, int log2r) {
+                  int log2u, int log2r, float post_h, float post_l, int add_identity, int N, int kmin) {
   extern __shared__ float4 sm[];
   const int e = threadIdx.x, y = threadIdx.y, b = blockIdx.y;
   const long long e0 = (long long)blockIdx.x * EB;
@@ -128,7 +138,11 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   if (!valid) return;
   double2* dst = out + (long long)b * out_stride * E + e0 + e;
   constexpr int LOGM = 31 - __builtin_clz(M);
+  const long long ent = e0 + e;
+  const bool diag = add_identity && (ent / N) == (ent % N);
+  const bool scaled = !(post_h == 1.f && post_l == 0.f);
   for (int k = y; k <= T; k += 8) {
+    if (k < kmin) continue;
     const cdf u = ld(&sm[k * EB + e]);
     cdf v = ld(&sm[(k + M / 2) * EB + e]);
     if (k != 0) {
@@ -140,6 +154,8 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
     float f1, f2;
     pow2_pair(log2u - k * log2r - LOGM, f1, f2);
     r = cdf{df_scale(df_scale(r.re, f1), f2), df_scale(df_scale(r.im, f1), f2)};
+    if (scaled) r = cdf{df_mul(r.re, dfl{post_h, post_l}), df_mul(r.im, dfl{post_h, post_l})};
+    if (diag && k == 0) r.re = df_add(r.re, dfl{1.f, 0.f});
     dst[(long long)k * E] = make_double2(df_to_double(r.re), df_to_double(r.im));
   }
 }
@@ -162,14 +178,14 @@ cudaError_t launch_fwd(const double2* in, long long ins, float4* out, int E, int
 
 template <int M>
 cudaError_t launch_inv(const float4* in, double2* out, long long outs, int E, int T, int batch, int lu, int lr,
-                       cudaStream_t st) {
+                       float ph, float pl, int addi, int N, int kmin, cudaStream_t st) {
   constexpr int EB = strip_entries<M>();
   const size_t smem = (size_t)M * EB * sizeof(float4);
   auto kern = fft_inv_df_kernel<M, EB>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, out, outs, E, T, lu, lr);
+  kern<<<grid, block, smem, st>>>(in, out, outs, E, T, lu, lr, ph, pl, addi, N, kmin);
   return cudaGetLastError();
 }
 
@@ -189,11 +205,13 @@ cudaError_t nspt_fft_fwd_df(const double2* in, long long in_stride, float4* out,
 }
 
 cudaError_t nspt_fft_inv_df(const float4* in, double2* out, long long out_stride, int E, int t, int batch, int M,
-                            int log2u, int log2r, cudaStream_t st) {
+                            int log2u, int log2r, cudaStream_t st, double post, int add_identity, int N, int kmin) {
   if (2 * (t + 1) > M) return cudaErrorInvalidValue;
+  if (add_identity && N < 1) return cudaErrorInvalidValue;
+  const float ph = (float)post, pl = (float)(post - (double)ph);
   ProfScope ps(NSPT_STAGE_FFT_INV, st);
   switch (M) {
-#define NSPT_CASE(m) case m: return launch_inv<m>(in, out, out_stride, E, t, batch, log2u, log2r, st);
+#define NSPT_CASE(m) case m: return launch_inv<m>(in, out, out_stride, E, t, batch, log2u, log2r, ph, pl, add_identity, (N > 0 ? N : 1), kmin, st);
     NSPT_CASE(2) NSPT_CASE(4) NSPT_CASE(8) NSPT_CASE(16) NSPT_CASE(32) NSPT_CASE(64) NSPT_CASE(128)
     NSPT_CASE(256) NSPT_CASE(512)
 #undef NSPT_CASE

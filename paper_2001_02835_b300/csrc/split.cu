@@ -25,6 +25,7 @@
 #include "split_gemm.cuh"
 #include "zgemm64.cuh"
 #include "dfloat.cuh"
+#include "tek.cuh"
 
 namespace {
 
@@ -237,6 +238,7 @@ SplitGemmArgs gemm_args(const SplitWs& w, int N, int Q, int S) {
   SplitGemmArgs a;
   a.slicesA = w.slA; a.slicesB = w.slB; a.expA = w.expA; a.expB = w.expB; a.C = w.Ct;
   a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
+  a.alpha = make_double2(1.0, 0.0); a.use_alpha = 0; a.accumulate = 0;
   return a;
 }
 
@@ -338,16 +340,12 @@ int nspt_split_bwd(int N, int T, int batch, int M, int S, int log2r, const doubl
   return NSPT_OK;
 }
 
-int nspt_split_langevin(int, int, int, int, int, double2*, const double2*, double2*, int, double, void*,
-                        cudaStream_t) {
-  return NSPT_ERR_UNSUPPORTED;
-}
-
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st) {
   SplitGemmArgs a;
   a.slicesA = slA; a.slicesB = slB; a.expA = expA; a.expB = expB; a.C = (float4*)C;
-  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = err;
+  a.N = N; a.Kp = kpad(N); a.Q = Q; a.S = S; a.num_sms = g_num_sms; a.err = err; a.bn = 0;
+  a.alpha = make_double2(1.0, 0.0); a.use_alpha = 0; a.accumulate = 0;
   return nspt_split_gemm(a, st);
 }
 
@@ -497,5 +495,221 @@ int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, vo
     }
   }
   *chosen = best_bn;
+  return NSPT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Langevin step of the TEK model in the split form (Eqs. 1-3): the same
+// sequence of star products as the FP64 form, with double-float spectra,
+// digit slices and tensor-core mode GEMMs.  Spectra of daggered series come
+// from the spectra of the series themselves: FFT(X^+)_p = (X~_{(M-p) mod M})^H,
+// realised by the slicer's reversal, transposition and conjugation.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SpecRef {
+  const float4* p;  // batch element b, mode m at p + (b * bs + m) * N^2
+  long long bs;
+  int dag;          // use (X~_{(M-p) mod M})^H
+};
+
+struct Job {
+  SpecRef a, b;
+  float4* c;        // [nb][M] output spectrum
+  double2 alpha;
+  int use_alpha, accumulate;
+};
+
+const int kPairsS[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+int pair_idx(int a, int b) {
+  for (int i = 0; i < 6; ++i)
+    if (kPairsS[i][0] == a && kPairsS[i][1] == b) return i;
+  return -1;
+}
+int ord_idx(int mu, int nu) { return mu * 3 + (nu < mu ? nu : nu - 1); }
+
+constexpr int kMaxJobs = 18;
+
+// X[s][0] += identity for every series s (stride in matrices)
+__global__ void identity_order0_kernel(double2* X, long long stride_mats, int N, long long count) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count * N) return;
+  const long long s = i / N;
+  const int d = (int)(i % N);
+  X[s * stride_mats * N * N + (long long)d * N + d].x += 1.0;
+}
+
+cudaError_t set_identity_order0(double2* X, long long stride_mats, int N, long long count, cudaStream_t st) {
+  const long long n = count * N;
+  if (n == 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  identity_order0_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(X, stride_mats, N, count);
+  return cudaGetLastError();
+}
+
+struct LangevinWs {
+  int* err;
+  float4 *specU, *specAcc, *specPQ, *specIn, *spY, *spR, *spC;
+  double2 *serTmp, *serS, *serY, *serR[2];
+  double* imtr;
+  __nv_bfloat16 *slA[kMaxJobs], *slB[kMaxJobs];
+  int *expA[kMaxJobs], *expB[kMaxJobs];
+  size_t total;
+};
+
+LangevinWs carve_langevin(void* base, int N, int T, int nb, int M, int S) {
+  LangevinWs w;
+  WsCarver c(base, SIZE_MAX);
+  const long long E = (long long)N * N, T1 = T + 1;
+  const long long spec = (long long)nb * M * E, ser = (long long)nb * T1 * E;
+  w.err = c.take<int>(64);
+  w.specU = c.take<float4>(4 * spec);
+  w.specAcc = c.take<float4>(18 * spec);
+  w.specPQ = c.take<float4>(18 * spec);
+  w.specIn = c.take<float4>(4 * spec);
+  w.spY = c.take<float4>(4 * spec);
+  w.spR = c.take<float4>(4 * spec);
+  w.spC = c.take<float4>(4 * spec);
+  w.serTmp = c.take<double2>(18 * ser);
+  w.serS = c.take<double2>(4 * ser);
+  w.serY = c.take<double2>(4 * ser);
+  w.serR[0] = c.take<double2>(4 * ser);
+  w.serR[1] = c.take<double2>(4 * ser);
+  w.imtr = c.take<double>(4 * nb * T1);
+  // per-job slices sized for Q = nb * M modes, one contiguous pool per kind; the
+  // exp_star product (one job of up to 4 nb M modes) uses the first four slots of each pool
+  const size_t Q = (size_t)nb * M;
+  const size_t sa = Q * S * 2 * N * kpad(N), sb = Q * S * 3 * N * kpad(N), se = Q * N;
+  __nv_bfloat16* poolA = c.take<__nv_bfloat16>(kMaxJobs * sa);
+  __nv_bfloat16* poolB = c.take<__nv_bfloat16>(kMaxJobs * sb);
+  int* poolEA = c.take<int>(kMaxJobs * se);
+  int* poolEB = c.take<int>(kMaxJobs * se);
+  for (int j = 0; j < kMaxJobs; ++j) {
+    w.slA[j] = base ? poolA + j * sa : nullptr;
+    w.slB[j] = base ? poolB + j * sb : nullptr;
+    w.expA[j] = base ? poolEA + j * se : nullptr;
+    w.expB[j] = base ? poolEB + j * se : nullptr;
+  }
+  w.total = c.off;
+  return w;
+}
+
+int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int M, int S, cudaStream_t st,
+             __nv_bfloat16* slA_big = nullptr, __nv_bfloat16* slB_big = nullptr, int* eA_big = nullptr,
+             int* eB_big = nullptr) {
+  std::vector<SplitGemmArgs> args;
+  std::vector<std::pair<int, int>> sig;
+  for (int j = 0; j < count; ++j) {
+    const Job& J = jobs[j];
+    __nv_bfloat16* sa = slA_big ? slA_big : w.slA[j];
+    __nv_bfloat16* sb = slB_big ? slB_big : w.slB[j];
+    int* ea = eA_big ? eA_big : w.expA[j];
+    int* eb = eB_big ? eB_big : w.expB[j];
+    // left operand: rows of A (dagger: conjugated columns of the reversed spectrum)
+    TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag, J.a.dag, N, nb * M, 2, sa, ea, st));
+    // right operand: rows of B^T (dagger: conjugated rows of the reversed spectrum)
+    TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, !J.b.dag, J.b.dag, N, nb * M, 3, sb, eb, st));
+    SplitGemmArgs a;
+    a.slicesA = sa; a.slicesB = sb; a.expA = ea; a.expB = eb; a.C = J.c;
+    a.N = N; a.Kp = kpad(N); a.Q = nb * M; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
+    a.alpha = J.alpha; a.use_alpha = J.use_alpha; a.accumulate = J.accumulate;
+    args.push_back(a);
+    sig.push_back({N, nb * M});
+  }
+  return nspt_split_gemm_batch(args.data(), count, S, choose_bn(signature(S, sig)), g_num_sms, st);
+}
+
+}  // namespace
+
+size_t nspt_split_ws_langevin(int N, int T, int nb, int M, int S) {
+  return carve_langevin(nullptr, N, T, nb, M, S).total;
+}
+
+int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const double2* eta, double2* F, int flux,
+                        double eps, void* ws, cudaStream_t st) {
+  const int E = N * N;
+  const long long T1 = T + 1;
+  const long long specE = (long long)M * E;  // one spectrum
+  const int L = (int)llround(sqrt((double)N));
+  double2 z[4][4];
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = 0; nu < 4; ++nu) {
+      const double ang = 2.0 * M_PI * flux * (mu < nu ? 1.0 : -1.0) / L;
+      z[mu][nu] = (mu == nu) ? make_double2(0, 0) : make_double2(cos(ang), sin(ang));
+    }
+  LangevinWs w = carve_langevin(ws, N, T, nb, M, S);
+  TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  // 1. spectra of the four links, [nb][4][M]
+  TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, 0, st));
+  auto link = [&](int mu, int dag) { return SpecRef{w.specU + mu * specE, 4LL * M, dag}; };
+  auto slot = [&](float4* base, int s) { return base + (long long)s * nb * specE; };
+  // 2. P1(mu,nu) = U_nu U_mu^+ (mu < nu) and Q(mu,nu) = U_mu U_nu: one launch of 18 products
+  Job jobs[kMaxJobs];
+  for (int i = 0; i < 6; ++i) {
+    const int mu = kPairsS[i][0], nu = kPairsS[i][1];
+    jobs[i] = Job{link(nu, 0), link(mu, 1), slot(w.specAcc, i), make_double2(1, 0), 0, 0};
+  }
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = 0; nu < 4; ++nu)
+      if (mu != nu)
+        jobs[6 + ord_idx(mu, nu)] = Job{link(mu, 0), link(nu, 0), slot(w.specAcc, 6 + ord_idx(mu, nu)),
+                                        make_double2(1, 0), 0, 0};
+  TRYS(run_jobs(w, jobs, 18, N, nb, M, S, st));
+  // truncate (Step 5) and return to the frequency domain
+  TRYC(nspt_fft_inv_df(w.specAcc, w.serTmp, T1, E, T, 18 * nb, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specPQ, E, T, 18 * nb, M, 0, 0, st));
+  auto pq = [&](int s, int dag) { return SpecRef{slot(w.specPQ, s), (long long)M, dag}; };
+  // 3. inner_mu = sum_nu z P1(mu,nu) U_nu^+ + conj(z) Q(mu,nu)^+ U_nu, six accumulating terms
+  for (int tt = 0; tt < 6; ++tt) {
+    for (int mu = 0; mu < 4; ++mu) {
+      const int k = tt / 2;
+      const int nu = k < mu ? k : k + 1;  // k-th neighbour of mu
+      Job& J = jobs[mu];
+      if (tt % 2 == 0) {
+        J.a = (mu < nu) ? pq(pair_idx(mu, nu), 0) : pq(pair_idx(nu, mu), 1);
+        J.b = link(nu, 1);
+        J.alpha = z[mu][nu];
+      } else {
+        J.a = pq(6 + ord_idx(mu, nu), 1);
+        J.b = link(nu, 0);
+        J.alpha = make_double2(z[mu][nu].x, -z[mu][nu].y);
+      }
+      J.c = slot(w.specIn, mu);
+      J.use_alpha = 1;
+      J.accumulate = tt > 0;
+    }
+    TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
+  }
+  TRYC(nspt_fft_inv_df(w.specIn, w.serTmp, T1, E, T, 4 * nb, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specIn, E, T, 4 * nb, M, 0, 0, st));
+  // 4. S_mu = U_mu inner_mu
+  for (int mu = 0; mu < 4; ++mu)
+    jobs[mu] = Job{link(mu, 0), SpecRef{slot(w.specIn, mu), (long long)M, 0}, slot(w.specAcc, mu),
+                   make_double2(1, 0), 0, 0};
+  TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
+  for (int mu = 0; mu < 4; ++mu)
+    TRYC(nspt_fft_inv_df(slot(w.specAcc, mu), w.serS + mu * T1 * E, 4 * T1, E, T, nb, M, 0, 0, st));
+  // 5. drift and Y = i X
+  TRYC(nspt_tek_drift(w.serS, w.imtr, eta, F, w.serY, N, T, (long long)nb * 4, eps, st));
+  // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
+  TRYC(cudaMemsetAsync(w.serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+  TRYC(cudaMemsetAsync(w.serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
+  TRYC(set_identity_order0(w.serR[0], T1, N, (long long)nb * 4, st));
+  int cur = 0;
+  for (int n = T; n >= 1; --n) {
+    const int t = T - n + 1;
+    const int Mt = 1 << (int)ceil(log2(2.0 * (t + 1)));
+    TRYC(nspt_fft_fwd_df(w.serY, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
+    TRYC(nspt_fft_fwd_df(w.serR[cur], T1, w.spR, E, t - 1, nb * 4, Mt, 0, 0, st));
+    Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0}, w.spC, make_double2(1, 0), 0, 0};
+    TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
+    TRYC(nspt_fft_inv_df(w.spC, w.serR[cur ^ 1], T1, E, t, nb * 4, Mt, 0, 0, st, 1.0 / n, 1, N));
+    cur ^= 1;
+  }
+  // 7. U <- exp_star(i X) U, order 0 untouched
+  TRYC(nspt_fft_fwd_df(w.serR[cur], T1, w.spR, E, T, nb * 4, M, 0, 0, st));
+  Job J{SpecRef{w.spR, (long long)M, 0}, SpecRef{w.specU, (long long)M, 0}, w.spC, make_double2(1, 0), 0, 0};
+  TRYS(run_jobs(w, &J, 1, N, nb * 4, M, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
+  TRYC(nspt_fft_inv_df(w.spC, U, T1, E, T, nb * 4, M, 0, 0, st, 1.0, 0, N, 1));
   return NSPT_OK;
 }

@@ -26,3 +26,4 @@ size_t nspt_split_ws_grouped(const nspt_polymat_desc* d, int count, int S);
 int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log2r, void* ws, cudaStream_t st);
 int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,
                                 int* chosen, cudaStream_t st);
+size_t nspt_split_ws_langevin(int N, int T, int nb, int M, int S);

@@ -32,6 +32,7 @@
 #include "prof.cuh"
 #include "split_gemm.cuh"
 #include "tc_ptx.cuh"
+#include "dfloat.cuh"
 
 #include <cstring>
 #include <memory>
@@ -54,6 +55,8 @@ struct alignas(64) GemmProblem {
   float4* C;
   int N, Q, tilesM, tilesN;
   long long tile_begin;  // first global tile index of this problem
+  float4 alpha;          // C = alpha * A B (+ C): (re_hi, re_lo, im_hi, im_lo)
+  int use_alpha, accumulate;
 };
 
 template <int MAXP>
@@ -302,7 +305,17 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           const int k = ea + eb - 14;
           const int k1 = k / 2, k2 = k - k1;
           const float f1 = pow2f(k1), f2 = pow2f(k2);
-          crow[n] = make_float4(rh * f1 * f2, rl * f1 * f2, ih * f1 * f2, il * f1 * f2);
+          if (!P.use_alpha && !P.accumulate) {
+            crow[n] = make_float4(rh * f1 * f2, rl * f1 * f2, ih * f1 * f2, il * f1 * f2);
+          } else {
+            cdf v{dfl{rh * f1 * f2, rl * f1 * f2}, dfl{ih * f1 * f2, il * f1 * f2}};
+            if (P.use_alpha) v = cdf_mul(v, dfl{P.alpha.x, P.alpha.y}, dfl{P.alpha.z, P.alpha.w});
+            if (P.accumulate) {
+              const float4 o = crow[n];
+              v = cdf_add(v, cdf{dfl{o.x, o.y}, dfl{o.z, o.w}});
+            }
+            crow[n] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+          }
         }
       }
       tc::fence_before_sync();
@@ -351,6 +364,12 @@ int launch(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
     P.tilesM = (a[i].N + BM - 1) / BM;
     P.tilesN = (a[i].N + BN - 1) / BN;
     P.tile_begin = tiles;
+    P.use_alpha = a[i].use_alpha;
+    P.accumulate = a[i].accumulate;
+    {
+      const float rh = (float)a[i].alpha.x, ih = (float)a[i].alpha.y;
+      P.alpha = make_float4(rh, (float)(a[i].alpha.x - (double)rh), ih, (float)(a[i].alpha.y - (double)ih));
+    }
     tiles += (long long)a[i].Q * P.tilesM * P.tilesN;
   }
   gb->count = count;

@@ -11,6 +11,8 @@ struct SplitGemmArgs {
   int num_sms;
   int* err;             // device error word (0 = ok)
   int bn;               // output tile width (32 or 48; 0 = default 48)
+  double2 alpha;        // C = alpha * A B (+ C) when use_alpha / accumulate
+  int use_alpha, accumulate;
 };
 
 // problems per grouped launch (their tensor maps travel in the kernel parameters)

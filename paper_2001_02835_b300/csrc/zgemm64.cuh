@@ -40,4 +40,5 @@ cudaError_t nspt_fft_inv64_df(const float4* in, double2* out, long long out_stri
 cudaError_t nspt_fft_fwd_df(const double2* in, long long in_stride, float4* out, int E, int t, int batch, int M,
                             int log2s, int log2r, cudaStream_t st);
 cudaError_t nspt_fft_inv_df(const float4* in, double2* out, long long out_stride, int E, int t, int batch, int M,
-                            int log2u, int log2r, cudaStream_t st);
+                            int log2u, int log2r, cudaStream_t st, double post = 1.0, int add_identity = 0,
+                            int N = 0, int kmin = 0);

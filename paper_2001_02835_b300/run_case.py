@@ -12,6 +12,7 @@ import argparse
 import os
 import sys
 
+import numpy as np
 import torch
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -41,8 +42,8 @@ def main(argv=None):
     kw = dict(algo=a.algo, prec=a.prec, slices=a.slices)
     if a.op == "langevin":
         L = int(round(a.N ** 0.5))
-        U = torch.from_numpy(syn.link_series(g, L, 1, a.T, a.batch)).cuda()
-        eta = torch.from_numpy(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N)).cuda()
+        U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
+        eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
         fn = lambda: nspt.tek_langevin_step(U, eta, 1, 0.01, **kw)  # noqa: E731
     else:
         A = torch.from_numpy(syn.series_batch(g, a.N, a.T, a.batch)).cuda()

@@ -19,9 +19,9 @@ def nspt():
     return n
 
 
-@pytest.mark.parametrize("algo", ["naive", "fft"])
+@pytest.mark.parametrize("algo,prec", [("naive", "fp64"), ("fft", "fp64"), ("fft", "split")])
 @pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 8, 1), (3, 1, 2, 2), (2, 1, 5, 1), (5, 2, 4, 2)])
-def test_langevin_step_matches_oracle(nspt, algo, L, flux, T, streams):
+def test_langevin_step_matches_oracle(nspt, algo, prec, L, flux, T, streams):
     g = syn.rng(syn.SEED_BASE + 10 * L + T)
     N = L * L
     U = syn.link_series(g, L, flux, T, streams)
@@ -33,12 +33,13 @@ def test_langevin_step_matches_oracle(nspt, algo, L, flux, T, streams):
     for s in range(streams):
         refU[s], refF[s] = tek.langevin_step(U[s], eta[s], z, eps)
     tU = dev(U)
-    _, F = nspt.tek_langevin_step(tU, dev(eta), flux, eps, want_drift=True, algo=algo)
+    _, F = nspt.tek_langevin_step(tU, dev(eta), flux, eps, want_drift=True, algo=algo, prec=prec)
     gotU = host(tU)
     gotF = host(F)
+    tol = TOL if prec == "fp64" else 2.0 ** 10 * np.sqrt(L * L) * (2.0 ** -47 + 2.0 ** -44)
     # F^(0) vanishes at the twist-eater vacuum: compare with an absolute floor
-    assert np.abs(gotF - refF).max() <= 1e-12 * max(1.0, np.abs(refF).max())
-    assert max_order_rel(gotU, refU) <= TOL
+    assert np.abs(gotF - refF).max() <= tol * max(1.0, np.abs(refF).max())
+    assert max_order_rel(gotU, refU) <= tol
     np.testing.assert_array_equal(gotU[:, :, 0], U[:, :, 0])
 
 

@@ -154,3 +154,16 @@ def test_langevin_step_with_backward_drift(nspt, c4):
     nspt.tek_langevin_step(U1, eta, FLUX, EPS, algo="fft")
     assert per_order_err(Uc[:, :, 1:], U1[:, :, 1:]) <= 1e-10
     assert torch.equal(U1[:, :, 0], tU[:, :, 0])
+
+
+def test_split_langevin_step_matches_fp64_form(nspt, c4):
+    """The split-precision Langevin step (tensor-core staples and exp_star) against the FP64
+    form at SU(121), O(g^31), 8 streams; stated bound 2^10 sqrt(N) (2^-47 + 2^-44)."""
+    eta = dev(c4["eta"])
+    U64, Us = c4["tU"].clone(), c4["tU"].clone()
+    _, F64 = nspt.tek_langevin_step(U64, eta, FLUX, EPS, want_drift=True, algo="fft", prec="fp64")
+    _, Fs = nspt.tek_langevin_step(Us, eta, FLUX, EPS, want_drift=True, algo="fft", prec="split")
+    tol = 2.0 ** 10 * math.sqrt(N) * (2.0 ** -47 + 2.0 ** -44)
+    assert per_order_err(Fs, F64) <= tol
+    assert per_order_err(Us[:, :, 1:], U64[:, :, 1:]) <= tol
+    assert torch.equal(Us[:, :, 0], c4["tU"][:, :, 0])
