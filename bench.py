@@ -262,6 +262,31 @@ def grouped_leg(torch, nspt, barrier, count=64, reps=5):
             "sizes": "N ~ U{49,121,169,225,289}, T ~ U{15,31,63}, seed 200102838"}
 
 
+def langevin_leg(torch, nspt, barrier, L=11, T=31, streams=8, flux=3, eps=0.01):
+    """One NSPT Langevin step of 8 streams x 4 links at SU(121), O(g^31), flux 3, both forms,
+    with the oracle's step on one stream timed on the host cores beside it."""
+    from oracle import tek
+    g = syn.rng(syn.SEED_BASE + 4)
+    N = L * L
+    U = np.ascontiguousarray(syn.link_series(g, L, flux, T, streams))
+    eta = np.ascontiguousarray(syn.hermitian_noise(g, N, streams * 4).reshape(streams, 4, N, N))
+    tU0, tE = torch.from_numpy(U).cuda(), torch.from_numpy(eta).cuda()
+    out = {}
+    for p in ("split", "fp64"):
+        tU = tU0.clone()
+        reps = 5 if p == "split" else 1
+        ms = time_steps(torch, lambda: nspt.tek_langevin_step(tU, tE, flux, eps, algo="fft", prec=p), reps, 1,
+                        barrier) / reps
+        out["%s_ms_per_step" % p] = ms
+        out["%s_link_updates_per_s" % p] = streams * 4 / (ms * 1e-3)
+    t0 = time.perf_counter()
+    tek.langevin_step(U[0], eta[0], tek.twist_phases(L, flux), eps)
+    out["oracle_ms_per_stream"] = 1e3 * (time.perf_counter() - t0)
+    out["oracle_cores"] = oracle_threads()
+    del tU0, tE
+    return out
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -401,6 +426,14 @@ def run_ours(args):
             extras["%s_fft_T31" % p] = {"products_per_s": BATCH * 3 / (ms31 * 1e-3), "ms_per_step": ms31 / 3,
                                         "eff_tflops": fft_flops(N, 64) * BATCH * 3 / (ms31 * 1e-3) / 1e12}
         extras["grouped_64_uneven"] = grouped_leg(torch, nspt, barrier)
+        gC = torch.from_numpy(syn.gaussian(syn.rng(syn.SEED_BASE + 9), A.shape, 1.0)).cuda()
+        for p in ("split", "fp64"):
+            reps = 5 if p == "split" else 2
+            msb = time_steps(torch, lambda: nspt.polymat_mul_backward(dA, dB, gC, algo="fft", prec=p), reps, 1,
+                             barrier) / reps
+            extras["backward_%s_T%d" % (p, T)] = {"ms_per_batch": msb, "products_per_s": BATCH / (msb * 1e-3)}
+        del gC
+        extras["langevin_su121_T31_8streams"] = langevin_leg(torch, nspt, barrier)
         msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
         extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
