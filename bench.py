@@ -68,6 +68,25 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_seed(rank):
+    """Each rank of an N-GPU run multiplies its own batch (independent products)."""
+    return syn.SEED_BASE + 2 + 1000 * rank
+
+
+def max_over_ranks(value, dist, device):
+    """The slowest rank's time (the job finishes when the last replica does)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second of the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def inputs(N, T, batch, seed):
     g = syn.rng(seed)
     return syn.series_batch(g, N, T, batch), syn.series_batch(g, N, T, batch)
@@ -326,7 +345,7 @@ def run_ours(args):
     N, T = args.N, args.T
     M = 1 << math.ceil(math.log2(2 * (T + 1)))
     prec = args.prec or "split"
-    A, B = inputs(N, T, BATCH, syn.SEED_BASE + 2 + 1000 * rank)
+    A, B = inputs(N, T, BATCH, replica_seed(rank))
     dA = torch.from_numpy(A).cuda()
     dB = torch.from_numpy(B).cuda()
     dC = torch.empty_like(dA)
@@ -352,12 +371,9 @@ def run_ours(args):
     stages = nspt.profile_end()
     launches = nspt.launch_count() - l0
     clocks = clk.summary()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / args.steps
-    value = ws * BATCH * args.steps / (ms * 1e-3)
+    value = whole_job_rate(BATCH * args.steps, ws, ms)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     hA = torch.from_numpy(A).pin_memory()
@@ -372,10 +388,7 @@ def run_ours(args):
 
     e2e_steps = max(3, args.steps // 2)
     ms_e2e = time_steps(torch, e2e_step, e2e_steps, 1, barrier)
-    t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = ws * BATCH * e2e_steps / (float(t.item()) * 1e-3)
+    e2e_value = whole_job_rate(BATCH * e2e_steps, ws, max_over_ranks(ms_e2e, dist, "cuda"))
     nbytes = A.nbytes
 
     peaks, peak_kind = measured_peaks()
