@@ -22,7 +22,8 @@
 // 2^(e_A[m] + e_B[n] - 14) and writes float4 (re_hi, re_lo, im_hi, im_lo).
 //
 // Roles (one CTA per SM, persistent over tiles): warp 0 lane 0 issues TMA
-// loads, warp 1 lane 0 issues tcgen05.mma, warps 2-5 drain TMEM.  Per K block
+// loads, warp 1 lane 0 issues tcgen05.mma, warps 2-9 drain TMEM (two per lane
+// quarter, each half of the columns).  Per K block
 // of 32, all S slices of the B tile (re, im, -re) are loaded once and the A
 // slices stream through a 4-stage ring; the triangle of slice pairs
 // i + j < S is issued against the resident B slices.  Every wait is bounded
@@ -48,7 +49,7 @@ constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
 // One problem of a (possibly grouped) launch; all of them travel in the kernel
 // parameters, so a launch needs no device-side table and can be captured.
-struct alignas(64) GemmProblem {
+struct GemmProblem {  // aligned like its CUtensorMap members
   CUtensorMap mA, mB;    // slice planes of the left / right operand
   const int* expA;
   const int* expB;
@@ -120,7 +121,7 @@ __device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, flo
 }
 
 template <int S, int BN, int MAXP>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
 split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
   constexpr int NACC = 2 * BN;  // accumulator columns per group: (re | im)
   static_assert(NGROUPS * NACC <= (int)TMEM_COLS, "accumulators exceed TMEM");
@@ -135,7 +136,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     for (int s = 0; s < NA_STAGES; ++s) { tc::mbar_init(&sm.full_a[s], 1); tc::mbar_init(&sm.empty_a[s], 1); }
     for (int s = 0; s < 2; ++s) { tc::mbar_init(&sm.full_b[s], 1); tc::mbar_init(&sm.empty_b[s], 1); }
     tc::mbar_init(&sm.acc_full, 1);
-    tc::mbar_init(&sm.acc_empty, 128);
+    tc::mbar_init(&sm.acc_empty, 256);
     tc::mbar_init(&sm.drain, 1);
     sm.abort_flag = 0;
     tc::fence_mbar_init();
@@ -207,35 +208,44 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     int local = 0, pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x, ++local) {
       while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
-      const int nK = (gb.p[pi].N + KB - 1) / KB;
+      const int Nk = gb.p[pi].N;
+      const int nK = (Nk + KB - 1) / KB;
       if (local > 0) {
         if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
       }
       tc::fence_after_sync();
-      uint32_t started = 0;  // bit g: accumulator of group g already written in this tile
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
         tc::fence_after_sync();
+        // the last K block may hold no more than 16 valid columns: one K = 16 step then
+        const bool two_k = (Nk - kb * KB) > 16;
         for (int i = 0; i < S; ++i) {
           if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
           tc::fence_after_sync();
-          const uint32_t a_re = tc::smem_u32(sm.a[ia][0]), a_im = tc::smem_u32(sm.a[ia][1]);
-          for (int j = 0; j + i < S; ++j) {
+          // descriptors: start addresses differ only in bits 0-13, so they are formed once and
+          // advanced by adding (byte offset >> 4)
+          const uint64_t a_re = tc::desc_sw64(tc::smem_u32(sm.a[ia][0]));
+          const uint64_t a_im = tc::desc_sw64(tc::smem_u32(sm.a[ia][1]));
+          const uint64_t b_0 = tc::desc_sw64(tc::smem_u32(sm.b[ib][0][0]));
+          // in the first K block of a tile, the first pair of each group (i = 0, j = g for g < 4,
+          // and j = 4 for the merged group) overwrites its accumulator
+          const bool first = (kb == 0) && (i == 0);
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            if (j + i >= S) break;
             const int g = min(i + j, NGROUPS - 1);
             const uint32_t d = tmem + (uint32_t)(g * NACC);
-            const uint32_t b_re = tc::smem_u32(sm.b[ib][j][0]);  // rows [re; im]
-            const uint32_t b_im = tc::smem_u32(sm.b[ib][j][1]);  // rows [im; -re]
-#pragma unroll
-            for (int kk = 0; kk < KB / 16; ++kk) {
-              const uint32_t off = kk * 32;  // 16 bf16 = 32 bytes along K inside the 64-byte swizzle row
-              const uint32_t acc = (started >> g) & 1u;
-              tc::mma_f16(d, tc::desc_sw64(a_re + off), tc::desc_sw64(b_re + off), ID, acc);
-              tc::mma_f16(d, tc::desc_sw64(a_im + off), tc::desc_sw64(b_im + off), IDN, 1u);
-              started |= 1u << g;
-              any = true;
+            const uint64_t b_re = b_0 + (uint64_t)(j * 3 * (B_TILE >> 4));  // rows [re; im]
+            const uint64_t b_im = b_re + (B_TILE >> 4);                      // rows [im; -re]
+            tc::mma_f16(d, a_re, b_re, ID, (first && j < NGROUPS) ? 0u : 1u);
+            tc::mma_f16(d, a_im, b_im, IDN, 1u);
+            if (two_k) {  // second K = 16 step: 32 bytes further inside the 64-byte swizzle row
+              tc::mma_f16(d, a_re + 2, b_re + 2, ID, 1u);
+              tc::mma_f16(d, a_im + 2, b_im + 2, IDN, 1u);
             }
           }
+          any = true;
           tc::mma_commit(&sm.empty_a[ia]);
           if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
         }
@@ -255,62 +265,68 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     }
   } else if (warp >= 2) {
     // ------------------------------ epilogue ------------------------------
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31
+    // warps 2..9: warp w drains TMEM lanes 32*(w % 4) .. +31 (the quarter its
+    // rank within the warpgroup may access) and half of the tile's columns
+    const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;  // 0: columns [0, BN/2), 1: [BN/2, BN)
     const int row = quarter * 32 + lane;
     uint32_t pacc = 0;
     constexpr int G = S < NGROUPS ? S : NGROUPS;
+    constexpr int HALF = BN / 2;
     int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
       while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
       const GemmProblem& P = gb.p[pi];
       const int N = P.N;
       const long long lt = t - P.tile_begin;
-      const int q = (int)(lt / (P.tilesM * P.tilesN));
-      const int r = (int)(lt % (P.tilesM * P.tilesN));
-      const int m0 = (r / P.tilesN) * BM, n0 = (r % P.tilesN) * BN;
-      const int* __restrict__ expA = P.expA;
-      const int* __restrict__ expB = P.expB;
+      const int tm = P.tilesM, tn = P.tilesN;
+      const int q = (int)(lt / (tm * tn));
+      const int r = (int)(lt % (tm * tn));
+      const int m0 = (r / tn) * BM, n0 = (r % tn) * BN + half * HALF;
+      const int* __restrict__ expB = P.expB + (long long)q * N;
+      const bool plain = !P.use_alpha && !P.accumulate;
+      const bool use_alpha = P.use_alpha, accumulate = P.accumulate;
+      const float4 alpha = P.alpha;
+      const int m = m0 + row;
+      const bool mvalid = m < N;
+      const int ea = mvalid ? __ldg(P.expA + (long long)q * N + m) : 0;
+      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6)) break;
       pacc ^= 1;
       tc::fence_after_sync();
-      const int m = m0 + row;
-      const bool mvalid = m < N;
-      const int ea = mvalid ? __ldg(expA + (long long)q * N + m) : 0;
-      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
-      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + half * HALF;
 #pragma unroll 1
-      for (int ch = 0; ch < BN / 16; ++ch) {
-        float re[NGROUPS][16], im[NGROUPS][16];
+      for (int ch = 0; ch < HALF / 8; ++ch) {
+        float re[NGROUPS][8], im[NGROUPS][8];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-          tc::tmem_ld16(lane_base + (uint32_t)(g * NACC) + ch * 16, re[g]);
-          tc::tmem_ld16(lane_base + (uint32_t)(g * NACC + BN) + ch * 16, im[g]);
+          tc::tmem_ld8(lane_base + (uint32_t)(g * NACC) + ch * 8, re[g]);
+          tc::tmem_ld8(lane_base + (uint32_t)(g * NACC + BN) + ch * 8, im[g]);
         }
         tc::tmem_wait_ld();
 #pragma unroll
         for (int g = G; g < NGROUPS; ++g)
 #pragma unroll
-          for (int c = 0; c < 16; ++c) { re[g][c] = 0.f; im[g][c] = 0.f; }
+          for (int c = 0; c < 8; ++c) { re[g][c] = 0.f; im[g][c] = 0.f; }
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int n = n0 + ch * 16 + c;
+        for (int c = 0; c < 8; ++c) {
+          const int n = n0 + ch * 8 + c;
           if (!mvalid || n >= N) continue;
-          const int eb = __ldg(expB + (long long)q * N + n);
           float ar[NGROUPS], ai[NGROUPS];
 #pragma unroll
           for (int g = 0; g < NGROUPS; ++g) { ar[g] = re[g][c]; ai[g] = im[g][c]; }
           float rh, rl, ih, il;
           df_sum(ar, rh, rl);
           df_sum(ai, ih, il);
-          const int k = ea + eb - 14;
+          const int k = ea + __ldg(expB + n) - 14;
           const int k1 = k / 2, k2 = k - k1;
-          const float f1 = pow2f(k1), f2 = pow2f(k2);
-          if (!P.use_alpha && !P.accumulate) {
-            crow[n] = make_float4(rh * f1 * f2, rl * f1 * f2, ih * f1 * f2, il * f1 * f2);
+          const float f = pow2f(k1) * pow2f(k2);
+          if (plain) {
+            crow[n] = make_float4(rh * f, rl * f, ih * f, il * f);
           } else {
-            cdf v{dfl{rh * f1 * f2, rl * f1 * f2}, dfl{ih * f1 * f2, il * f1 * f2}};
-            if (P.use_alpha) v = cdf_mul(v, dfl{P.alpha.x, P.alpha.y}, dfl{P.alpha.z, P.alpha.w});
-            if (P.accumulate) {
+            cdf v{dfl{rh * f, rl * f}, dfl{ih * f, il * f}};
+            if (use_alpha) v = cdf_mul(v, dfl{alpha.x, alpha.y}, dfl{alpha.z, alpha.w});
+            if (accumulate) {
               const float4 o = crow[n];
               v = cdf_add(v, cdf{dfl{o.x, o.y}, dfl{o.z, o.w}});
             }
@@ -378,7 +394,7 @@ int launch(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
   if (tiles < grid) grid = (int)tiles;
   if (grid < 1) return NSPT_OK;
   ProfScope ps(NSPT_STAGE_GEMM_TC, st);
-  split_gemm_kernel<S, BN, MAXP><<<grid, 192, smem_bytes<S, BN>(), st>>>(*gb, a[0].err);
+  split_gemm_kernel<S, BN, MAXP><<<grid, 320, smem_bytes<S, BN>(), st>>>(*gb, a[0].err);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
