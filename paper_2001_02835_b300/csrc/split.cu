@@ -115,10 +115,12 @@ __device__ __forceinline__ void digits_re_im(float4 v, int e, float (&re)[S], fl
 // right operand of the tensor-core GEMM;
 // the source of plane q = b*M + p is mode p (rev = 0) or (M - p) mod M (rev = 1)
 // of batch element b.
+constexpr int RB = 8;  // output rows per CTA
+
 template <int S, typename InT>
 __global__ void __launch_bounds__(256)
 slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
-             int RB, int P, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+             int P, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   extern __shared__ __align__(16) unsigned char tile_raw[];
   InT* tile = reinterpret_cast<InT*>(tile_raw);
   const int q = blockIdx.y;
@@ -129,15 +131,15 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   const int nr = min(RB, N - r0);
   const int ld = RB + 1;
   if (!trans) {
-    for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
-      const int rr = idx / N, k = idx % N;
-      tile[rr * N + k] = Xm[(long long)(r0 + rr) * N + k];
-    }
+    // one warp per source row: coalesced row reads
+    for (int rr = threadIdx.x >> 5; rr < nr; rr += blockDim.x >> 5)
+      for (int k = threadIdx.x & 31; k < N; k += 32) tile[rr * N + k] = Xm[(long long)(r0 + rr) * N + k];
   } else {
-    for (int idx = threadIdx.x; idx < nr * N; idx += blockDim.x) {
-      const int k = idx / nr, rr = idx % nr;
-      tile[k * ld + rr] = Xm[(long long)k * N + r0 + rr];
-    }
+    // RB consecutive entries of every source row: one 128- or 256-byte run per row
+    const int rr = threadIdx.x % RB;
+    if (rr < nr)
+      for (int k = threadIdx.x / RB; k < N; k += blockDim.x / RB)
+        tile[k * ld + rr] = Xm[(long long)k * N + r0 + rr];
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -173,21 +175,15 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   }
 }
 
-int row_block(int N) {
-  int rb = (int)(190000 / ((long long)(N + 1) * 16)) - 1;
-  return std::max(1, std::min(16, rb));
-}
-
 template <int S, typename InT>
 int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q, int P,
                  __nv_bfloat16* out, int* exps, cudaStream_t st) {
-  const int RB = row_block(N);
   const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
   cudaError_t e = cudaFuncSetAttribute(slice_kernel<S, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, RB, P, out, exps);
+  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, P, out, exps);
   e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
