@@ -72,9 +72,12 @@ typedef struct nspt_opts {
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
   int complex_mode;    /* split form: 4 (four real products per complex product); 0 = 4 */
   int rescale_log2r;   /* split form: per-order rescale A_k, B_k -> r^k A_k, r^k B_k with
-                          r = 2^rescale_log2r, undone exactly on C; NSPT_RESCALE_AUTO = fit
-                          r from the operands' order magnitudes on the host (never
-                          used inside graph capture); default 0 */
+                          r = 2^rescale_log2r, undone exactly on C (not part of the paper);
+                          NSPT_RESCALE_AUTO (nspt_polymat_mul only): r = 2^round(-sigma/2)
+                          with sigma the least-squares slope over k of
+                          log2 max|A_k| + log2 max|B_k| -- this reads per-order maxima
+                          back and synchronises the stream, so never inside graph
+                          capture; default 0 */
   void* workspace;     /* device scratch, >= nspt_workspace_size() bytes */
   size_t workspace_bytes;
 } nspt_opts;

@@ -289,11 +289,76 @@ size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int S) {
   return nspt_split_ws_mul(N, T, batch, M, S) + (((size_t)batch * M * N * N * sizeof(double2) + 255) & ~(size_t)255);
 }
 
+namespace {
+
+// per order k: the largest FP64 exponent field over the real and imaginary parts of
+// every entry of A_k (out[k]) and of B_k (out[T + 1 + k]) across the batch (0 = all zero)
+__global__ void order_maxexp_kernel(const double2* __restrict__ A, const double2* __restrict__ B, int* out, long long E,
+                                    int T, int batch) {
+  const int k = blockIdx.y;
+  int ma = 0, mb = 0;
+  for (int b = 0; b < batch; ++b) {
+    const double2* a = A + ((long long)b * (T + 1) + k) * E;
+    const double2* bb = B + ((long long)b * (T + 1) + k) * E;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < E; i += (long long)gridDim.x * blockDim.x) {
+      const double2 x = a[i], y = bb[i];
+      ma = max(ma, max((int)((__double_as_longlong(x.x) >> 52) & 0x7FF), (int)((__double_as_longlong(x.y) >> 52) & 0x7FF)));
+      mb = max(mb, max((int)((__double_as_longlong(y.x) >> 52) & 0x7FF), (int)((__double_as_longlong(y.y) >> 52) & 0x7FF)));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ma = max(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+    mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out + k, ma);
+    atomicMax(out + T + 1 + k, mb);
+  }
+}
+
+}  // namespace
+
+// Fits log2 r for the per-order rescale (a0): with m_k = log2 max|A_k| + log2 max|B_k|
+// over the orders where both are non-zero, the least-squares slope sigma of m_k
+// against k gives r = 2^round(-sigma / 2), one r for both operands so that
+// C_k = r^-k (A' * B')_k.  Reads a few integers back: synchronises the stream.
+int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int batch, void* scratch, int* log2r,
+                           cudaStream_t st) {
+  int* d = (int*)scratch;
+  TRYC(cudaMemsetAsync(d, 0, sizeof(int) * 2 * (T + 1), st));
+  const long long E = (long long)N * N;
+  dim3 grid((unsigned)std::min<long long>((E + 255) / 256, 64), T + 1);
+  order_maxexp_kernel<<<grid, 256, 0, st>>>(A, B, d, E, T, batch);
+  TRYC(cudaGetLastError());
+  std::vector<int> h(2 * (T + 1));
+  TRYC(cudaMemcpyAsync(h.data(), d, sizeof(int) * 2 * (T + 1), cudaMemcpyDeviceToHost, st));
+  TRYC(cudaStreamSynchronize(st));
+  // exponent fields: log2 max|A_k| + log2 max|B_k| ~ (eA - 1023) + (eB - 1023)
+  double sx = 0, sy = 0, sxx = 0, sxy = 0;
+  int n = 0;
+  for (int k = 0; k <= T; ++k) {
+    if (h[k] == 0 || h[T + 1 + k] == 0) continue;
+    const double y = (double)(h[k] - 1023) + (double)(h[T + 1 + k] - 1023);
+    sx += k; sy += y; sxx += (double)k * k; sxy += k * y; ++n;
+  }
+  *log2r = 0;
+  if (n >= 2) {
+    const double den = n * sxx - sx * sx;
+    if (den > 0) {
+      const double sigma = (n * sxy - sx * sy) / den;
+      *log2r = (int)std::lround(-sigma / 2.0);
+      *log2r = std::max(-60, std::min(60, *log2r));
+    }
+  }
+  return NSPT_OK;
+}
+
 int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescale_auto, const double2* A,
                    const double2* B, double2* C, void* ws, cudaStream_t st) {
-  if (rescale_auto) return NSPT_ERR_UNSUPPORTED;
   const int E = N * N, Q = batch * M;
   SplitWs w = carve(ws, N, batch, M, S, nullptr);
+  if (rescale_auto) TRYS(nspt_split_fit_rescale(A, B, N, T, batch, w.expA, &log2r, st));
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
   TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));

@@ -75,6 +75,9 @@ def test_split_per_order_rescale(nspt):
     assert err <= bound(6, N), err
     C0 = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", rescale_log2r=0))
     assert max_order_rel(C0, ref) > 1e3 * err
+    # the automatic fit finds r = 1/2 for these operands and gives the same result
+    Ca = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", rescale_log2r=nspt.RESCALE_AUTO))
+    np.testing.assert_array_equal(Ca, C)
 
 
 @pytest.mark.parametrize("N,T,batch", [(3, 2, 1), (9, 8, 2), (70, 5, 1)])
