@@ -131,15 +131,32 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   const int nr = min(RB, N - r0);
   const int ld = RB + 1;
   if (!trans) {
-    // one warp per source row: coalesced row reads
-    for (int rr = threadIdx.x >> 5; rr < nr; rr += blockDim.x >> 5)
-      for (int k = threadIdx.x & 31; k < N; k += 32) tile[rr * N + k] = Xm[(long long)(r0 + rr) * N + k];
+    // one warp per source row: coalesced row reads, four loads in flight per thread
+    for (int rr = threadIdx.x >> 5; rr < nr; rr += blockDim.x >> 5) {
+      const InT* src = Xm + (long long)(r0 + rr) * N;
+      InT* dst = tile + rr * N;
+      int k = threadIdx.x & 31;
+      for (; k + 96 < N; k += 128) {
+        const InT x0 = src[k], x1 = src[k + 32], x2 = src[k + 64], x3 = src[k + 96];
+        dst[k] = x0; dst[k + 32] = x1; dst[k + 64] = x2; dst[k + 96] = x3;
+      }
+      for (; k < N; k += 32) dst[k] = src[k];
+    }
   } else {
     // RB consecutive entries of every source row: one 128- or 256-byte run per row
     const int rr = threadIdx.x % RB;
-    if (rr < nr)
-      for (int k = threadIdx.x / RB; k < N; k += blockDim.x / RB)
-        tile[k * ld + rr] = Xm[(long long)k * N + r0 + rr];
+    constexpr int STEP = 256 / RB;
+    if (rr < nr) {
+      const InT* src = Xm + r0 + rr;
+      int k = threadIdx.x / RB;
+      for (; k + 3 * STEP < N; k += 4 * STEP) {
+        const InT x0 = src[(long long)k * N], x1 = src[(long long)(k + STEP) * N];
+        const InT x2 = src[(long long)(k + 2 * STEP) * N], x3 = src[(long long)(k + 3 * STEP) * N];
+        tile[k * ld + rr] = x0; tile[(k + STEP) * ld + rr] = x1;
+        tile[(k + 2 * STEP) * ld + rr] = x2; tile[(k + 3 * STEP) * ld + rr] = x3;
+      }
+      for (; k < N; k += STEP) tile[k * ld + rr] = src[(long long)k * N];
+    }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

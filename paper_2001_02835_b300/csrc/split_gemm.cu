@@ -21,8 +21,8 @@
 // the groups in double-float (hi + lo float pair), applies
 // 2^(e_A[m] + e_B[n] - 14) and writes float4 (re_hi, re_lo, im_hi, im_lo).
 //
-// Roles (one CTA per SM, persistent over tiles): warp 0 lane 0 issues TMA
-// loads, warp 1 lane 0 issues tcgen05.mma, warps 2-9 drain TMEM (two per lane
+// Roles (one CTA per SM, persistent over tiles): warp 0 lanes 0 and 1 issue the
+// TMA loads of A and B, warp 1 lane 0 issues tcgen05.mma, warps 2-9 drain TMEM (two per lane
 // quarter, each half of the columns).  Per K block
 // of 32, all S slices of the B tile (re, im, -re) are loaded once and the A
 // slices stream through a 4-stage ring; the triangle of slice pairs
@@ -34,38 +34,14 @@
 #include "split_gemm.cuh"
 #include "tc_ptx.cuh"
 #include "dfloat.cuh"
+#include "split_gemm_common.cuh"
 
 #include <cstring>
 #include <memory>
 
 namespace {
 
-constexpr int BM = 128, KB = 32;
-constexpr int NA_STAGES = 4;
-constexpr uint32_t A_TILE = BM * KB * 2;  // 8 KB per part
-constexpr int NGROUPS = 5;
-constexpr uint32_t TMEM_COLS = 512;
-constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
-
-// One problem of a (possibly grouped) launch; all of them travel in the kernel
-// parameters, so a launch needs no device-side table and can be captured.
-struct GemmProblem {  // aligned like its CUtensorMap members
-  CUtensorMap mA, mB;    // slice planes of the left / right operand
-  const int* expA;
-  const int* expB;
-  float4* C;
-  int N, Q, tilesM, tilesN;
-  long long tile_begin;  // first global tile index of this problem
-  float4 alpha;          // C = alpha * A B (+ C): (re_hi, re_lo, im_hi, im_lo)
-  int use_alpha, accumulate;
-};
-
-template <int MAXP>
-struct GemmBatch {
-  GemmProblem p[MAXP];
-  int count;
-  long long total_tiles;
-};
+using namespace sg;
 
 template <int S, int BN>
 struct Smem {
@@ -78,47 +54,6 @@ struct Smem {
   uint32_t tmem_base;
   volatile int abort_flag;
 };
-
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                         int code) {
-  if (tc::mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = tc::globaltimer();
-  uint32_t n = 0;
-  while (!tc::mbar_try_wait(bar, parity)) {
-    if ((++n & 255) == 0) {
-      if (*abort_flag) return false;
-      if (tc::globaltimer() - t0 > WAIT_LIMIT_NS) {
-        *abort_flag = 1;
-        atomicCAS(err, 0, code);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-
-// error-free sum of two floats (Knuth's TwoSum)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
-__device__ __forceinline__ float pow2f(int k) {
-  k = max(-126, min(127, k));
-  return __int_as_float((k + 127) << 23);
-}
-
-// double-float sum of the digit-group accumulators, largest first
-__device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, float& lo) {
-  float h, s2, s3, e1, e2, e3;
-  two_sum(a[0], a[1], h, e1);
-  two_sum(h, a[2], s2, e2);
-  two_sum(s2, a[3], s3, e3);
-  const float l = ((e1 + e2) + e3) + a[4];
-  hi = s3 + l;
-  lo = l - (hi - s3);
-}
 
 template <int S, int BN, int MAXP>
 __global__ void __launch_bounds__(320, 1)
@@ -155,12 +90,15 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
   tc::fence_after_sync();
   const uint32_t tmem = sm.tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // ------------------------------ TMA producer ------------------------------
+  if (warp == 0 && lane < 2) {
+    // ---------------- TMA producers: lane 0 streams A slices, lane 1 B slices ----------------
+    // (two threads, so that the next K block's B tile is requested as soon as its buffer frees,
+    // not behind the waits of the A ring)
+    const bool isA = (lane == 0);
     int ia = 0, ib = 0;
     uint32_t pa = 0, pb = 0;
-    uint32_t last_a_parity[NA_STAGES] = {0, 0, 0, 0}, last_b_parity[2] = {0, 0};
-    bool issued_a[NA_STAGES] = {false, false, false, false}, issued_b[2] = {false, false};
+    uint32_t last_a_parity[NA_STAGES] = {}, last_b_parity[2] = {0, 0};
+    bool issued_a[NA_STAGES] = {}, issued_b[2] = {false, false};
     int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
       while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
@@ -172,22 +110,25 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int nK = (P.N + KB - 1) / KB;
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
-        if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
-        tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
-        for (int j = 0; j < S; ++j)
-          for (int c = 0; c < 3; ++c)
-            tc::tma_load_3d(sm.b[ib][j][c], &P.mB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
-        issued_b[ib] = true;
-        last_b_parity[ib] = pb;
-        if (++ib == 2) { ib = 0; pb ^= 1; }
-        for (int i = 0; i < S; ++i) {
-          if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
-          tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
-          for (int c = 0; c < 2; ++c)
-            tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
-          issued_a[ia] = true;
-          last_a_parity[ia] = pa;
-          if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+        if (!isA) {
+          if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
+          tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
+          for (int j = 0; j < S; ++j)
+            for (int c = 0; c < 3; ++c)
+              tc::tma_load_3d(sm.b[ib][j][c], &P.mB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
+          issued_b[ib] = true;
+          last_b_parity[ib] = pb;
+          if (++ib == 2) { ib = 0; pb ^= 1; }
+        } else {
+          for (int i = 0; i < S; ++i) {
+            if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
+            tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
+            for (int c = 0; c < 2; ++c)
+              tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
+            issued_a[ia] = true;
+            last_a_parity[ia] = pa;
+            if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+          }
         }
       }
       if (!ok) break;
@@ -350,18 +291,6 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn g_encode = nullptr;
 
-// 3-D map over slice planes: (k < N, row < N, plane), row pitch Kp bf16
-int make_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes, int box_rows) {
-  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)N * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;
-}
-
 template <int S, int BN>
 size_t smem_bytes() { return sizeof(Smem<S, BN>) + 1024; }
 
@@ -369,27 +298,8 @@ template <int S, int BN, int MAXP>
 int launch(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
   std::unique_ptr<GemmBatch<MAXP>> gb(new GemmBatch<MAXP>());
   memset(gb.get(), 0, sizeof(GemmBatch<MAXP>));
-  long long tiles = 0;
-  for (int i = 0; i < count; ++i) {
-    GemmProblem& P = gb->p[i];
-    // left operand: planes (re, im) per digit; right operand: (re, im, -re)
-    if (make_map(&P.mA, a[i].slicesA, a[i].N, a[i].Kp, (long long)a[i].Q * S * 2, BM)) return NSPT_ERR_CUDA;
-    if (make_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, (long long)a[i].Q * S * 3, BN)) return NSPT_ERR_CUDA;
-    P.expA = a[i].expA; P.expB = a[i].expB; P.C = a[i].C;
-    P.N = a[i].N; P.Q = a[i].Q;
-    P.tilesM = (a[i].N + BM - 1) / BM;
-    P.tilesN = (a[i].N + BN - 1) / BN;
-    P.tile_begin = tiles;
-    P.use_alpha = a[i].use_alpha;
-    P.accumulate = a[i].accumulate;
-    {
-      const float rh = (float)a[i].alpha.x, ih = (float)a[i].alpha.y;
-      P.alpha = make_float4(rh, (float)(a[i].alpha.x - (double)rh), ih, (float)(a[i].alpha.y - (double)ih));
-    }
-    tiles += (long long)a[i].Q * P.tilesM * P.tilesN;
-  }
-  gb->count = count;
-  gb->total_tiles = tiles;
+  if (build_batch<MAXP>(gb.get(), a, count, S, BN)) return NSPT_ERR_CUDA;
+  const long long tiles = gb->total_tiles;
   int grid = num_sms;
   if (tiles < grid) grid = (int)tiles;
   if (grid < 1) return NSPT_OK;
@@ -432,6 +342,18 @@ int set_attrs() {
 
 }  // namespace
 
+// 3-D map over slice planes: (k < N, row < N, plane), row pitch Kp bf16
+int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes, int box_rows) {
+  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)planes};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)N * Kp * 2};
+  cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;
+}
+
 int nspt_split_gemm_init() {
   if (!g_encode) {
     void* fn = nullptr;
@@ -450,6 +372,7 @@ int nspt_split_gemm_init() {
   if (!rc) rc = set_attrs<6>();
   if (!rc) rc = set_attrs<7>();
   if (!rc) rc = set_attrs<8>();
+  if (!rc) rc = nspt_split_gemm_ta_init();
   if (rc) return rc;
   return NSPT_OK;
 }
@@ -458,6 +381,7 @@ int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int 
   if (count < 1) return NSPT_OK;
   for (int i = 0; i < count; ++i)
     if (a[i].N > 1024 || a[i].N < 1 || a[i].S != S) return NSPT_ERR_UNSUPPORTED;
+  if (bn == 40) return nspt_split_gemm_ta_batch(a, count, S, num_sms, st);
   switch (S) {
     case 2: return launch_bn<2>(a, count, bn, st, num_sms);
     case 3: return launch_bn<3>(a, count, bn, st, num_sms);

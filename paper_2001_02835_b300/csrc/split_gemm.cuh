@@ -22,3 +22,6 @@ int nspt_split_gemm_init();
 int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st);
 // one persistent launch over the tiles of `count` problems (same S); err of a[0] is used
 int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int num_sms, cudaStream_t st);
+// variant with the left operand in tensor memory (tile 128 x 40), selected by bn = 40
+int nspt_split_gemm_ta_init();
+int nspt_split_gemm_ta_batch(const SplitGemmArgs* a, int count, int S, int num_sms, cudaStream_t st);
