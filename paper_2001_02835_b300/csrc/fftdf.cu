@@ -48,7 +48,7 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
   const long long e0 = (long long)blockIdx.x * EB;
   const bool valid = (e0 + e) < E;
   const double2* src = in + (long long)b * in_stride * E + e0 + e;
-  for (int k = y; k < M / 2; k += 8) {
+  auto load_in = [&](int k) -> cdf {
     cdf v = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
     if (k <= T && valid) {
       const double2 x = src[(long long)k * E];
@@ -59,32 +59,71 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
         v = cdf{df_scale(df_scale(v.re, f1), f2), df_scale(df_scale(v.im, f1), f2)};
       }
     }
-    st(&sm[k * EB + e], v);
-    if (k == 0) {
-      st(&sm[(k + M / 2) * EB + e], v);
-    } else {
-      dfl c, s;
-      tw(k, M, false, c, s);
-      st(&sm[(k + M / 2) * EB + e], cdf_mul(v, c, s));
+    return v;
+  };
+  int h;  // span of the next radix-2 stage still to do
+  if (M >= 4) {
+    // first two DIF stages at once (radix 2^2), upper half of the input zero:
+    // X[n] = x0 + x1, X[n + M/4] = (x0 - x1) w^2n, X[n + M/2] = (x0 + i x1) w^n,
+    // X[n + 3M/4] = (x0 - i x1) w^3n, with x0 = x[n], x1 = x[n + M/4], n < M/4
+    for (int n = y; n < M / 4; n += 8) {
+      const cdf x0 = load_in(n), x1 = load_in(n + M / 4);
+      const cdf ix1 = cdf{df_neg(x1.im), x1.re};
+      cdf o0 = cdf_add(x0, x1), o1 = cdf_sub(x0, x1), o2 = cdf_add(x0, ix1), o3 = cdf_sub(x0, ix1);
+      if (n != 0) {
+        dfl c, s;
+        tw(2 * n, M, false, c, s); o1 = cdf_mul(o1, c, s);
+        tw(n, M, false, c, s);     o2 = cdf_mul(o2, c, s);
+        tw(3 * n, M, false, c, s); o3 = cdf_mul(o3, c, s);
+      }
+      st(&sm[n * EB + e], o0);
+      st(&sm[(n + M / 4) * EB + e], o1);
+      st(&sm[(n + M / 2) * EB + e], o2);
+      st(&sm[(n + 3 * M / 4) * EB + e], o3);
     }
+    h = M / 8;  // span of the next stage
+  } else {
+    // M = 2: one stage, x[1] = 0
+    for (int k = y; k < 1; k += 8) {
+      const cdf v = load_in(0);
+      st(&sm[0 * EB + e], v);
+      st(&sm[1 * EB + e], v);
+    }
+    h = 0;
   }
   __syncthreads();
+  // remaining DIF stages: radix 2^2 steps over spans (h, h/2) while two are left
 #pragma unroll 1
-  for (int h = M / 4; h >= 1; h >>= 1) {
+  for (; h >= 2; h >>= 2) {
+    const int q4 = h / 2;   // quarter of the group of size L = 2h
     const int tstep = M / (2 * h);
+    for (int u = y; u < M / 4; u += 8) {
+      const int g = u / q4, n = u % q4;
+      const int base = g * 2 * h + n;
+      const cdf x0 = ld(&sm[base * EB + e]), x1 = ld(&sm[(base + q4) * EB + e]);
+      const cdf x2 = ld(&sm[(base + 2 * q4) * EB + e]), x3 = ld(&sm[(base + 3 * q4) * EB + e]);
+      const cdf s0 = cdf_add(x0, x2), s1 = cdf_add(x1, x3), d0 = cdf_sub(x0, x2), d1 = cdf_sub(x1, x3);
+      const cdf id1 = cdf{df_neg(d1.im), d1.re};
+      cdf o0 = cdf_add(s0, s1), o1 = cdf_sub(s0, s1), o2 = cdf_add(d0, id1), o3 = cdf_sub(d0, id1);
+      if (n != 0) {
+        dfl c, s;
+        tw(2 * n * tstep, M, false, c, s); o1 = cdf_mul(o1, c, s);
+        tw(n * tstep, M, false, c, s);     o2 = cdf_mul(o2, c, s);
+        tw(3 * n * tstep, M, false, c, s); o3 = cdf_mul(o3, c, s);
+      }
+      st(&sm[base * EB + e], o0);
+      st(&sm[(base + q4) * EB + e], o1);
+      st(&sm[(base + 2 * q4) * EB + e], o2);
+      st(&sm[(base + 3 * q4) * EB + e], o3);
+    }
+    __syncthreads();
+  }
+  if (h == 1) {  // one radix-2 stage of span 1 left (twiddles all 1)
     for (int bf = y; bf < M / 2; bf += 8) {
-      const int g = bf / h, j = bf % h;
-      const int i0 = g * 2 * h + j, i1 = i0 + h;
+      const int i0 = 2 * bf, i1 = i0 + 1;
       const cdf u = ld(&sm[i0 * EB + e]), v = ld(&sm[i1 * EB + e]);
       st(&sm[i0 * EB + e], cdf_add(u, v));
-      const cdf d = cdf_sub(u, v);
-      if (j == 0) {
-        st(&sm[i1 * EB + e], d);
-      } else {
-        dfl c, s;
-        tw(j * tstep, M, false, c, s);
-        st(&sm[i1 * EB + e], cdf_mul(d, c, s));
-      }
+      st(&sm[i1 * EB + e], cdf_sub(u, v));
     }
     __syncthreads();
   }
@@ -117,8 +156,32 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   for (int p = y; p < M; p += 8)
     sm[bitrev<M>(p) * EB + e] = valid ? src[(long long)p * E] : make_float4(0.f, 0.f, 0.f, 0.f);
   __syncthreads();
+  // DIT stages of spans 1 .. M/4: radix 2^2 steps over spans (h, 2h) while two are left
+  int h = 1;
 #pragma unroll 1
-  for (int h = 1; h <= M / 4; h <<= 1) {
+  for (; 2 * h <= M / 4; h <<= 2) {
+    const int tstep = M / (4 * h);  // w_L^-m = conj(w_M^(m M / L)), L = 4h
+    for (int u = y; u < M / 4; u += 8) {
+      const int g = u / h, n = u % h;
+      const int base = g * 4 * h + n;
+      cdf a = ld(&sm[base * EB + e]), bq = ld(&sm[(base + h) * EB + e]);
+      cdf c = ld(&sm[(base + 2 * h) * EB + e]), d = ld(&sm[(base + 3 * h) * EB + e]);
+      if (n != 0) {
+        dfl cw, sw;
+        tw(2 * n * tstep, M, true, cw, sw); bq = cdf_mul(bq, cw, sw);
+        tw(n * tstep, M, true, cw, sw);     c = cdf_mul(c, cw, sw);
+        tw(3 * n * tstep, M, true, cw, sw); d = cdf_mul(d, cw, sw);
+      }
+      const cdf apb = cdf_add(a, bq), amb = cdf_sub(a, bq), cpd = cdf_add(c, d), cmd = cdf_sub(c, d);
+      const cdf mi = cdf{cmd.im, df_neg(cmd.re)};  // (-i)(c - d)
+      st(&sm[base * EB + e], cdf_add(apb, cpd));
+      st(&sm[(base + h) * EB + e], cdf_add(amb, mi));
+      st(&sm[(base + 2 * h) * EB + e], cdf_sub(apb, cpd));
+      st(&sm[(base + 3 * h) * EB + e], cdf_sub(amb, mi));
+    }
+    __syncthreads();
+  }
+  if (h <= M / 4) {  // one radix-2 DIT stage of span h left
     const int tstep = M / (2 * h);
     for (int bf = y; bf < M / 2; bf += 8) {
       const int g = bf / h, j = bf % h;
