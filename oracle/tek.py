@@ -129,3 +129,32 @@ def langevin_step(U, eta, z, eps: float):
         X[..., :, 1, :, :] += math.sqrt(2.0 * eps) * eta
     Unew = pm.star(exp_star(1j * X), U)
     return Unew, F
+
+
+def md_step(U, P, z, eps: float):
+    """One leapfrog step of the NSPT molecular dynamics (Eq. 3 with beta absorbed by the
+    rescaled time): the momentum series P~ = sum_{k>=1} g^k P^(k) (stored with P^(0) = 0),
+    dU^(k)/dt = i (P~ * U)^(k), dP^(k)/dt = F^(k) for k >= 1 (order 0 of F is dropped:
+    the momentum has no order g^0):
+        P_half = P + eps/2 F(U);  U' = exp_star(i eps P_half) * U;  P' = P_half + eps/2 F(U').
+    Returns (U', P')."""
+    U = np.asarray(U, np.complex128)
+    P = np.array(P, np.complex128)
+    P[..., :, 0, :, :] = 0.0
+    F = drift(U, z)
+    F[..., :, 0, :, :] = 0.0
+    Ph = P + 0.5 * eps * F
+    Unew = pm.star(exp_star(1j * eps * Ph), U)
+    F2 = drift(Unew, z)
+    F2[..., :, 0, :, :] = 0.0
+    return Unew, Ph + 0.5 * eps * F2
+
+
+def md_trajectory(U, eta, z, eps: float, nsteps: int):
+    """Momentum refresh (P^(1) = eta, higher orders 0) followed by `nsteps` leapfrog steps."""
+    U = np.asarray(U, np.complex128)
+    P = np.zeros_like(U)
+    P[..., :, 1, :, :] = eta
+    for _ in range(nsteps):
+        U, P = md_step(U, P, z, eps)
+    return U, P

@@ -491,3 +491,82 @@ def test_langevin_small_eps_first_order():
         scale = np.abs(lin).max()
     assert d[0] < 1e-3 * scale
     assert 1.6 < d[1] / d[0] < 2.4
+
+
+# ----------------------------------------------------------------------------
+# molecular dynamics (leapfrog with momentum refresh)
+# ----------------------------------------------------------------------------
+
+
+def test_md_step_is_time_reversible():
+    """Leapfrog is reversible: step, flip the momentum, step again -> back to the start
+    (exact in the truncated ring, so up to rounding)."""
+    rg = syn.rng(61)
+    L, k, T = 3, 1, 4
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    P = np.zeros_like(U)
+    P[:, 1] = syn.hermitian_noise(rg, N, 4)
+    P[:, 2:] = 0.3 * syn.hermitian_traceless(rg, N, 4 * (T - 1)).reshape(4, T - 1, N, N)
+    z = tek.twist_phases(L, k)
+    U1, P1 = tek.md_step(U, P, z, 0.05)
+    U2, P2 = tek.md_step(U1, -P1, z, 0.05)
+    np.testing.assert_allclose(U2, U, atol=1e-12)
+    np.testing.assert_allclose(-P2, P, atol=1e-12)
+    assert np.abs(U1 - U).max() > 1e-3
+
+
+def test_md_step_matches_nonperturbative_leapfrog():
+    """sum_k g^k of the series step equals the leapfrog of the matrix equations
+    U' = exp(i eps Ph(g)) U(g), Ph = P(g) + eps/2 (F(g) - F^(0)) ... to O(g^{T+1})."""
+    rg = syn.rng(62)
+    L, k, T, eps = 3, 1, 3, 0.07
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    U[:, 0] = syn.haar_sun(rg, N, 4)           # generic order 0: F^(0) != 0 is dropped
+    P = np.zeros_like(U)
+    P[:, 1] = syn.hermitian_noise(rg, N, 4)
+    z = tek.twist_phases(L, k)
+    U1, P1 = tek.md_step(U, P, z, eps)
+
+    def force(Ug):
+        S = _nonpert_staple(Ug, z)
+        D = S - np.conj(np.swapaxes(S, -1, -2))
+        D = D - (np.trace(D, axis1=-2, axis2=-1) / N)[:, None, None] * np.eye(N)
+        return 1j * D
+
+    F0 = tek.drift(U, z)[:, 0]                  # order-0 parts removed at both force evaluations
+    errs = []
+    for gc in (5e-3, 1e-2):
+        pw = gc ** np.arange(T + 1)
+        Ug = np.einsum("k,mkij->mij", pw, U)
+        Pg = np.einsum("k,mkij->mij", pw, P)
+        Ph = Pg + 0.5 * eps * (force(Ug) - F0)
+        U1g = np.stack([sla.expm(1j * eps * Ph[m]) @ Ug[m] for m in range(4)])
+        F0b = tek.drift(U1, z)[:, 0]
+        P1g = Ph + 0.5 * eps * (force(U1g) - F0b)
+        errs.append(max(np.abs(np.einsum("k,mkij->mij", pw, U1) - U1g).max(),
+                        np.abs(np.einsum("k,mkij->mij", pw, P1) - P1g).max()))
+    assert errs[0] < 1e-8
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+
+
+def test_md_trajectory_refresh_and_vacuum():
+    rg = syn.rng(63)
+    L, k, T = 3, 1, 3
+    N = L * L
+    U = np.zeros((4, T + 1, N, N), np.complex128)
+    U[:, 0] = syn.twist_eaters(L, k)
+    z = tek.twist_phases(L, k)
+    # the vacuum with zero momentum is a fixed point of the dynamics
+    U0, P0 = tek.md_trajectory(U, np.zeros((4, N, N)), z, 0.1, 3)
+    assert np.abs(U0 - U).max() < 1e-13 and np.abs(P0).max() < 1e-13
+    # with refreshed momentum the links move, order 0 never does, and P^(0) stays 0
+    eta = syn.hermitian_noise(rg, N, 4)
+    U1, P1 = tek.md_trajectory(U, eta, z, 0.1, 3)
+    np.testing.assert_array_equal(U1[:, 0], U[:, 0])
+    assert np.all(P1[:, 0] == 0)
+    assert np.abs(U1[:, 1]).max() > 1e-2
+    # momentum and drift stay Hermitian and traceless order by order
+    np.testing.assert_allclose(P1, np.conj(np.swapaxes(P1, -1, -2)), atol=1e-13)
+    assert np.abs(np.trace(P1, axis1=-2, axis2=-1)).max() < 1e-12
