@@ -60,7 +60,7 @@ enum { NSPT_PREC_FP64 = 0,  /* plain FP64 everywhere (the paper's ZGEMM form) */
                                FP32 partial sums, double-word recombination */ };
 
 /* which call a workspace is sized for */
-enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2 };
+enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_MD = 3 };
 
 #define NSPT_RESCALE_AUTO (-1000)
 
@@ -167,6 +167,23 @@ NSPT_API int nspt_polymat_mul_grouped(const nspt_polymat_desc* descs, int count,
  */
 NSPT_API int nspt_autotune_grouped(const nspt_polymat_desc* descs, int count, const nspt_opts* opts,
                                    const char* cache_path, int* chosen_bn, void* stream);
+
+/*
+ * NSPT molecular dynamics of the TEK model, the integrator of the paper
+ * (symplectic MD with periodic momentum refresh, Sec. 2; Eq. 3 with beta
+ * absorbed by the rescaled time).  The momentum series P~ = sum_{k>=1} g^k P^(k)
+ * has no order g^0; the drift's order 0 is dropped.  Leapfrog step of size eps:
+ *   P_half = P + eps/2 F(U);  U <- exp_star(i eps P_half) star U;  P = P_half + eps/2 F(U),
+ * with F and exp_star exactly as in nspt_tek_langevin_step (order 0 of U is
+ * never rewritten).
+ *   U   : [batch][4][T+1][N][N] link series, updated in place
+ *   P   : [batch][4][T+1][N][N] momentum series, updated in place (order 0 kept 0)
+ *   eta_refresh : [batch][4][N][N] traceless Hermitian Gaussian, or NULL; when given,
+ *         the momentum is refreshed to P^(1) = eta, P^(k != 1) = 0 before the steps
+ *   nsteps >= 0 leapfrog steps of size eps > 0.  Workspace: NSPT_OP_MD.
+ */
+NSPT_API int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, int N, int T, int batch, int flux,
+                                    double eps, int nsteps, const nspt_opts* opts, void* stream);
 
 /*
  * Single stages of FFT-CONV, for stage timing and per-stage tests.

@@ -22,14 +22,14 @@ import torch
 
 __all__ = [
     "lib", "library_path", "Opts", "NsptError",
-    "polymat_mul", "polymat_mul_backward", "tek_langevin_step", "order_fft", "order_ifft",
+    "polymat_mul", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "order_fft", "order_ifft",
     "workspace_size", "star", "PolymatMul",
     "ALGO_NAIVE", "ALGO_FFT", "ALGO_AUTO", "PREC_FP64", "PREC_SPLIT", "RESCALE_AUTO",
 ]
 
 ALGO_NAIVE, ALGO_FFT, ALGO_AUTO = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0, 1
-OP_MUL, OP_MUL_BACKWARD, OP_LANGEVIN = 0, 1, 2
+OP_MUL, OP_MUL_BACKWARD, OP_LANGEVIN, OP_MD = 0, 1, 2, 3
 RESCALE_AUTO = -1000
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -67,6 +67,7 @@ _SIGS = {
     "nspt_polymat_mul": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_langevin_step": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, ctypes.POINTER(Opts), _vp]),
+    "nspt_tek_md_trajectory": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_order_fft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_order_ifft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_status_string": (ctypes.c_char_p, [_i]),
@@ -228,6 +229,28 @@ def tek_langevin_step(U: torch.Tensor, eta: torch.Tensor, flux: int, eps: float,
                                       N, T, batch, int(flux), float(eps), ctypes.byref(opts), _stream_ptr(U.device))
     _check(rc, "nspt_tek_langevin_step")
     return U, F
+
+
+def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, nsteps: int,
+                      eta: Optional[torch.Tensor] = None, **kw):
+    """Leapfrog molecular dynamics in place on U and P (batch, 4, T+1, N, N); with eta
+    (batch, 4, N, N) the momentum is refreshed to P^(1) = eta first.  Returns (U, P)."""
+    _check_tensor(U, "U")
+    _check_tensor(P, "P")
+    if U.shape != P.shape or U.dim() != 5 or U.shape[1] != 4:
+        raise ValueError("U and P must be (batch, 4, T+1, N, N)")
+    batch, T, N = U.shape[0], U.shape[2] - 1, U.shape[3]
+    if eta is not None:
+        _check_tensor(eta, "eta")
+        if tuple(eta.shape) != (batch, 4, N, N):
+            raise ValueError("eta must be (batch, 4, N, N)")
+    opts = make_opts(**kw)
+    ws = _with_ws(OP_MD, N, T, batch, opts, U.device)  # noqa: F841
+    rc = lib().nspt_tek_md_trajectory(U.data_ptr(), P.data_ptr(), eta.data_ptr() if eta is not None else None, N, T,
+                                      batch, int(flux), float(eps), int(nsteps), ctypes.byref(opts),
+                                      _stream_ptr(U.device))
+    _check(rc, "nspt_tek_md_trajectory")
+    return U, P
 
 
 def order_fft(A: torch.Tensor, M: int) -> torch.Tensor:

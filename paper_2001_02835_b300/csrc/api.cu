@@ -196,8 +196,10 @@ size_t ws_langevin(const Plan& p) {
   return (size_t)p.batch * mats * E * sizeof(double2) + (size_t)p.batch * 4 * T1 * sizeof(double) + 8 * 256;
 }
 
+// mode: NSPT_LMODE_STEP (drift, increment, update), NSPT_LMODE_DRIFT (drift F only),
+// NSPT_LMODE_UPDATE (U <- exp_star(Yin) U with the caller's Yin = i X, X^(0) = 0)
 int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int flux, double eps, void* ws,
-                  cudaStream_t st) {
+                  cudaStream_t st, int mode = NSPT_LMODE_STEP, const double2* Yin = nullptr) {
   const int N = p.N, T = p.T, nb = p.batch;
   const long long E = p.E, T1 = T + 1;
   int L = (int)llround(sqrt((double)N));
@@ -228,6 +230,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     // 1. spectra of the four links
     TRY(nspt_fft_fwd64(U, T1, specU, (int)E, T, nb * 4, M, 0, 0, st));
     auto specOf = [&](double2* base, int slot) { return base + (long long)slot * M * E; };
+    if (mode != NSPT_LMODE_UPDATE) {
     // 2. P1(mu,nu) = U_nu * U_mu^+ (mu<nu), Q(mu,nu) = U_mu * U_nu (mu != nu)
     for (int i = 0; i < 6; ++i) {
       const int mu = kPairs[i][0], nu = kPairs[i][1];
@@ -284,6 +287,9 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     TRY(nspt_fft_inv64(specAcc, serS, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st));
     // 5. drift and the Langevin increment Y = i X
     TRY(nspt_tek_drift(serS, imtr, eta, F, serY, N, T, (long long)nb * 4, eps, st));
+    }
+    if (mode == NSPT_LMODE_DRIFT) return NSPT_OK;
+    const double2* Ysrc = (mode == NSPT_LMODE_UPDATE) ? Yin : serY;
     // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
     TRY(cudaMemsetAsync(serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
     TRY(cudaMemsetAsync(serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
@@ -292,7 +298,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     for (int n = T; n >= 1; --n) {
       const int t = T - n + 1;
       const int Mt = next_pow2(2 * (t + 1));
-      TRY(nspt_fft_fwd64(serY, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
+      TRY(nspt_fft_fwd64(Ysrc, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
       TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, t - 1, nb * 4, Mt, 0, 0, st));
       ZgemmParams P = zg(ZG_MODE, spY, Mt, spR, Mt, spC, Mt, N, Mt, t);
       TRY(nspt_zgemm64(P, nb * 4, st));
@@ -318,6 +324,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
   double* imtr = w.take<double>((size_t)nb * 4 * T1);
   auto link = [&](const double2* base, int mu) { return base + (long long)mu * T1 * E; };
   auto wlink = [&](double2* base, int mu) { return base + (long long)mu * T1 * E; };
+  if (mode != NSPT_LMODE_UPDATE) {
   for (int i = 0; i < 6; ++i) {
     const int mu = kPairs[i][0], nu = kPairs[i][1];
     ZgemmParams P = zg(ZG_CONV, link(U, nu), 4 * T1, link(U, mu), 4 * T1, serP1 + (long long)i * T1 * E, 6 * T1, N,
@@ -362,13 +369,16 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     TRY(nspt_zgemm64(P, nb * 4, st));
   }
   TRY(nspt_tek_drift(serS, imtr, eta, F, serY, N, T, (long long)nb * 4, eps, st));
+  }
+  if (mode == NSPT_LMODE_DRIFT) return NSPT_OK;
+  const double2* Ysrc = (mode == NSPT_LMODE_UPDATE) ? Yin : serY;
   TRY(cudaMemsetAsync(serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
   TRY(cudaMemsetAsync(serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
   TRY(add_identity(serR[0], T1, N, (long long)nb * 4, st));
   int cur = 0;
   for (int n = T; n >= 1; --n) {
     const int t = T - n + 1;
-    ZgemmParams P = zg(ZG_CONV, serY, T1, serR[cur], T1, serR[cur ^ 1], T1, N, t + 1, t);
+    ZgemmParams P = zg(ZG_CONV, Ysrc, T1, serR[cur], T1, serR[cur ^ 1], T1, N, t + 1, t);
     P.alpha = make_double2(1.0 / n, 0.0);
     TRY(nspt_zgemm64(P, nb * 4, st));
     TRY(add_identity(serR[cur ^ 1], T1, N, (long long)nb * 4, st));
@@ -377,6 +387,43 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
   TRY(cudaMemcpyAsync(serU0, U, (size_t)nb * 4 * T1 * E * sizeof(double2), cudaMemcpyDeviceToDevice, st));
   ZgemmParams P = zg(ZG_CONV, serR[cur], T1, serU0, T1, U, T1, N, T + 1, T);
   TRY(nspt_zgemm64(P, nb * 4, st));
+  return NSPT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Molecular dynamics: leapfrog with momentum refresh (Eq. 3, the paper's
+// integrator), built from the drift-only and update-only phases above.
+// ---------------------------------------------------------------------------
+size_t ws_md(const Plan& p) {
+  const size_t ser = ((size_t)p.batch * 4 * (p.T + 1) * p.E * sizeof(double2) + 255) & ~(size_t)255;
+  return ((ws_langevin(p) + 255) & ~(size_t)255) + 2 * ser;
+}
+
+int md_phase(const Plan& p, double2* U, double2* F, const double2* Y, int flux, void* lws, cudaStream_t st, int mode) {
+  if (p.prec == NSPT_PREC_SPLIT)
+    return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, U, nullptr, F, flux, 0.0, lws, st, mode, Y);
+  return langevin_fp64(p, U, nullptr, F, flux, 0.0, lws, st, mode, Y);
+}
+
+int md_run(const Plan& p, double2* U, double2* P, const double2* eta, int flux, double eps, int nsteps, void* ws,
+           cudaStream_t st) {
+  const long long E = p.E, ns = (long long)p.batch * 4;
+  const int T = p.T;
+  WsCarver w(ws, SIZE_MAX);
+  void* lws = w.take<char>(ws_langevin(p));
+  double2* F = w.take<double2>((size_t)ns * (T + 1) * E);
+  double2* Y = w.take<double2>((size_t)ns * (T + 1) * E);
+  int rc;
+  if (eta) TRY(nspt_md_refresh(P, eta, T, E, ns, st));
+  if (nsteps <= 0) return NSPT_OK;
+  if ((rc = md_phase(p, U, F, nullptr, flux, lws, st, NSPT_LMODE_DRIFT))) return rc;
+  for (int s = 0; s < nsteps; ++s) {
+    TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));   // P_half = P + eps/2 F(U)
+    TRY(nspt_md_y(Y, P, eps, T, E, ns, st));            // Y = i eps P_half
+    if ((rc = md_phase(p, U, F, Y, flux, lws, st, NSPT_LMODE_UPDATE))) return rc;   // U <- exp_star(Y) U
+    if ((rc = md_phase(p, U, F, nullptr, flux, lws, st, NSPT_LMODE_DRIFT))) return rc;  // F(U')
+    TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));   // P' = P_half + eps/2 F(U')
+  }
   return NSPT_OK;
 }
 
@@ -422,6 +469,7 @@ size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opt
     case NSPT_OP_MUL: return ws_mul(p);
     case NSPT_OP_MUL_BACKWARD: return ws_bwd(p);
     case NSPT_OP_LANGEVIN: return ws_langevin(p);
+    case NSPT_OP_MD: return ws_md(p);
     default: return 0;
   }
 }
@@ -561,6 +609,29 @@ int nspt_autotune_grouped(const nspt_polymat_desc* d, int count, const nspt_opts
   if ((rc = check_ws(o, nspt_workspace_size_grouped(d, count, o)))) return rc;
   if ((rc = nspt_init())) return rc;
   return nspt_split_autotune_grouped(d, count, p.slices, o->workspace, cache_path, chosen_bn, (cudaStream_t)stream);
+}
+
+int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, int N, int T, int batch, int flux, double eps,
+                           int nsteps, const nspt_opts* opts, void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!U || !P || nsteps < 0) return NSPT_ERR_ARG;
+  const int L = (int)llround(sqrt((double)N));
+  if (L * L != N || flux <= 0) return NSPT_ERR_ARG;
+  int a = flux % L, bb = L;
+  while (a) { int t = bb % a; bb = a; a = t; }
+  if (bb != 1) return NSPT_ERR_ARG;
+  if (!(eps > 0.0) || !std::isfinite(eps)) return NSPT_ERR_ARG;
+  const size_t ubytes = (size_t)batch * 4 * (T + 1) * p.E * sizeof(double2);
+  const size_t ebytes = (size_t)batch * 4 * p.E * sizeof(double2);
+  if (overlaps(U, ubytes, P, ubytes) || overlaps(U, ubytes, eta_refresh, ebytes) ||
+      overlaps(P, ubytes, eta_refresh, ebytes))
+    return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_md(p)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  return md_run(p, (double2*)U, (double2*)P, (const double2*)eta_refresh, flux, eps, nsteps, opts->workspace,
+                (cudaStream_t)stream);
 }
 
 int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {

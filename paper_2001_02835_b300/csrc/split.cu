@@ -704,7 +704,7 @@ size_t nspt_split_ws_langevin(int N, int T, int nb, int M, int S) {
 }
 
 int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const double2* eta, double2* F, int flux,
-                        double eps, void* ws, cudaStream_t st) {
+                        double eps, void* ws, cudaStream_t st, int mode, const double2* Yin) {
   const int E = N * N;
   const long long T1 = T + 1;
   const long long specE = (long long)M * E;  // one spectrum
@@ -721,8 +721,9 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, 0, st));
   auto link = [&](int mu, int dag) { return SpecRef{w.specU + mu * specE, 4LL * M, dag}; };
   auto slot = [&](float4* base, int s) { return base + (long long)s * nb * specE; };
-  // 2. P1(mu,nu) = U_nu U_mu^+ (mu < nu) and Q(mu,nu) = U_mu U_nu: one launch of 18 products
   Job jobs[kMaxJobs];
+  if (mode != NSPT_LMODE_UPDATE) {
+  // 2. P1(mu,nu) = U_nu U_mu^+ (mu < nu) and Q(mu,nu) = U_mu U_nu: one launch of 18 products
   for (int i = 0; i < 6; ++i) {
     const int mu = kPairsS[i][0], nu = kPairsS[i][1];
     jobs[i] = Job{link(nu, 0), link(mu, 1), slot(w.specAcc, i), make_double2(1, 0), 0, 0};
@@ -769,6 +770,9 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
     TRYC(nspt_fft_inv_df(slot(w.specAcc, mu), w.serS + mu * T1 * E, 4 * T1, E, T, nb, M, 0, 0, st));
   // 5. drift and Y = i X
   TRYC(nspt_tek_drift(w.serS, w.imtr, eta, F, w.serY, N, T, (long long)nb * 4, eps, st));
+  }
+  if (mode == NSPT_LMODE_DRIFT) return NSPT_OK;
+  const double2* Ysrc = (mode == NSPT_LMODE_UPDATE) ? Yin : w.serY;
   // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
   TRYC(cudaMemsetAsync(w.serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
   TRYC(cudaMemsetAsync(w.serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
@@ -777,7 +781,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   for (int n = T; n >= 1; --n) {
     const int t = T - n + 1;
     const int Mt = 1 << (int)ceil(log2(2.0 * (t + 1)));
-    TRYC(nspt_fft_fwd_df(w.serY, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
+    TRYC(nspt_fft_fwd_df(Ysrc, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
     TRYC(nspt_fft_fwd_df(w.serR[cur], T1, w.spR, E, t - 1, nb * 4, Mt, 0, 0, st));
     Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0}, w.spC, make_double2(1, 0), 0, 0};
     TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));

@@ -12,8 +12,9 @@ int nspt_split_mul(int N, int T, int batch, int M, int slices, int log2r, bool r
                    const double2* B, double2* C, void* ws, cudaStream_t st);
 int nspt_split_bwd(int N, int T, int batch, int M, int slices, int log2r, const double2* A, const double2* B,
                    const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
+// mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE
 int nspt_split_langevin(int N, int T, int batch, int M, int slices, double2* U, const double2* eta, double2* F,
-                        int flux, double eps, void* ws, cudaStream_t st);
+                        int flux, double eps, void* ws, cudaStream_t st, int mode = 0, const double2* Yin = nullptr);
 // slices of Q planes of X (see slice_kernel): out bf16 [Q][S][2][N][Kp], exps [Q][N]
 int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
                      int P, void* out, int* exps, cudaStream_t st);

@@ -60,7 +60,7 @@ __global__ void drift_kernel(const double2* __restrict__ S, const double* __rest
     // X = eps F (+ noise at order 1), X^(0) = 0; Y = i X
     double2 x = make_double2(eps * f.x, eps * f.y);
     if (k == 0) x = make_double2(0.0, 0.0);
-    if (k == 1) {
+    if (k == 1 && eta) {
       const double2 e = eta[series * N * N + (long long)i * N + j];
       x.x += noise_amp * e.x;
       x.y += noise_amp * e.y;
@@ -97,5 +97,61 @@ cudaError_t nspt_tek_drift(const double2* S, double* imtr_ws, const double2* eta
   }
   dim3 grid(tiles, tiles, (unsigned)nmat);
   drift_kernel<<<grid, dim3(32, 8), 0, st>>>(S, imtr_ws, eta, F, Y, N, T, eps, sqrt(2.0 * eps));
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Molecular dynamics (leapfrog, Eq. 3 with beta absorbed): momentum series with
+// no order g^0, so order 0 of the drift is dropped.
+// ---------------------------------------------------------------------------
+namespace {
+
+// P[s][0] = 0, P[s][1] = eta[s], P[s][k>=2] = 0
+__global__ void md_refresh_kernel(double2* P, const double2* eta, int T, long long E, long long nseries) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = nseries * (T + 1) * E;
+  if (i >= n) return;
+  const long long e = i % E, k = (i / E) % (T + 1), s = i / (E * (T + 1));
+  P[i] = (k == 1) ? eta[s * E + e] : make_double2(0.0, 0.0);
+}
+
+// P^(k) += a F^(k) for k >= 1; P^(0) = 0
+__global__ void md_kick_kernel(double2* P, const double2* F, double a, int T, long long E, long long nseries) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = nseries * (T + 1) * E;
+  if (i >= n) return;
+  const long long k = (i / E) % (T + 1);
+  if (k == 0) { P[i] = make_double2(0.0, 0.0); return; }
+  const double2 f = F[i];
+  P[i] = make_double2(fma(a, f.x, P[i].x), fma(a, f.y, P[i].y));
+}
+
+// Y = i eps P, Y^(0) = 0
+__global__ void md_y_kernel(double2* Y, const double2* P, double eps, int T, long long E, long long nseries) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = nseries * (T + 1) * E;
+  if (i >= n) return;
+  const long long k = (i / E) % (T + 1);
+  const double2 p = P[i];
+  Y[i] = (k == 0) ? make_double2(0.0, 0.0) : make_double2(-eps * p.y, eps * p.x);
+}
+
+unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+cudaError_t nspt_md_refresh(double2* P, const double2* eta, int T, long long E, long long nseries, cudaStream_t st) {
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  md_refresh_kernel<<<blocks_for(nseries * (T + 1) * E), 256, 0, st>>>(P, eta, T, E, nseries);
+  return cudaGetLastError();
+}
+cudaError_t nspt_md_kick(double2* P, const double2* F, double a, int T, long long E, long long nseries, cudaStream_t st) {
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  md_kick_kernel<<<blocks_for(nseries * (T + 1) * E), 256, 0, st>>>(P, F, a, T, E, nseries);
+  return cudaGetLastError();
+}
+cudaError_t nspt_md_y(double2* Y, const double2* P, double eps, int T, long long E, long long nseries, cudaStream_t st) {
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  md_y_kernel<<<blocks_for(nseries * (T + 1) * E), 256, 0, st>>>(Y, P, eps, T, E, nseries);
   return cudaGetLastError();
 }
