@@ -306,6 +306,28 @@ def langevin_leg(torch, nspt, barrier, L=11, T=31, streams=8, flux=3, eps=0.01):
     return out
 
 
+def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
+    """One MD trajectory of the paper's length (40 leapfrog steps, momentum refreshed at its
+    start) of one SU(225) configuration at O(g^31) in the split form, with the time split
+    into the force phase (drift plus momentum kicks) and the link-update phase."""
+    g = syn.rng(syn.SEED_BASE + 5)
+    N = L * L
+    tU = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, flux, T, 1))).cuda()
+    tE = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, N, 4).reshape(1, 4, N, N))).cuda()
+    tP = torch.zeros_like(tU)
+    nspt.tek_md_trajectory(tU, tP, flux, eps, 2, eta=tE, algo="fft", prec="split")   # warm-up
+    nspt.profile_begin(200000)
+    ms = time_steps(torch, lambda: nspt.tek_md_trajectory(tU, tP, flux, eps, nsteps, eta=tE, algo="fft",
+                                                          prec="split"), 1, 0, barrier)
+    ph = nspt.profile_end()
+    out = {"ms_per_trajectory": ms, "md_steps": nsteps, "ms_per_md_step": ms / nsteps,
+           "force_ms": ph.get("md_force", (0.0, 0))[0], "link_update_ms": ph.get("md_link", (0.0, 0))[0],
+           "kernel_stages_ms": {k: v[0] for k, v in ph.items() if k not in ("md_force", "md_link")},
+           "note": "one configuration (4 links), split form; 10 trajectories = 10 x ms_per_trajectory"}
+    del tU, tE, tP
+    return out
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -447,6 +469,7 @@ def run_ours(args):
             extras["backward_%s_T%d" % (p, T)] = {"ms_per_batch": msb, "products_per_s": BATCH / (msb * 1e-3)}
         del gC
         extras["langevin_su121_T31_8streams"] = langevin_leg(torch, nspt, barrier)
+        extras["md_trajectory_su225_T31"] = md_leg(torch, nspt, barrier)
         msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
         extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}

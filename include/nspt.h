@@ -204,7 +204,10 @@ NSPT_API int nspt_order_ifft(const void* Ct, void* C, int N, int T, int batch, i
  * nspt_profile_end: wait for those events and sum their durations per stage
  *   (total_ms[s], launches[s] for s < nstages); returns the records used.
  * nspt_stage_name: name of stage s (fft_fwd, slice, gemm_mode, fft_inv,
- *   gemm_conv, tek_elementwise, gemm_tc, other).
+ *   gemm_conv, tek_elementwise, gemm_tc, other, md_force, md_link).  The last
+ *   two are phases of nspt_tek_md_trajectory (force with the momentum kicks,
+ *   link update): scopes around many launches whose "launches" count is the
+ *   number of scopes; their time overlaps the kernel stages inside them.
  */
 NSPT_API long long nspt_launch_count(void);
 NSPT_API int nspt_profile_begin(int max_records);

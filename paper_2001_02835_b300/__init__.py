@@ -272,7 +272,7 @@ def order_ifft(Ct: torch.Tensor, T: int) -> torch.Tensor:
     return C
 
 
-NSTAGES = 8
+NSTAGES = 10
 
 
 def launch_count() -> int:

@@ -416,13 +416,25 @@ int md_run(const Plan& p, double2* U, double2* P, const double2* eta, int flux, 
   int rc;
   if (eta) TRY(nspt_md_refresh(P, eta, T, E, ns, st));
   if (nsteps <= 0) return NSPT_OK;
-  if ((rc = md_phase(p, U, F, nullptr, flux, lws, st, NSPT_LMODE_DRIFT))) return rc;
+  // force phase: F(U) and the momentum kicks; link phase: U <- exp_star(i eps P) U
+  auto force = [&]() -> int {
+    ProfScope ps(NSPT_STAGE_MD_FORCE, st, 0);
+    return md_phase(p, U, F, nullptr, flux, lws, st, NSPT_LMODE_DRIFT);
+  };
+  if ((rc = force())) return rc;
   for (int s = 0; s < nsteps; ++s) {
-    TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));   // P_half = P + eps/2 F(U)
-    TRY(nspt_md_y(Y, P, eps, T, E, ns, st));            // Y = i eps P_half
-    if ((rc = md_phase(p, U, F, Y, flux, lws, st, NSPT_LMODE_UPDATE))) return rc;   // U <- exp_star(Y) U
-    if ((rc = md_phase(p, U, F, nullptr, flux, lws, st, NSPT_LMODE_DRIFT))) return rc;  // F(U')
-    TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));   // P' = P_half + eps/2 F(U')
+    {
+      ProfScope ps(NSPT_STAGE_MD_FORCE, st, 0);
+      TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));   // P_half = P + eps/2 F(U)
+    }
+    {
+      ProfScope ps(NSPT_STAGE_MD_LINK, st, 0);
+      TRY(nspt_md_y(Y, P, eps, T, E, ns, st));            // Y = i eps P_half
+      if ((rc = md_phase(p, U, F, Y, flux, lws, st, NSPT_LMODE_UPDATE))) return rc;  // U <- exp_star(Y) U
+    }
+    if ((rc = force())) return rc;                          // F(U')
+    ProfScope ps(NSPT_STAGE_MD_FORCE, st, 0);
+    TRY(nspt_md_kick(P, F, 0.5 * eps, T, E, ns, st));     // P' = P_half + eps/2 F(U')
   }
   return NSPT_OK;
 }

@@ -20,8 +20,8 @@ int g_cap = 0;
 int g_n = 0;
 std::vector<cudaEvent_t> g_ev;  // 2 per record
 std::vector<int> g_stage;
-const char* kNames[NSPT_STAGE_COUNT] = {"fft_fwd", "slice", "gemm_mode", "fft_inv", "gemm_conv",
-                                        "tek_elementwise", "gemm_tc", "other"};
+const char* kNames[NSPT_STAGE_COUNT] = {"fft_fwd", "slice",   "gemm_mode", "fft_inv",  "gemm_conv",
+                                        "tek_elementwise", "gemm_tc", "other", "md_force", "md_link"};
 }  // namespace
 
 ProfScope::ProfScope(int stage, cudaStream_t st, int nlaunch) : idx_(-1), st_(st) {

@@ -25,7 +25,7 @@ import paper_2001_02835_b300 as nspt  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["mul", "backward", "langevin"], default="mul")
+    ap.add_argument("--op", choices=["mul", "backward", "langevin", "md"], default="mul")
     ap.add_argument("--algo", default="fft")
     ap.add_argument("--prec", default="split")
     ap.add_argument("--N", type=int, default=225)
@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
+    ap.add_argument("--md-steps", type=int, default=40, help="leapfrog steps per call of --op md")
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if nspt.lib().nspt_init() != 0:
@@ -45,6 +46,12 @@ def main(argv=None):
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
         eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
         fn = lambda: nspt.tek_langevin_step(U, eta, 1, 0.01, **kw)  # noqa: E731
+    elif a.op == "md":
+        L = int(round(a.N ** 0.5))
+        U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
+        P = torch.zeros_like(U)
+        eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
+        fn = lambda: nspt.tek_md_trajectory(U, P, 1, 0.02, a.md_steps, eta=eta, **kw)  # noqa: E731
     else:
         A = torch.from_numpy(syn.series_batch(g, a.N, a.T, a.batch)).cuda()
         B = torch.from_numpy(syn.series_batch(g, a.N, a.T, a.batch)).cuda()
