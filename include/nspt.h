@@ -155,8 +155,9 @@ NSPT_API int nspt_polymat_mul_grouped(const nspt_polymat_desc* descs, int count,
                                       void* stream);
 
 /*
- * Autotuner of the split form's tensor-core tile width (128 x 32 or 128 x 48
- * output tiles, i.e. 64- or 96-column MMAs): times the grouped mode-GEMM
+ * Autotuner of the split form's tensor-core tile width (128 x 32, 128 x 40 or
+ * 128 x 48 output tiles, i.e. 64-, 80- or 96-column MMAs; at width 40 the left
+ * operand's digit slices are held in tensor memory): times the grouped mode-GEMM
  * launch of this group signature (every product's N and M x batch, slices)
  * with each width on the caller's workspace (sized as for
  * nspt_polymat_mul_grouped, contents overwritten), keeps the fastest for

@@ -524,7 +524,7 @@ int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, vo
       char key[8192];
       int bn = 0;
       while (fscanf(f, "%8191s %d", key, &bn) == 2) {
-        if (sig == key && (bn == 32 || bn == 48)) {
+        if (sig == key && (bn == 32 || bn == 40 || bn == 48)) {
           std::lock_guard<std::mutex> lk(g_tune_mu);
           g_tuned_bn[sig] = bn;
         }
@@ -538,7 +538,7 @@ int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, vo
   GroupLayout g = carve_group(ws, d, count, S);
   std::vector<SplitGemmArgs> args;
   TRYS(group_prepare(d, count, S, 0, g, args, st));
-  const int cands[2] = {32, 48};
+  const int cands[3] = {32, 40, 48};  // 40: left operand held in tensor memory
   float best = 1e30f;
   int best_bn = 48;
   cudaEvent_t e0, e1;
