@@ -38,36 +38,63 @@ __device__ __forceinline__ cdf ld(const float4* p) {
 __device__ __forceinline__ void st(float4* p, cdf a) { *p = make_float4(a.re.h, a.re.l, a.im.h, a.im.l); }
 
 // in: FP64 series, batch element b at in + b*in_stride*E, orders 0..T read
-//     (row k pre-scaled by 2^(log2s + k*log2r));  out: [batch][M][E] float4
-template <int M, int EB>
+//     (row k pre-scaled by 2^(log2s + k*log2r));  out: [batch][M][E] float4.
+// TOUT: every spectrum matrix is written transposed (out entry (l, j) holds
+// mode p of input entry (j, l), E = N*N).  A CTA then takes a block of 8 rows
+// x EB/8 columns instead of a strip, so that its loads are EB/8 consecutive
+// entries of each row and its stores 8 consecutive entries (128 bytes) of
+// each transposed row.
+template <int M, int EB, bool TOUT>
 __global__ void __launch_bounds__(EB * 8)
 fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* __restrict__ out, int E, int T,
-                  int log2s, int log2r) {
+                  int log2s, int log2r, int N) {
   extern __shared__ float4 sm[];  // [M][EB]
+  constexpr int CB = EB / 8;      // columns per block (TOUT)
   const int e = threadIdx.x, y = threadIdx.y, b = blockIdx.y;
-  const long long e0 = (long long)blockIdx.x * EB;
-  const bool valid = (e0 + e) < E;
+  long long e0 = (long long)blockIdx.x * EB;
+  bool valid = (e0 + e) < E;
+  int j0 = 0, l0 = 0;
   const double2* src = in + (long long)b * in_stride * E + e0 + e;
-  auto load_in = [&](int k) -> cdf {
-    cdf v = cdf{dfl{0.f, 0.f}, dfl{0.f, 0.f}};
-    if (k <= T && valid) {
-      const double2 x = src[(long long)k * E];
-      v = cdf{df_from_double(x.x), df_from_double(x.y)};
-      if (log2s != 0 || log2r != 0) {
-        float f1, f2;
-        pow2_pair(log2s + k * log2r, f1, f2);
-        v = cdf{df_scale(df_scale(v.re, f1), f2), df_scale(df_scale(v.im, f1), f2)};
-      }
+  if (TOUT) {
+    const int nlb = (N + CB - 1) / CB;
+    j0 = (blockIdx.x / nlb) * 8;
+    l0 = (blockIdx.x % nlb) * CB;
+    const int j = j0 + e / CB, l = l0 + e % CB;   // loaded entry of this thread
+    valid = j < N && l < N;
+    src = in + (long long)b * in_stride * E + (long long)j * N + l;
+  }
+  auto raw_in = [&](int k) -> double2 {
+    return (k <= T && valid) ? src[(long long)k * E] : make_double2(0.0, 0.0);
+  };
+  auto conv_in = [&](double2 x, int k) -> cdf {
+    cdf v = cdf{df_from_double(x.x), df_from_double(x.y)};
+    if (log2s != 0 || log2r != 0) {
+      float f1, f2;
+      pow2_pair(log2s + k * log2r, f1, f2);
+      v = cdf{df_scale(df_scale(v.re, f1), f2), df_scale(df_scale(v.im, f1), f2)};
     }
     return v;
   };
+  auto load_in = [&](int k) -> cdf { return conv_in(raw_in(k), k); };
   int h;  // span of the next radix-2 stage still to do
   if (M >= 4) {
     // first two DIF stages at once (radix 2^2), upper half of the input zero:
     // X[n] = x0 + x1, X[n + M/4] = (x0 - x1) w^2n, X[n + M/2] = (x0 + i x1) w^n,
     // X[n + 3M/4] = (x0 - i x1) w^3n, with x0 = x[n], x1 = x[n + M/4], n < M/4
-    for (int n = y; n < M / 4; n += 8) {
-      const cdf x0 = load_in(n), x1 = load_in(n + M / 4);
+    // every input of this thread is requested before the first butterfly
+    constexpr int NIT = M >= 4 ? (M / 4 + 7) / 8 : 1;
+    double2 r0[NIT], r1[NIT];
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int n = y + 8 * it;
+      r0[it] = (n < M / 4) ? raw_in(n) : make_double2(0.0, 0.0);
+      r1[it] = (n < M / 4) ? raw_in(n + M / 4) : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int n = y + 8 * it;
+      if (n >= M / 4) break;
+      const cdf x0 = conv_in(r0[it], n), x1 = conv_in(r1[it], n + M / 4);
       const cdf ix1 = cdf{df_neg(x1.im), x1.re};
       cdf o0 = cdf_add(x0, x1), o1 = cdf_sub(x0, x1), o2 = cdf_add(x0, ix1), o3 = cdf_sub(x0, ix1);
       if (n != 0) {
@@ -127,6 +154,14 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
     }
     __syncthreads();
   }
+  if (TOUT) {
+    // this thread stores smem column c = entry (j0 + e % 8, l0 + e / 8) at (l, j)
+    const int jj = e % 8, ll = e / 8, c = jj * CB + ll;
+    if (j0 + jj >= N || l0 + ll >= N) return;
+    float4* dst = out + (long long)b * M * E + (long long)(l0 + ll) * N + j0 + jj;
+    for (int i = y; i < M; i += 8) dst[(long long)bitrev<M>(i) * E] = sm[i * EB + c];
+    return;
+  }
   if (!valid) return;
   float4* dst = out + (long long)b * M * E + e0 + e;
   for (int i = y; i < M; i += 8) dst[(long long)bitrev<M>(i) * E] = sm[i * EB + e];
@@ -153,8 +188,22 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   const long long e0 = (long long)blockIdx.x * EB;
   const bool valid = (e0 + e) < E;
   const float4* src = in + (long long)b * M * E + e0 + e;
-  for (int p = y; p < M; p += 8)
-    sm[bitrev<M>(p) * EB + e] = valid ? src[(long long)p * E] : make_float4(0.f, 0.f, 0.f, 0.f);
+  // loads in groups of up to 16 per thread, all in flight before their stores
+  constexpr int NL = (M + 7) / 8, G = NL < 16 ? NL : 16;
+#pragma unroll 1
+  for (int g0 = 0; g0 < NL; g0 += G) {
+    float4 v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int p = y + 8 * (g0 + i);
+      v[i] = (valid && p < M) ? src[(long long)p * E] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int p = y + 8 * (g0 + i);
+      if (p < M) sm[bitrev<M>(p) * EB + e] = v[i];
+    }
+  }
   __syncthreads();
   // DIT stages of spans 1 .. M/4: radix 2^2 steps over spans (h, 2h) while two are left
   int h = 1;
@@ -228,14 +277,16 @@ constexpr int strip_entries() { return M <= 128 ? 32 : (M == 256 ? 16 : 8); }
 
 template <int M>
 cudaError_t launch_fwd(const double2* in, long long ins, float4* out, int E, int T, int batch, int ls, int lr,
-                       cudaStream_t st) {
+                       int tout_n, cudaStream_t st) {
   constexpr int EB = strip_entries<M>();
   const size_t smem = (size_t)M * EB * sizeof(float4);
-  auto kern = fft_fwd_df_kernel<M, EB>;
+  auto kern = tout_n ? fft_fwd_df_kernel<M, EB, true> : fft_fwd_df_kernel<M, EB, false>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr);
+  const long long blocks = tout_n ? (long long)((tout_n + 7) / 8) * ((tout_n + EB / 8 - 1) / (EB / 8))
+                                  : ((long long)E + EB - 1) / EB;
+  dim3 grid((unsigned)blocks, batch), block(EB, 8);
+  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr, tout_n);
   return cudaGetLastError();
 }
 
@@ -255,11 +306,12 @@ cudaError_t launch_inv(const float4* in, double2* out, long long outs, int E, in
 }  // namespace
 
 cudaError_t nspt_fft_fwd_df(const double2* in, long long in_stride, float4* out, int E, int t, int batch, int M,
-                            int log2s, int log2r, cudaStream_t st) {
+                            int log2s, int log2r, cudaStream_t st, int transpose_n) {
   if (2 * (t + 1) > M) return cudaErrorInvalidValue;
+  if (transpose_n && (long long)transpose_n * transpose_n != E) return cudaErrorInvalidValue;
   ProfScope ps(NSPT_STAGE_FFT_FWD, st);
   switch (M) {
-#define NSPT_CASE(m) case m: return launch_fwd<m>(in, in_stride, out, E, t, batch, log2s, log2r, st);
+#define NSPT_CASE(m) case m: return launch_fwd<m>(in, in_stride, out, E, t, batch, log2s, log2r, transpose_n, st);
     NSPT_CASE(2) NSPT_CASE(4) NSPT_CASE(8) NSPT_CASE(16) NSPT_CASE(32) NSPT_CASE(64) NSPT_CASE(128)
     NSPT_CASE(256) NSPT_CASE(512)
 #undef NSPT_CASE

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -192,9 +193,80 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   }
 }
 
+// Row form without shared memory (trans = 0, double-float spectra): one warp
+// per output row; every lane loads its NP pairs of adjacent entries up front
+// (all loads in flight at once), the row exponent is a warp max over the
+// registers, and each pair leaves as one bf16x2 per plane, so a warp store is
+// 128 contiguous bytes.  Same output as slice_kernel.
+template <int S, int NP>
+__global__ void __launch_bounds__(256)
+slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int rev, int conj, int N, int Kp, int P,
+                  __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+  const int q = blockIdx.y;
+  const int b = q / M, p = q % M;
+  const int sp = rev ? (M - p) % M : p;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r = blockIdx.x * RB + warp;
+  if (r >= N) return;
+  const float4* src = X + ((long long)b * bstride + sp) * N * N + (long long)r * N;
+  float4 v[NP][2];
+#pragma unroll
+  for (int t = 0; t < NP; ++t) {
+    const int k = 2 * lane + 64 * t;
+    v[t][0] = (k < N) ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[t][1] = (k + 1 < N) ? src[k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int mx = -100000;
+#pragma unroll
+  for (int t = 0; t < NP; ++t) mx = max(mx, max(exp_bound(v[t][0]), exp_bound(v[t][1])));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
+  if (lane == 0) exps[(long long)q * N + r] = e;
+  const long long plane = (long long)N * Kp;
+  __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
+#pragma unroll
+  for (int t = 0; t < NP; ++t) {
+    const int k = 2 * lane + 64 * t;
+    if (k >= N) break;
+    const float4 v0 = conj ? conj_of(v[t][0]) : v[t][0];
+    const float4 v1 = conj ? conj_of(v[t][1]) : v[t][1];
+    float re0[S], im0[S], re1[S], im1[S];
+    digits_re_im<S>(v0, e, re0, im0);
+    digits_re_im<S>(v1, e, re1, im1);
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+      *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
+      *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
+      if (P == 3)
+        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 2) * plane + k) =
+            __floats2bfloat162_rn(-re0[i], -re1[i]);
+    }
+  }
+}
+
+template <int S, int NP>
+int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int conj, int N, int Kp, int Q, int P,
+                      __nv_bfloat16* out, int* exps, cudaStream_t st) {
+  dim3 grid((N + RB - 1) / RB, Q);
+  ProfScope ps(NSPT_STAGE_SLICE, st);
+  slice_rows_kernel<S, NP><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
+  return NSPT_OK;
+}
+
 template <int S, typename InT>
 int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q, int P,
                  __nv_bfloat16* out, int* exps, cudaStream_t st) {
+  if constexpr (std::is_same<InT, float4>::value) {
+    if (!trans && N <= 512) {
+      if (N <= 64) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      if (N <= 128) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      if (N <= 256) return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      return launch_slice_rows<S, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+    }
+  }
   const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
   cudaError_t e = cudaFuncSetAttribute(slice_kernel<S, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
@@ -378,11 +450,12 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
   if (rescale_auto) TRYS(nspt_split_fit_rescale(A, B, N, T, batch, w.expA, &log2r, st));
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
+  // (B's spectra are written transposed, so that both operands are sliced by rows)
   TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
-  TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-  // a2: slices of A~_q (rows) and of B~_q^T (columns of B~_q)
+  TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st, N));
+  // a2: slices of A~_q (rows) and of B~_q^T (rows of the transposed spectra)
   TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
-  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
+  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, st));
   // a3: mode GEMMs on the tensor cores
   TRYS(gemm(w, N, Q, S, st));
   // a4: inverse transform, truncation, unscale 2^(-k log2r)
@@ -409,8 +482,8 @@ int nspt_split_bwd(int N, int T, int batch, int M, int S, int log2r, const doubl
   }
   if (gB) {
     // gB~_p = (A~_p)^H G~_p
-    TRYC(nspt_fft_fwd_df(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st));
-    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 1, N, Q, 2, w.slA, w.expA, st));
+    TRYC(nspt_fft_fwd_df(A, T + 1, w.Bt, E, T, batch, M, 0, log2r, st, N));   // A~ transposed
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 1, N, Q, 2, w.slA, w.expA, st));
     TRYS(nspt_split_slice_df(S, Gt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
     TRYS(gemm(w, N, Q, S, st));
     TRYC(nspt_fft_inv_df(w.Ct, gB, T + 1, E, T, batch, M, 0, -log2r, st));
@@ -490,9 +563,9 @@ int group_prepare(const nspt_polymat_desc* d, int count, int S, int log2r, const
     const int E = N * N, Q = b * M;
     const SplitWs& w = g.ws[i];
     TRYC(nspt_fft_fwd_df((const double2*)d[i].A, T + 1, w.At, E, T, b, M, 0, log2r, st));
-    TRYC(nspt_fft_fwd_df((const double2*)d[i].B, T + 1, w.Bt, E, T, b, M, 0, log2r, st));
+    TRYC(nspt_fft_fwd_df((const double2*)d[i].B, T + 1, w.Bt, E, T, b, M, 0, log2r, st, N));
     TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
-    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 1, 0, N, Q, 3, w.slB, w.expB, st));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, st));
     args.push_back(gemm_args(w, N, Q, S));
   }
   return NSPT_OK;

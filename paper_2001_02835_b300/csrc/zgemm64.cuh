@@ -36,9 +36,10 @@ cudaError_t nspt_fft_inv64(const double2* in, double2* out, long long out_stride
 cudaError_t nspt_fft_inv64_df(const float4* in, double2* out, long long out_stride, int E, int N, int t, int batch,
                               int M, int log2u, int log2r, cudaStream_t st);
 // Double-float order FFTs of the split form (fftdf.cu): FP64 series in,
-// float4 (re_hi, re_lo, im_hi, im_lo) spectrum out, and back.
+// float4 (re_hi, re_lo, im_hi, im_lo) spectrum out, and back.  transpose_n = N
+// writes every spectrum matrix transposed (E = N*N); 0 keeps the layout.
 cudaError_t nspt_fft_fwd_df(const double2* in, long long in_stride, float4* out, int E, int t, int batch, int M,
-                            int log2s, int log2r, cudaStream_t st);
+                            int log2s, int log2r, cudaStream_t st, int transpose_n = 0);
 cudaError_t nspt_fft_inv_df(const float4* in, double2* out, long long out_stride, int E, int t, int batch, int M,
                             int log2u, int log2r, cudaStream_t st, double post = 1.0, int add_identity = 0,
                             int N = 0, int kmin = 0);
