@@ -26,89 +26,14 @@
 #include "split_gemm.cuh"
 #include "zgemm64.cuh"
 #include "dfloat.cuh"
+#include "digits.cuh"
 #include "tek.cuh"
 
 namespace {
 
 int g_num_sms = 0;
 
-// exact int -> float for |d| < 2^22 without a conversion instruction
-// (1.5 * 2^23 + d has d in its low mantissa bits)
-__device__ __forceinline__ float small_int_to_float(int d) {
-  return __int_as_float(0x4B400000 + d) - 12582912.0f;
-}
-
-template <int S>
-__device__ __forceinline__ void to_digits(double x, int e, float (&s)[S]) {
-  constexpr int W = 8 * S - 1;
-  const long long bits = __double_as_longlong(x);
-  const int bexp = (int)((bits >> 52) & 0x7FF);
-  unsigned long long X = 0;
-  if (bexp != 0) {
-    const unsigned long long mant = ((unsigned long long)bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = 1075 + e - W - bexp;
-    if (sh <= 0) X = mant << (-sh);
-    else if (sh < 64) X = (mant + (1ull << (sh - 1))) >> sh;
-  }
-  const float sign = bits < 0 ? -1.f : 1.f;
-#pragma unroll
-  for (int i = S - 1; i >= 1; --i) {
-    int d = (int)(X & 255ull);
-    X >>= 8;
-    if (d > 128) { d -= 256; X += 1; }
-    s[i] = sign * small_int_to_float(d) * __int_as_float((127 - 8 * i) << 23);
-  }
-  s[0] = sign * small_int_to_float((int)X);
-}
-
-// digits of a double-float value x = hi + lo (|x| < 2^e) in FP32 arithmetic:
-// with v = x 2^-e (|v| < 1) and sigma_i = 1.5 * 2^(16 - 8i), t = (v + sigma_i) -
-// sigma_i rounds v to the nearest multiple of 2^(-7-8i) exactly, v - t is
-// exact, and t * 2^7 = d_i 2^(-8i) is the stored slice value.  Digits 0..2
-// come from hi alone (|lo| < 2^-25 lies below their grid); lo joins the
-// residual before digit 3, so |d_i| <= 128 for i < 3 and <= 192 after.
-template <int S>
-__device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
-  float f1, f2;
-  pow2_pair(-e, f1, f2);
-  float v = (x.h * f1) * f2;
-  const float lo = (x.l * f1) * f2;
-#pragma unroll
-  for (int i = 0; i < S; ++i) {
-    if (i == 3) v = v + lo;
-    const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
-    const float t = (v + sig) - sig;
-    v = v - t;
-    s[i] = t * 128.f;
-  }
-}
-
-// smallest e with |x| < 2^e for every part, from the exponent field
-__device__ __forceinline__ int exp_bound(double2 v) {
-  const int a = (int)((__double_as_longlong(v.x) >> 52) & 0x7FF), b = (int)((__double_as_longlong(v.y) >> 52) & 0x7FF);
-  const int m = max(a, b);
-  return m == 0 ? -100000 : m - 1022;
-}
-__device__ __forceinline__ int exp_bound(float4 v) {
-  // |hi + lo| < 2^(exponent(hi) + 1) since |lo| <= ulp(hi)/2
-  const int a = (int)((__float_as_uint(v.x) >> 23) & 0xFF), b = (int)((__float_as_uint(v.z) >> 23) & 0xFF);
-  const int m = max(a, b);
-  return m == 0 ? -100000 : m - 126;
-}
-__device__ __forceinline__ double2 conj_of(double2 v) { return make_double2(v.x, -v.y); }
-__device__ __forceinline__ float4 conj_of(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }
-__device__ __forceinline__ double2 zero_of(double2) { return make_double2(0.0, 0.0); }
-__device__ __forceinline__ float4 zero_of(float4) { return make_float4(0.f, 0.f, 0.f, 0.f); }
-template <int S>
-__device__ __forceinline__ void digits_re_im(double2 v, int e, float (&re)[S], float (&im)[S]) {
-  to_digits<S>(v.x, e, re);
-  to_digits<S>(v.y, e, im);
-}
-template <int S>
-__device__ __forceinline__ void digits_re_im(float4 v, int e, float (&re)[S], float (&im)[S]) {
-  to_digits<S>(dfl{v.x, v.y}, e, re);
-  to_digits<S>(dfl{v.z, v.w}, e, im);
-}
+using namespace digits;
 
 // grid (ceil(N/RB), Q); block 256.  Output row r of plane q is row r of the
 // source matrix (trans = 0) or its column r (trans = 1), conjugated if conj;
@@ -194,12 +119,18 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
 }
 
 // Row form without shared memory (trans = 0, double-float spectra): one warp
-// per output row; every lane loads its NP pairs of adjacent entries up front
-// (all loads in flight at once), the row exponent is a warp max over the
-// registers, and each pair leaves as one bf16x2 per plane, so a warp store is
-// 128 contiguous bytes.  Same output as slice_kernel.
-template <int S, int NP>
-__global__ void __launch_bounds__(256)
+// per output row; every lane loads its NQ quads of four adjacent entries up
+// front (all loads in flight at once), the row exponent is a warp max over the
+// registers, and the digits are produced one digit index at a time for the
+// four entries, each leaving as one 8-byte bf16x4 store per plane (256
+// contiguous bytes per warp store).  Same output as slice_kernel.
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
+template <int S, int NQ>
+__global__ void __launch_bounds__(256, NQ <= 2 ? 4 : 2)
 slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int rev, int conj, int N, int Kp, int P,
                   __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   const int q = blockIdx.y;
@@ -209,48 +140,69 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   const int r = blockIdx.x * RB + warp;
   if (r >= N) return;
   const float4* src = X + ((long long)b * bstride + sp) * N * N + (long long)r * N;
-  float4 v[NP][2];
+  float4 v[NQ][4];
 #pragma unroll
-  for (int t = 0; t < NP; ++t) {
-    const int k = 2 * lane + 64 * t;
-    v[t][0] = (k < N) ? src[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-    v[t][1] = (k + 1 < N) ? src[k + 1] : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int t = 0; t < NQ; ++t) {
+    const int k = 4 * lane + 128 * t;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[t][c] = (k + c < N) ? src[k + c] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   int mx = -100000;
 #pragma unroll
-  for (int t = 0; t < NP; ++t) mx = max(mx, max(exp_bound(v[t][0]), exp_bound(v[t][1])));
+  for (int t = 0; t < NQ; ++t)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) mx = max(mx, exp_bound(v[t][c]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
   if (lane == 0) exps[(long long)q * N + r] = e;
   const long long plane = (long long)N * Kp;
   __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
+  float f1, f2;
+  pow2_pair(-e, f1, f2);
 #pragma unroll
-  for (int t = 0; t < NP; ++t) {
-    const int k = 2 * lane + 64 * t;
+  for (int t = 0; t < NQ; ++t) {
+    const int k = 4 * lane + 128 * t;
     if (k >= N) break;
-    const float4 v0 = conj ? conj_of(v[t][0]) : v[t][0];
-    const float4 v1 = conj ? conj_of(v[t][1]) : v[t][1];
-    float re0[S], im0[S], re1[S], im1[S];
-    digits_re_im<S>(v0, e, re0, im0);
-    digits_re_im<S>(v1, e, re1, im1);
+    // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the four entries
+    float vr[4], vi[4], lr[4], li[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float4 x = v[t][c];
+      const float sg = conj ? -1.f : 1.f;
+      vr[c] = (x.x * f1) * f2;
+      lr[c] = (x.y * f1) * f2;
+      vi[c] = sg * ((x.z * f1) * f2);
+      li[c] = sg * ((x.w * f1) * f2);
+    }
 #pragma unroll
     for (int i = 0; i < S; ++i) {
-      *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
-      *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
-      if (P == 3)
-        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 2) * plane + k) =
-            __floats2bfloat162_rn(-re0[i], -re1[i]);
+      // digit i: t = v rounded to a multiple of 2^(-7-8i); lo joins before digit 3 (see to_digits)
+      const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
+      float dr[4], di[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (i == 3) { vr[c] = vr[c] + lr[c]; vi[c] = vi[c] + li[c]; }
+        const float tr = (vr[c] + sig) - sig, ti = (vi[c] + sig) - sig;
+        vr[c] = vr[c] - tr;
+        vi[c] = vi[c] - ti;
+        dr[c] = tr * 128.f;
+        di[c] = ti * 128.f;
+      }
+      __nv_bfloat16* o = orow + (long long)P * i * plane + k;
+      *reinterpret_cast<uint2*>(o) = pack_bf16x4(dr[0], dr[1], dr[2], dr[3]);
+      *reinterpret_cast<uint2*>(o + plane) = pack_bf16x4(di[0], di[1], di[2], di[3]);
+      if (P == 3) *reinterpret_cast<uint2*>(o + 2 * plane) = pack_bf16x4(-dr[0], -dr[1], -dr[2], -dr[3]);
     }
   }
 }
 
-template <int S, int NP>
+template <int S, int NQ>
 int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int conj, int N, int Kp, int Q, int P,
                       __nv_bfloat16* out, int* exps, cudaStream_t st) {
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_rows_kernel<S, NP><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+  slice_rows_kernel<S, NQ><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
@@ -261,10 +213,9 @@ int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int
                  __nv_bfloat16* out, int* exps, cudaStream_t st) {
   if constexpr (std::is_same<InT, float4>::value) {
     if (!trans && N <= 512) {
-      if (N <= 64) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
-      if (N <= 128) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
-      if (N <= 256) return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
-      return launch_slice_rows<S, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      if (N <= 128) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      if (N <= 256) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
     }
   }
   const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
