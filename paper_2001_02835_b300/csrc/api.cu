@@ -290,19 +290,48 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     }
     if (mode == NSPT_LMODE_DRIFT) return NSPT_OK;
     const double2* Ysrc = (mode == NSPT_LMODE_UPDATE) ? Yin : serY;
-    // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
-    TRY(cudaMemsetAsync(serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
-    TRY(cudaMemsetAsync(serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
-    TRY(add_identity(serR[0], T1, N, (long long)nb * 4, st));
-    int cur = 0;
-    for (int n = T; n >= 1; --n) {
-      const int t = T - n + 1;
+    // 6. exp_star(Y) by Paterson-Stockmeyer in the truncated ring (Y^(0) = 0, so Y^k
+    //    starts at order k and every product runs at its own truncation on
+    //    order-shifted series): Y^2 .. Y^s, then Q_j = B_j + Y^s Q_{j+1} for
+    //    j = r-1 .. 0 with B_j = sum_{i<s} Y^i / (js+i)!, Q_j needed to order T - s j
+    const long long ns = (long long)nb * 4, ser4 = ns * T1 * E;
+    // c^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
+    auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
       const int Mt = next_pow2(2 * (t + 1));
-      TRY(nspt_fft_fwd64(Ysrc, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
-      TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, t - 1, nb * 4, Mt, 0, 0, st));
+      TRY(nspt_fft_fwd64(a, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
+      TRY(nspt_fft_fwd64(b, T1, spR, (int)E, t, nb * 4, Mt, 0, 0, st));
       ZgemmParams P = zg(ZG_MODE, spY, Mt, spR, Mt, spC, Mt, N, Mt, t);
       TRY(nspt_zgemm64(P, nb * 4, st));
-      TRY(nspt_fft_inv64(spC, serR[cur ^ 1], T1, (int)E, N, t, nb * 4, Mt, 0, 0, 1.0 / n, 1, st));
+      TRY(nspt_fft_inv64(spC, c, T1, (int)E, N, t, nb * 4, Mt, 0, 0, 1.0, 0, st));
+      return NSPT_OK;
+    };
+    const int sb = nspt_ps_block(T), r = T / sb;
+    const double2* Yp[NSPT_PS_MAX_BLOCK + 1] = {nullptr, Ysrc};
+    int rc;
+    for (int k = 2; k <= sb; ++k) {
+      double2* Pk = serTmp + (k - 2) * ser4;
+      TRY(cudaMemsetAsync(Pk, 0, (size_t)ser4 * sizeof(double2), st));  // orders below k stay 0
+      if ((rc = star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k))) return rc;
+      Yp[k] = Pk;
+    }
+    double2* prod = serTmp + (NSPT_PS_MAX_BLOCK - 1) * ser4;
+    auto block = [&](int j) {
+      PsTerms tm{};
+      double f = 1.0;  // 1 / (j s)!
+      for (int n = 2; n <= j * sb; ++n) f /= n;
+      for (int i = 0; i < sb; ++i) {
+        if (i > 0) f /= (j * sb + i);
+        tm.c[i] = (j * sb + i <= T) ? f : 0.0;
+        if (i > 0) tm.P[i] = Yp[i];
+      }
+      return tm;
+    };
+    int cur = 0;
+    TRY(nspt_ps_combine(serR[0], block(r), sb - 1, nullptr, sb, T - sb * r, T, N, ns, st));
+    for (int j = r - 1; j >= 0; --j) {
+      const int t = T - sb * (j + 1);
+      if ((rc = star_t(Yp[sb] + sb * E, serR[cur], prod, t))) return rc;  // (Y^s Q_{j+1}) from order s
+      TRY(nspt_ps_combine(serR[cur ^ 1], block(j), sb - 1, prod, sb, T - sb * j, T, N, ns, st));
       cur ^= 1;
     }
     // 7. U <- exp_star(i X) * U  (spectrum of the old U is still in specU);

@@ -797,23 +797,53 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   }
   if (mode == NSPT_LMODE_DRIFT) return NSPT_OK;
   const double2* Ysrc = (mode == NSPT_LMODE_UPDATE) ? Yin : w.serY;
-  // 6. exp_star(Y) by Horner with shrinking truncation: R_n = 1 + (Y * R_{n+1}) / n
-  TRYC(cudaMemsetAsync(w.serR[0], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
-  TRYC(cudaMemsetAsync(w.serR[1], 0, (size_t)nb * 4 * T1 * E * sizeof(double2), st));
-  TRYC(set_identity_order0(w.serR[0], T1, N, (long long)nb * 4, st));
-  int cur = 0;
-  for (int n = T; n >= 1; --n) {
-    const int t = T - n + 1;
-    const int Mt = 1 << (int)ceil(log2(2.0 * (t + 1)));
-    TRYC(nspt_fft_fwd_df(Ysrc, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
-    TRYC(nspt_fft_fwd_df(w.serR[cur], T1, w.spR, E, t - 1, nb * 4, Mt, 0, 0, st));
+  // 6. exp_star(Y) by Paterson-Stockmeyer in the truncated ring (Y^(0) = 0, so Y^k
+  //    starts at order k and every product runs at its own truncation on
+  //    order-shifted series): Y^2 .. Y^s, then Q_j = B_j + Y^s Q_{j+1} for
+  //    j = r-1 .. 0 with B_j = sum_{i<s} Y^i / (js+i)!, Q_j needed to order T - s j
+  const long long ns = (long long)nb * 4, ser4 = ns * T1 * E;
+  // C^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
+  auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
+    const int Mt = nspt_pow2_at_least(2 * (t + 1));
+    TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
+    TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, 0, st));
     Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0}, w.spC, make_double2(1, 0), 0, 0};
     TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
-    TRYC(nspt_fft_inv_df(w.spC, w.serR[cur ^ 1], T1, E, t, nb * 4, Mt, 0, 0, st, 1.0 / n, 1, N));
+    TRYC(nspt_fft_inv_df(w.spC, c, T1, E, t, nb * 4, Mt, 0, 0, st));
+    return NSPT_OK;
+  };
+  const int sb = nspt_ps_block(T), r = T / sb;
+  const double2* Yp[NSPT_PS_MAX_BLOCK + 1] = {nullptr, Ysrc};
+  for (int k = 2; k <= sb; ++k) {
+    double2* Pk = w.serTmp + (k - 2) * ser4;
+    TRYC(cudaMemsetAsync(Pk, 0, (size_t)ser4 * sizeof(double2), st));  // orders below k stay 0
+    TRYS(star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k));
+    Yp[k] = Pk;
+  }
+  double2* prod = w.serTmp + (NSPT_PS_MAX_BLOCK - 1) * ser4;
+  double2* Qs[2] = {w.serR[0], w.serR[1]};
+  auto block = [&](int j) {
+    PsTerms tm{};
+    double f = 1.0;  // 1 / (j s)!
+    for (int n = 2; n <= j * sb; ++n) f /= n;
+    for (int i = 0; i < sb; ++i) {
+      if (i > 0) f /= (j * sb + i);
+      tm.c[i] = (j * sb + i <= T) ? f : 0.0;
+      if (i > 0) tm.P[i] = Yp[i];
+    }
+    return tm;
+  };
+  int cur = 0;
+  TRYC(nspt_ps_combine(Qs[0], block(r), sb - 1, nullptr, sb, T - sb * r, T, N, ns, st));
+  for (int j = r - 1; j >= 0; --j) {
+    const int t = T - sb * (j + 1);
+    TRYS(star_t(Yp[sb] + sb * E, Qs[cur], prod, t));  // (Y^s Q_{j+1}) from order s
+    TRYC(nspt_ps_combine(Qs[cur ^ 1], block(j), sb - 1, prod, sb, T - sb * j, T, N, ns, st));
     cur ^= 1;
   }
+  double2* const expY = Qs[cur];
   // 7. U <- exp_star(i X) U, order 0 untouched
-  TRYC(nspt_fft_fwd_df(w.serR[cur], T1, w.spR, E, T, nb * 4, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(expY, T1, w.spR, E, T, nb * 4, M, 0, 0, st));
   Job J{SpecRef{w.spR, (long long)M, 0}, SpecRef{w.specU, (long long)M, 0}, w.spC, make_double2(1, 0), 0, 0};
   TRYS(run_jobs(w, &J, 1, N, nb * 4, M, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
   TRYC(nspt_fft_inv_df(w.spC, U, T1, E, T, nb * 4, M, 0, 0, st, 1.0, 0, N, 1));

@@ -138,7 +138,40 @@ __global__ void md_y_kernel(double2* Y, const double2* P, double eps, int T, lon
 
 unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
 
+// Q^(k) = c_0 delta_{k0} 1 + sum_{i=1}^{m} c_i (Y^i)^(k) + prod^(k - shift) [k >= shift], k = 0..tq;
+// series of T1 orders, nseries of them
+__global__ void ps_combine_kernel(double2* __restrict__ Q, PsTerms t, int m, const double2* __restrict__ prod,
+                                  int shift, int tq, int T1, int N, long long E, long long nseries) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = nseries * (tq + 1) * E;
+  if (i >= n) return;
+  const long long e = i % E, k = (i / E) % (tq + 1), sr = i / (E * (tq + 1));
+  const long long idx = (sr * T1 + k) * E + e;
+  double2 v = make_double2((k == 0 && e / N == e % N) ? t.c[0] : 0.0, 0.0);
+  for (int j = 1; j <= m; ++j) {
+    const double2 p = t.P[j][idx];
+    v.x = fma(t.c[j], p.x, v.x);
+    v.y = fma(t.c[j], p.y, v.y);
+  }
+  if (prod && k >= shift) {
+    const double2 p = prod[(sr * T1 + k - shift) * E + e];
+    v.x += p.x;
+    v.y += p.y;
+  }
+  Q[idx] = v;
+}
+
 }  // namespace
+
+cudaError_t nspt_ps_combine(double2* Q, const PsTerms& t, int m, const double2* prod, int shift, int tq, int T, int N,
+                            long long nseries, cudaStream_t st) {
+  if (m < 0 || m >= NSPT_PS_MAX_BLOCK || tq < 0 || tq > T) return cudaErrorInvalidValue;
+  const long long E = (long long)N * N;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  ps_combine_kernel<<<blocks_for(nseries * (tq + 1) * E), 256, 0, st>>>(Q, t, m, prod, shift, tq, T + 1, N, E,
+                                                                       nseries);
+  return cudaGetLastError();
+}
 
 cudaError_t nspt_md_refresh(double2* P, const double2* eta, int T, long long E, long long nseries, cudaStream_t st) {
   ProfScope ps(NSPT_STAGE_TEK, st);

@@ -10,3 +10,34 @@ cudaError_t nspt_md_kick(double2* P, const double2* F, double a, int T, long lon
 cudaError_t nspt_md_y(double2* Y, const double2* P, double eps, int T, long long E, long long nseries, cudaStream_t st);
 // phases of one Langevin / MD evaluation
 enum { NSPT_LMODE_STEP = 0, NSPT_LMODE_DRIFT = 1, NSPT_LMODE_UPDATE = 2 };
+
+// exp_star(Y) (Y^(0) = 0) by Paterson-Stockmeyer in the truncated ring:
+// Y^2 .. Y^s, then Horner in Y^s, Q_j = B_j + Y^s Q_{j+1}, B_j = sum_{i<s} Y^i / (js+i)!.
+// Block size s <= NSPT_PS_MAX_BLOCK minimising the mode-GEMM count when every
+// product runs at its own truncation (Y^k starts at order k).
+constexpr int NSPT_PS_MAX_BLOCK = 4;
+inline int nspt_pow2_at_least(int x) {
+  int m = 1;
+  while (m < x) m <<= 1;
+  return m;
+}
+inline long long nspt_ps_cost(int T, int s) {
+  long long c = 0;
+  for (int k = 2; k <= s; ++k) c += nspt_pow2_at_least(2 * (T - k + 1));
+  for (int j = T / s - 1; j >= 0; --j) c += nspt_pow2_at_least(2 * (T - s * (j + 1) + 1));
+  return c;
+}
+inline int nspt_ps_block(int T) {
+  int best = 1;
+  for (int s = 2; s <= NSPT_PS_MAX_BLOCK && s <= T; ++s)
+    if (nspt_ps_cost(T, s) < nspt_ps_cost(T, best)) best = s;
+  return best;
+}
+// terms of one block: P[i] = Y^i (i >= 1; P[0] unused), c[i] its coefficient, c[0] that of 1
+struct PsTerms {
+  const double2* P[NSPT_PS_MAX_BLOCK];
+  double c[NSPT_PS_MAX_BLOCK];
+};
+// Q^(k) = c_0 delta_{k0} 1 + sum_{i=1}^{m} c_i (Y^i)^(k) + prod^(k - shift) (k >= shift), k = 0..tq
+cudaError_t nspt_ps_combine(double2* Q, const PsTerms& t, int m, const double2* prod, int shift, int tq, int T, int N,
+                            long long nseries, cudaStream_t st);
