@@ -613,6 +613,7 @@ struct SpecRef {
   const float4* p;  // batch element b, mode m at p + (b * bs + m) * N^2
   long long bs;
   int dag;          // use (X~_{(M-p) mod M})^H
+  int tr = 0;       // the stored matrices are the transposed spectra X~^T
 };
 
 struct Job {
@@ -651,7 +652,7 @@ cudaError_t set_identity_order0(double2* X, long long stride_mats, int N, long l
 
 struct LangevinWs {
   int* err;
-  float4 *specU, *specAcc, *specPQ, *specIn, *spY, *spR, *spC;
+  float4 *specU, *specUT, *specAcc, *specPQ, *specIn, *spY, *spR, *spC;  // specUT: transposed link spectra
   double2 *serTmp, *serS, *serY, *serR[2];
   double* imtr;
   __nv_bfloat16 *slA[kMaxJobs], *slB[kMaxJobs];
@@ -666,6 +667,7 @@ LangevinWs carve_langevin(void* base, int N, int T, int nb, int M, int S) {
   const long long spec = (long long)nb * M * E, ser = (long long)nb * T1 * E;
   w.err = c.take<int>(64);
   w.specU = c.take<float4>(4 * spec);
+  w.specUT = c.take<float4>(4 * spec);
   w.specAcc = c.take<float4>(18 * spec);
   w.specPQ = c.take<float4>(18 * spec);
   w.specIn = c.take<float4>(4 * spec);
@@ -708,9 +710,9 @@ int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int
     int* ea = eA_big ? eA_big : w.expA[j];
     int* eb = eB_big ? eB_big : w.expB[j];
     // left operand: rows of A (dagger: conjugated columns of the reversed spectrum)
-    TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag, J.a.dag, N, nb * M, 2, sa, ea, st));
+    TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag ^ J.a.tr, J.a.dag, N, nb * M, 2, sa, ea, st));
     // right operand: rows of B^T (dagger: conjugated rows of the reversed spectrum)
-    TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, !J.b.dag, J.b.dag, N, nb * M, 3, sb, eb, st));
+    TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, (!J.b.dag) ^ J.b.tr, J.b.dag, N, nb * M, 3, sb, eb, st));
     SplitGemmArgs a;
     a.slicesA = sa; a.slicesB = sb; a.expA = ea; a.expB = eb; a.C = J.c;
     a.N = N; a.Kp = kpad(N); a.Q = nb * M; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
@@ -741,9 +743,12 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
     }
   LangevinWs w = carve_langevin(ws, N, T, nb, M, S);
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
-  // 1. spectra of the four links, [nb][4][M]
-  TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, 0, st));
+  // 1. spectra of the four links, [nb][4][M], and their transposes (right
+  //    operands that are not daggered are sliced by rows of those)
+  if (mode != NSPT_LMODE_UPDATE) TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(U, T1, w.specUT, E, T, nb * 4, M, 0, 0, st, N));
   auto link = [&](int mu, int dag) { return SpecRef{w.specU + mu * specE, 4LL * M, dag}; };
+  auto linkT = [&](int mu) { return SpecRef{w.specUT + mu * specE, 4LL * M, 0, 1}; };
   auto slot = [&](float4* base, int s) { return base + (long long)s * nb * specE; };
   Job jobs[kMaxJobs];
   if (mode != NSPT_LMODE_UPDATE) {
@@ -755,7 +760,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   for (int mu = 0; mu < 4; ++mu)
     for (int nu = 0; nu < 4; ++nu)
       if (mu != nu)
-        jobs[6 + ord_idx(mu, nu)] = Job{link(mu, 0), link(nu, 0), slot(w.specAcc, 6 + ord_idx(mu, nu)),
+        jobs[6 + ord_idx(mu, nu)] = Job{link(mu, 0), linkT(nu), slot(w.specAcc, 6 + ord_idx(mu, nu)),
                                         make_double2(1, 0), 0, 0};
   TRYS(run_jobs(w, jobs, 18, N, nb, M, S, st));
   // truncate (Step 5) and return to the frequency domain
@@ -774,7 +779,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
         J.alpha = z[mu][nu];
       } else {
         J.a = pq(6 + ord_idx(mu, nu), 1);
-        J.b = link(nu, 0);
+        J.b = linkT(nu);
         J.alpha = make_double2(z[mu][nu].x, -z[mu][nu].y);
       }
       J.c = slot(w.specIn, mu);
@@ -784,10 +789,10 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
     TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
   }
   TRYC(nspt_fft_inv_df(w.specIn, w.serTmp, T1, E, T, 4 * nb, M, 0, 0, st));
-  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specIn, E, T, 4 * nb, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specIn, E, T, 4 * nb, M, 0, 0, st, N));  // transposed
   // 4. S_mu = U_mu inner_mu
   for (int mu = 0; mu < 4; ++mu)
-    jobs[mu] = Job{link(mu, 0), SpecRef{slot(w.specIn, mu), (long long)M, 0}, slot(w.specAcc, mu),
+    jobs[mu] = Job{link(mu, 0), SpecRef{slot(w.specIn, mu), (long long)M, 0, 1}, slot(w.specAcc, mu),
                    make_double2(1, 0), 0, 0};
   TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
   for (int mu = 0; mu < 4; ++mu)
@@ -806,8 +811,8 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
     const int Mt = nspt_pow2_at_least(2 * (t + 1));
     TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
-    TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, 0, st));
-    Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0}, w.spC, make_double2(1, 0), 0, 0};
+    TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, 0, st, N));  // transposed: sliced by rows
+    Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0, 1}, w.spC, make_double2(1, 0), 0, 0};
     TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
     TRYC(nspt_fft_inv_df(w.spC, c, T1, E, t, nb * 4, Mt, 0, 0, st));
     return NSPT_OK;
@@ -844,7 +849,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   double2* const expY = Qs[cur];
   // 7. U <- exp_star(i X) U, order 0 untouched
   TRYC(nspt_fft_fwd_df(expY, T1, w.spR, E, T, nb * 4, M, 0, 0, st));
-  Job J{SpecRef{w.spR, (long long)M, 0}, SpecRef{w.specU, (long long)M, 0}, w.spC, make_double2(1, 0), 0, 0};
+  Job J{SpecRef{w.spR, (long long)M, 0}, SpecRef{w.specUT, (long long)M, 0, 1}, w.spC, make_double2(1, 0), 0, 0};
   TRYS(run_jobs(w, &J, 1, N, nb * 4, M, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
   TRYC(nspt_fft_inv_df(w.spC, U, T1, E, T, nb * 4, M, 0, 0, st, 1.0, 0, N, 1));
   return NSPT_OK;
