@@ -17,7 +17,11 @@ functions fix (each pinned by a test):
   absorbed by the rescaled time of Eq. 3;
 * Langevin step (Euler-Maruyama in the rescaled time):
   X^(0) = 0, X^(1) = eps F^(1) + sqrt(2 eps) eta, X^(k>=2) = eps F^(k),
-  U' = exp_star(i X) star U; order 0 of U is left unchanged.
+  U' = exp_star(i X) star U; order 0 of U is left unchanged;
+* Wilson loops: W(a, b) = 1/(12 N) sum over ordered planes of
+  z_{mu nu}^(ab) Tr[U_mu^a U_nu^b (U_mu^a)^+ (U_nu^b)^+] (the paper measures Wilson
+  loops but does not restate their definition; the z^(ab) factor makes the
+  twist-eater vacuum value exactly 1).
 """
 from __future__ import annotations
 
@@ -158,3 +162,31 @@ def md_trajectory(U, eta, z, eps: float, nsteps: int):
     for _ in range(nsteps):
         U, P = md_step(U, P, z, eps)
     return U, P
+
+
+def wilson_loops(U, z, amax: int) -> np.ndarray:
+    """Perturbative coefficients of the plane-averaged a x b Wilson loops of the TEK
+    model (the observables the NSPT runs measure, Sec. 1):
+        W(a, b)^(k) = 1/(12 N) sum_{mu != nu} z_{mu nu}^(a b) Tr[(U_mu^a U_nu^b (U_mu^a)^+ (U_nu^b)^+)^(k)],
+    powers and products being star products of the link series.  Returns shape
+    (..., amax, amax, T+1) with [a-1, b-1, k]; W(1, 1) is the plaquette of Eq. 1."""
+    U = np.asarray(U, np.complex128)
+    N = U.shape[-1]
+    T = U.shape[-3] - 1
+    powers = []
+    for mu in range(4):
+        pw = [None, U[..., mu, :, :, :]]
+        for _ in range(2, amax + 1):
+            pw.append(pm.star(pw[-1], U[..., mu, :, :, :]))
+        powers.append(pw)
+    W = np.zeros(U.shape[:-4] + (amax, amax, T + 1), np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            for a in range(1, amax + 1):
+                for b in range(1, amax + 1):
+                    A, B = powers[mu][a], powers[nu][b]
+                    X = pm.star(pm.star(pm.star(A, B), pm.dagger(A)), pm.dagger(B))
+                    W[..., a - 1, b - 1, :] += z[mu, nu] ** (a * b) * np.trace(X, axis1=-2, axis2=-1)
+    return W / (12 * N)

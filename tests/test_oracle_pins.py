@@ -570,3 +570,71 @@ def test_md_trajectory_refresh_and_vacuum():
     # momentum and drift stay Hermitian and traceless order by order
     np.testing.assert_allclose(P1, np.conj(np.swapaxes(P1, -1, -2)), atol=1e-13)
     assert np.abs(np.trace(P1, axis1=-2, axis2=-1)).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Wilson loops (the measured observable)
+# ---------------------------------------------------------------------------
+def test_wilson_loops_twist_eater_vacuum_is_one():
+    """Gamma_mu Gamma_nu = conj(z_{mu nu}) Gamma_nu Gamma_mu gives
+    Gamma_mu^a Gamma_nu^b Gamma_mu^-a Gamma_nu^-b = conj(z)^(ab): every loop is 1 at order 0
+    and vanishes at higher orders of the pure vacuum."""
+    for L, k in ((3, 1), (5, 2)):
+        N = L * L
+        U = np.zeros((4, 4, N, N), np.complex128)
+        U[:, 0] = syn.twist_eaters(L, k)
+        W = tek.wilson_loops(U, tek.twist_phases(L, k), 3)
+        np.testing.assert_allclose(W[..., 0], np.ones((3, 3)), atol=1e-12)
+        assert np.abs(W[..., 1:]).max() < 1e-13
+
+
+def test_wilson_loops_match_nonperturbative_loops():
+    """sum_k g^k W(a,b)^(k) equals the matrix Wilson loop of U(g) = sum_k g^k U^(k)
+    (real g) up to O(g^{T+1})."""
+    rg = syn.rng(71)
+    L, k, T, amax = 3, 1, 3, 2
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    z = tek.twist_phases(L, k)
+    W = tek.wilson_loops(U, z, amax)
+    errs = []
+    for gc in (5e-3, 1e-2):
+        pw = gc ** np.arange(T + 1)
+        Ug = np.einsum("k,mkij->mij", pw, U)
+        ref = np.zeros((amax, amax), np.complex128)
+        for mu in range(4):
+            for nu in range(4):
+                if mu == nu:
+                    continue
+                for a in range(1, amax + 1):
+                    for b in range(1, amax + 1):
+                        A = np.linalg.matrix_power(Ug[mu], a)
+                        B = np.linalg.matrix_power(Ug[nu], b)
+                        ref[a - 1, b - 1] += z[mu, nu] ** (a * b) * np.trace(A @ B @ A.conj().T @ B.conj().T)
+        ref /= 12 * N
+        got = np.einsum("k,abk->ab", pw, W)
+        errs.append(np.abs(got - ref).max())
+    assert errs[0] < 1e-8
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+
+
+def test_wilson_1x1_is_the_plaquette_of_the_action():
+    rg = syn.rng(72)
+    L, k, T = 3, 1, 4
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 2)
+    z = tek.twist_phases(L, k)
+    W = tek.wilson_loops(U, z, 1)
+    S = tek.action(U, z)
+    expect = -S / (12 * N)
+    expect[..., 0] += 1.0
+    np.testing.assert_allclose(W[..., 0, 0, :], expect, atol=1e-12)
+
+
+def test_wilson_loops_conjugation_symmetry():
+    """The (nu, mu) plane with extents (b, a) is the dagger of the (mu, nu) plane with (a, b),
+    and z_{nu mu} = conj(z_{mu nu}), so W(a, b) = conj(W(b, a)) order by order."""
+    rg = syn.rng(73)
+    U = syn.link_series(rg, 3, 1, 3, 1)[0]
+    W = tek.wilson_loops(U, tek.twist_phases(3, 1), 3)
+    np.testing.assert_allclose(W, np.conj(np.swapaxes(W, 0, 1)), atol=1e-12)
