@@ -309,7 +309,8 @@ def langevin_leg(torch, nspt, barrier, L=11, T=31, streams=8, flux=3, eps=0.01):
 def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     """One MD trajectory of the paper's length (40 leapfrog steps, momentum refreshed at its
     start) of one SU(225) configuration at O(g^31) in the split form, with the time split
-    into the force phase (drift plus momentum kicks) and the link-update phase."""
+    into the force phase (drift plus momentum kicks) and the link-update phase, and the
+    measurement of its Wilson loops up to 2 x 2."""
     g = syn.rng(syn.SEED_BASE + 5)
     N = L * L
     tU = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, flux, T, 1))).cuda()
@@ -320,7 +321,9 @@ def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     ms = time_steps(torch, lambda: nspt.tek_md_trajectory(tU, tP, flux, eps, nsteps, eta=tE, algo="fft",
                                                           prec="split"), 1, 0, barrier)
     ph = nspt.profile_end()
+    msw = time_steps(torch, lambda: nspt.tek_wilson_loops(tU, flux, 2, algo="fft", prec="split"), 2, 1, barrier) / 2
     out = {"ms_per_trajectory": ms, "md_steps": nsteps, "ms_per_md_step": ms / nsteps,
+           "wilson_loops_amax2_ms": msw,
            "force_ms": ph.get("md_force", (0.0, 0))[0], "link_update_ms": ph.get("md_link", (0.0, 0))[0],
            "kernel_stages_ms": {k: v[0] for k, v in ph.items() if k not in ("md_force", "md_link")},
            "note": "one configuration (4 links), split form; 10 trajectories = 10 x ms_per_trajectory"}

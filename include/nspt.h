@@ -187,6 +187,22 @@ NSPT_API int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, i
                                     double eps, int nsteps, const nspt_opts* opts, void* stream);
 
 /*
+ * Perturbative Wilson loops of the TEK links, the observable the NSPT runs of
+ * the paper measure (Sec. 1; the loops are the standard TEK ones, the twist
+ * factor z^(ab) making the twist-eater vacuum value 1):
+ *   W(a, b)^(k) = 1/(12 N) sum_{mu != nu} z_{mu nu}^(ab) Tr[(U_mu^a U_nu^b (U_mu^a)^+ (U_nu^b)^+)^(k)]
+ * for 1 <= a, b <= amax <= 8, with star products in the form of opts (FP64 or
+ * split, naive or FFT).  W(b, a) = conj(W(a, b)); the real part of W(a, a) and
+ * of (W(a, b) + W(b, a)) / 2 is the loop average.
+ *   U : [batch][4][T+1][N][N] link series (input; N = L^2, gcd(flux, L) = 1)
+ *   W : [batch][amax][amax][T+1] complex128 (output, [b][a-1][b'-1][k])
+ * Workspace: nspt_workspace_size_wilson().
+ */
+NSPT_API size_t nspt_workspace_size_wilson(int N, int T, int batch, int amax, const nspt_opts* opts);
+NSPT_API int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int amax, void* W,
+                                   const nspt_opts* opts, void* stream);
+
+/*
  * Single stages of FFT-CONV, for stage timing and per-stage tests.
  * nspt_order_fft: Steps 1-2 -- At[b][p] = sum_{k<=T} A[b][k] w^(kp), p = 0..M-1,
  *   A : [batch][T+1][N][N] -> At : [batch][M][N][N], w = exp(+2 pi i/M).

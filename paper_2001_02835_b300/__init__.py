@@ -22,7 +22,7 @@ import torch
 
 __all__ = [
     "lib", "library_path", "Opts", "NsptError",
-    "polymat_mul", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "order_fft", "order_ifft",
+    "polymat_mul", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops", "order_fft", "order_ifft",
     "workspace_size", "star", "PolymatMul",
     "ALGO_NAIVE", "ALGO_FFT", "ALGO_AUTO", "PREC_FP64", "PREC_SPLIT", "RESCALE_AUTO",
 ]
@@ -64,6 +64,8 @@ _SIGS = {
     "nspt_opts_default": (None, [ctypes.POINTER(Opts)]),
     "nspt_init": (_i, []),
     "nspt_workspace_size": (_sz, [_i, _i, _i, _i, ctypes.POINTER(Opts)]),
+    "nspt_workspace_size_wilson": (_sz, [_i, _i, _i, _i, ctypes.POINTER(Opts)]),
+    "nspt_tek_wilson_loops": (_i, [_vp, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_langevin_step": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, ctypes.POINTER(Opts), _vp]),
@@ -251,6 +253,28 @@ def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, n
                                       _stream_ptr(U.device))
     _check(rc, "nspt_tek_md_trajectory")
     return U, P
+
+
+def tek_wilson_loops(U: torch.Tensor, flux: int, amax: int, **kw) -> torch.Tensor:
+    """Perturbative Wilson loops W (batch, amax, amax, T+1) complex128 of the links U
+    (batch, 4, T+1, N, N), W[b, a-1, c-1, k] = W(a, c)^(k) (see include/nspt.h)."""
+    _check_tensor(U, "U")
+    if U.dim() != 5 or U.shape[1] != 4:
+        raise ValueError("U must be (batch, 4, T+1, N, N)")
+    batch, T, N = U.shape[0], U.shape[2] - 1, U.shape[3]
+    W = torch.empty((batch, amax, amax, T + 1), dtype=torch.complex128, device=U.device)
+    opts = make_opts(**kw)
+    nbytes = lib().nspt_workspace_size_wilson(N, T, batch, int(amax), ctypes.byref(opts))
+    if nbytes == 0:
+        raise ValueError("unsupported Wilson-loop sizes")
+    ws = _workspace(nbytes, U.device)  # noqa: F841
+    if ws is not None:
+        opts.workspace = ws.data_ptr()
+        opts.workspace_bytes = ws.numel()
+    rc = lib().nspt_tek_wilson_loops(U.data_ptr(), N, T, batch, int(flux), int(amax), W.data_ptr(),
+                                     ctypes.byref(opts), _stream_ptr(U.device))
+    _check(rc, "nspt_tek_wilson_loops")
+    return W
 
 
 def order_fft(A: torch.Tensor, M: int) -> torch.Tensor:

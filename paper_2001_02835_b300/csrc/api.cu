@@ -468,6 +468,67 @@ int md_run(const Plan& p, double2* U, double2* P, const double2* eta, int flux, 
   return NSPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Wilson loops of the TEK links (the NSPT measurement): powers of the links,
+// two products per plane and extent pair, and the trace of the last product
+// as a correlation of the two factors.
+// ---------------------------------------------------------------------------
+constexpr int kWilsonMaxExtent = 8;
+
+size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t ws_wilson(const Plan& p, int amax) {
+  const size_t ser = (size_t)p.batch * (p.T + 1) * p.E * sizeof(double2);
+  const size_t tr = (size_t)6 * amax * amax * p.batch * (p.T + 1) * NSPT_TRACE_CHUNKS * sizeof(double2);
+  return al256((size_t)4 * amax * ser) + al256(2 * ser) + al256(tr) + al256(ws_mul(p));
+}
+
+int mul_plan(const Plan& p, const double2* A, const double2* B, double2* C, void* ws, cudaStream_t st) {
+  if (p.prec == NSPT_PREC_FP64) return mul_fp64(p, A, B, C, ws, st);
+  return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, A, B, C, ws, st);
+}
+
+int wilson_run(const Plan& p, const double2* U, int flux, int amax, double2* W, void* ws, cudaStream_t st) {
+  const int N = p.N, T = p.T, batch = p.batch;
+  const long long E = p.E, T1 = T + 1, ser = (long long)batch * T1 * E;
+  const int L = (int)llround(sqrt((double)N));
+  char* base = (char*)ws;
+  double2* Pw = (double2*)base;                                  // [4][amax][batch][T+1][E]
+  base += al256((size_t)4 * amax * ser * sizeof(double2));
+  double2* L1 = (double2*)base;
+  double2* L2 = L1 + ser;
+  base += al256((size_t)2 * ser * sizeof(double2));
+  double2* tr = (double2*)base;                                  // [6][amax][amax][batch][T+1][chunks]
+  base += al256((size_t)6 * amax * amax * batch * T1 * NSPT_TRACE_CHUNKS * sizeof(double2));
+  void* mws = base;
+  auto pw = [&](int mu, int a) { return Pw + ((long long)mu * amax + (a - 1)) * ser; };
+  int rc;
+  for (int mu = 0; mu < 4; ++mu) {
+    // U_mu of every batch element into one contiguous batch
+    TRY(cudaMemcpy2DAsync(pw(mu, 1), (size_t)T1 * E * sizeof(double2), U + (long long)mu * T1 * E,
+                          (size_t)4 * T1 * E * sizeof(double2), (size_t)T1 * E * sizeof(double2), batch,
+                          cudaMemcpyDeviceToDevice, st));
+    for (int a = 2; a <= amax; ++a)
+      if ((rc = mul_plan(p, pw(mu, a - 1), pw(mu, 1), pw(mu, a), mws, st))) return rc;
+  }
+  int pl = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    for (int nu = mu + 1; nu < 4; ++nu, ++pl)
+      for (int a = 1; a <= amax; ++a)
+        for (int c = 1; c <= amax; ++c) {
+          // z_{mu nu}^(ac) Tr[(U_mu^a U_nu^c) * (U_nu^c U_mu^a)^+]
+          if ((rc = mul_plan(p, pw(mu, a), pw(nu, c), L1, mws, st))) return rc;
+          if ((rc = mul_plan(p, pw(nu, c), pw(mu, a), L2, mws, st))) return rc;
+          const double ang = 2.0 * M_PI * flux * a * c / L;
+          TRY(nspt_trace_corr(L1, L2,
+                              tr + (((long long)pl * amax + (a - 1)) * amax + (c - 1)) * batch * T1 * NSPT_TRACE_CHUNKS,
+                              make_double2(cos(ang), sin(ang)), T, E, batch, st));
+        }
+  // the (nu, mu) planes are the conjugates of the (mu, nu) planes with the extents swapped
+  TRY(nspt_wilson_combine(tr, W, 6, amax, batch, T, 1.0 / (12.0 * N), st));
+  return NSPT_OK;
+}
+
 std::mutex g_init_mu;
 int g_init_dev[64] = {0};
 
@@ -673,6 +734,31 @@ int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, int N, int
   if ((rc = nspt_init())) return rc;
   return md_run(p, (double2*)U, (double2*)P, (const double2*)eta_refresh, flux, eps, nsteps, opts->workspace,
                 (cudaStream_t)stream);
+}
+
+size_t nspt_workspace_size_wilson(int N, int T, int batch, int amax, const nspt_opts* opts) {
+  Plan p;
+  if (make_plan(N, T, batch, opts, &p) || amax < 1 || amax > kWilsonMaxExtent) return 0;
+  return ws_wilson(p, amax);
+}
+
+int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int amax, void* W, const nspt_opts* opts,
+                          void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!U || !W || amax < 1 || amax > kWilsonMaxExtent) return NSPT_ERR_ARG;
+  const int L = (int)llround(sqrt((double)N));
+  if (L * L != N || flux <= 0) return NSPT_ERR_ARG;
+  int a = flux % L, bb = L;
+  while (a) { int t = bb % a; bb = a; a = t; }
+  if (bb != 1) return NSPT_ERR_ARG;
+  const size_t ubytes = (size_t)batch * 4 * (T + 1) * p.E * sizeof(double2);
+  const size_t wbytes = (size_t)batch * amax * amax * (T + 1) * sizeof(double2);
+  if (overlaps(U, ubytes, W, wbytes)) return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_wilson(p, amax)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  return wilson_run(p, (const double2*)U, flux, amax, (double2*)W, opts->workspace, (cudaStream_t)stream);
 }
 
 int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {

@@ -188,3 +188,82 @@ cudaError_t nspt_md_y(double2* Y, const double2* P, double eps, int T, long long
   md_y_kernel<<<blocks_for(nseries * (T + 1) * E), 256, 0, st>>>(Y, P, eps, T, E, nseries);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Wilson loops: trace of the last star product without forming it,
+// Tr[(L1 * L2^+)^(k)] = sum_{l <= k} sum_ij L1^(l)_ij conj(L2^(k-l)_ij).
+// ---------------------------------------------------------------------------
+namespace {
+
+// grid (T+1, NSPT_TRACE_CHUNKS, batch), 256 threads: the partial sums
+// t[b][k][ch] = zc * sum_{l<=k} sum_{e in chunk ch} L1^(l)_e conj(L2^(k-l)_e)
+__global__ void __launch_bounds__(256) trace_corr_kernel(const double2* __restrict__ L1,
+                                                         const double2* __restrict__ L2, double2* __restrict__ t,
+                                                         double2 zc, int T, long long E) {
+  const int k = blockIdx.x, ch = blockIdx.y, b = blockIdx.z;
+  const long long csz = (E + NSPT_TRACE_CHUNKS - 1) / NSPT_TRACE_CHUNKS;
+  const long long e0 = ch * csz, e1 = min(E, e0 + csz);
+  const long long base = (long long)b * (T + 1) * E;
+  double sr = 0.0, si = 0.0;
+  for (int l = 0; l <= k; ++l) {
+    const double2* x = L1 + base + (long long)l * E;
+    const double2* y = L2 + base + (long long)(k - l) * E;
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const double2 u = x[e], v = y[e];
+      sr = fma(u.x, v.x, fma(u.y, v.y, sr));   // Re(u conj(v))
+      si = fma(u.y, v.x, fma(-u.x, v.y, si));  // Im(u conj(v))
+    }
+  }
+  __shared__ double red[2][8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = sr; red[1][threadIdx.x >> 5] = si; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ar = 0.0, ai = 0.0;
+    for (int w = 0; w < 8; ++w) { ar += red[0][w]; ai += red[1][w]; }
+    t[((long long)b * (T + 1) + k) * NSPT_TRACE_CHUNKS + ch] =
+        make_double2(zc.x * ar - zc.y * ai, zc.x * ai + zc.y * ar);
+  }
+}
+
+// W[b][a][c][k] = scale * sum_p sum_ch (tr[p][a][c][b][k][ch] + conj(tr[p][c][a][b][k][ch]))
+__global__ void wilson_combine_kernel(const double2* __restrict__ tr, double2* __restrict__ W, int nplanes, int amax,
+                                      int batch, int T1, double scale) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)batch * amax * amax * T1;
+  if (i >= n) return;
+  const int k = (int)(i % T1);
+  const int c = (int)((i / T1) % amax), a = (int)((i / ((long long)T1 * amax)) % amax);
+  const int b = (int)(i / ((long long)T1 * amax * amax));
+  double re = 0.0, im = 0.0;
+  for (int p = 0; p < nplanes; ++p) {
+    const double2* x = tr + (((((long long)p * amax + a) * amax + c) * batch + b) * T1 + k) * NSPT_TRACE_CHUNKS;
+    const double2* y = tr + (((((long long)p * amax + c) * amax + a) * batch + b) * T1 + k) * NSPT_TRACE_CHUNKS;
+    for (int ch = 0; ch < NSPT_TRACE_CHUNKS; ++ch) {
+      re += x[ch].x + y[ch].x;
+      im += x[ch].y - y[ch].y;
+    }
+  }
+  W[i] = make_double2(scale * re, scale * im);
+}
+
+}  // namespace
+
+cudaError_t nspt_trace_corr(const double2* L1, const double2* L2, double2* t, double2 zc, int T, long long E,
+                            int batch, cudaStream_t st) {
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  trace_corr_kernel<<<dim3(T + 1, NSPT_TRACE_CHUNKS, batch), 256, 0, st>>>(L1, L2, t, zc, T, E);
+  return cudaGetLastError();
+}
+
+cudaError_t nspt_wilson_combine(const double2* tr, double2* W, int nplanes, int amax, int batch, int T, double scale,
+                                cudaStream_t st) {
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  const long long n = (long long)batch * amax * amax * (T + 1);
+  wilson_combine_kernel<<<blocks_for(n), 256, 0, st>>>(tr, W, nplanes, amax, batch, T + 1, scale);
+  return cudaGetLastError();
+}

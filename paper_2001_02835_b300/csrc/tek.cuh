@@ -41,3 +41,13 @@ struct PsTerms {
 // Q^(k) = c_0 delta_{k0} 1 + sum_{i=1}^{m} c_i (Y^i)^(k) + prod^(k - shift) (k >= shift), k = 0..tq
 cudaError_t nspt_ps_combine(double2* Q, const PsTerms& t, int m, const double2* prod, int shift, int tq, int T, int N,
                             long long nseries, cudaStream_t st);
+
+// Wilson loops: t[b][k][ch] = zc sum_{l<=k} <L1^(l), L2^(k-l)>_ch, the sum over chunk ch
+// of the entries (summed over ch: zc Tr[(L1 * L2^+)^(k)]) for series L1, L2 [batch][T+1][E];
+// and W[b][a][c][k] = scale sum_p sum_ch (tr[p][a][c][b][k][ch] + conj(tr[p][c][a][b][k][ch]))
+// from tr [nplanes][amax][amax][batch][T+1][NSPT_TRACE_CHUNKS]
+constexpr int NSPT_TRACE_CHUNKS = 64;
+cudaError_t nspt_trace_corr(const double2* L1, const double2* L2, double2* t, double2 zc, int T, long long E,
+                            int batch, cudaStream_t st);
+cudaError_t nspt_wilson_combine(const double2* tr, double2* W, int nplanes, int amax, int batch, int T, double scale,
+                                cudaStream_t st);

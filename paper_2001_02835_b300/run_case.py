@@ -25,7 +25,7 @@ import paper_2001_02835_b300 as nspt  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["mul", "backward", "langevin", "md"], default="mul")
+    ap.add_argument("--op", choices=["mul", "backward", "langevin", "md", "wilson"], default="mul")
     ap.add_argument("--algo", default="fft")
     ap.add_argument("--prec", default="split")
     ap.add_argument("--N", type=int, default=225)
@@ -35,6 +35,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--md-steps", type=int, default=40, help="leapfrog steps per call of --op md")
+    ap.add_argument("--amax", type=int, default=2, help="largest loop extent of --op wilson")
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if nspt.lib().nspt_init() != 0:
@@ -46,6 +47,10 @@ def main(argv=None):
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
         eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
         fn = lambda: nspt.tek_langevin_step(U, eta, 1, 0.01, **kw)  # noqa: E731
+    elif a.op == "wilson":
+        L = int(round(a.N ** 0.5))
+        U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
+        fn = lambda: nspt.tek_wilson_loops(U, 1, a.amax, **kw)  # noqa: E731
     elif a.op == "md":
         L = int(round(a.N ** 0.5))
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
