@@ -187,6 +187,29 @@ NSPT_API int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, i
                                     double eps, int nsteps, const nspt_opts* opts, void* stream);
 
 /*
+ * C = A star B (as nspt_polymat_mul, same opts) for series in HOST memory --
+ * pinned (page-locked) for the copies to overlap; no counterpart in the paper.
+ * The batch goes through the GPU one element at a time in two device slots:
+ * the host-to-device copies of element i+1 and the device-to-host copy of
+ * element i-1 run on two library-owned streams while element i is multiplied
+ * on `stream`.  Work queued on `stream` after the call starts after the last
+ * element of C has reached host memory (synchronise `stream` before reading
+ * C; A and B must stay unchanged until then).  A call starts after the work
+ * already queued on `stream`, except when it continues the previous call of
+ * this device (same workspace, stream and element size): its copies in then
+ * wait only for the device slot they reuse, so they overlap the end of that
+ * call -- between such calls the workspace must not be used by other work.
+ * Enqueues are serialised per device.
+ *   A, B : host [batch][T+1][N][N] complex128;  C : host, same shape, no overlap
+ * Workspace: nspt_workspace_size_host() bytes of DEVICE memory (two slots of
+ * three series plus the product workspace of one element).
+ * NSPT_RESCALE_AUTO is refused (NSPT_ERR_UNSUPPORTED): it synchronises per element.
+ */
+NSPT_API size_t nspt_workspace_size_host(int N, int T, int batch, const nspt_opts* opts);
+NSPT_API int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, int batch,
+                                   const nspt_opts* opts, void* stream);
+
+/*
  * Perturbative Wilson loops of the TEK links, the observable the NSPT runs of
  * the paper measure (Sec. 1; the loops are the standard TEK ones, the twist
  * factor z^(ab) making the twist-eater vacuum value 1):

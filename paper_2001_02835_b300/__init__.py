@@ -22,7 +22,7 @@ import torch
 
 __all__ = [
     "lib", "library_path", "Opts", "NsptError",
-    "polymat_mul", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops", "order_fft", "order_ifft",
+    "polymat_mul", "polymat_mul_host", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops", "order_fft", "order_ifft",
     "workspace_size", "star", "PolymatMul",
     "ALGO_NAIVE", "ALGO_FFT", "ALGO_AUTO", "PREC_FP64", "PREC_SPLIT", "RESCALE_AUTO",
 ]
@@ -65,6 +65,8 @@ _SIGS = {
     "nspt_init": (_i, []),
     "nspt_workspace_size": (_sz, [_i, _i, _i, _i, ctypes.POINTER(Opts)]),
     "nspt_workspace_size_wilson": (_sz, [_i, _i, _i, _i, ctypes.POINTER(Opts)]),
+    "nspt_workspace_size_host": (_sz, [_i, _i, _i, ctypes.POINTER(Opts)]),
+    "nspt_polymat_mul_host": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_wilson_loops": (_i, [_vp, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
@@ -134,10 +136,10 @@ def make_opts(algo="auto", prec="fp64", fft_len=0, slices=0, rescale_log2r=0) ->
 _ws_cache: dict = {}
 
 
-def _workspace(nbytes: int, device: torch.device) -> Optional[torch.Tensor]:
+def _workspace(nbytes: int, device: torch.device, tag: str = "") -> Optional[torch.Tensor]:
     if nbytes == 0:
         return None
-    key = (device.index, torch.cuda.current_stream(device).cuda_stream)
+    key = (device.index, torch.cuda.current_stream(device).cuda_stream, tag)
     buf = _ws_cache.get(key)
     if buf is None or buf.numel() < nbytes:
         buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
@@ -194,6 +196,33 @@ def polymat_mul(A: torch.Tensor, B: torch.Tensor, C: Optional[torch.Tensor] = No
     rc = lib().nspt_polymat_mul(A.data_ptr(), B.data_ptr(), C.data_ptr(), N, T, batch, ctypes.byref(opts),
                                 _stream_ptr(A.device))
     _check(rc, "nspt_polymat_mul")
+    return C
+
+
+def polymat_mul_host(A: torch.Tensor, B: torch.Tensor, C: Optional[torch.Tensor] = None, device=None,
+                     **kw) -> torch.Tensor:
+    """C = A star B for CPU tensors (pinned for the copies to overlap the products) through
+    nspt_polymat_mul_host on `device` (default: the current CUDA device); queued on that
+    device's current stream -- synchronise it before reading C."""
+    for t, name in ((A, "A"), (B, "B")):
+        if t.device.type != "cpu" or t.dtype != torch.complex128 or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous complex128 CPU tensor" % name)
+    if A.shape != B.shape:
+        raise ValueError("A and B must have the same shape")
+    batch, T, N = _series_dims(A)
+    if C is None:
+        C = torch.empty_like(A).pin_memory()
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    opts = make_opts(**kw)
+    nbytes = lib().nspt_workspace_size_host(N, T, batch, ctypes.byref(opts))
+    # a workspace of its own: consecutive calls chain through its device slots
+    ws = _workspace(nbytes, dev, "host")  # noqa: F841
+    if ws is not None:
+        opts.workspace = ws.data_ptr()
+        opts.workspace_bytes = ws.numel()
+    rc = lib().nspt_polymat_mul_host(A.data_ptr(), B.data_ptr(), C.data_ptr(), N, T, batch, ctypes.byref(opts),
+                                     _stream_ptr(dev))
+    _check(rc, "nspt_polymat_mul_host")
     return C
 
 

@@ -532,6 +532,99 @@ int wilson_run(const Plan& p, const double2* U, int flux, int amax, double2* W, 
 std::mutex g_init_mu;
 int g_init_dev[64] = {0};
 
+// ---------------------------------------------------------------------------
+// Products of host-resident series: one batch element at a time through two
+// device slots, with the host-to-device copies of element i+1, the product of
+// element i (caller's stream) and the device-to-host copy of element i-1 on
+// three streams.  Streams and events are created once per device.
+// ---------------------------------------------------------------------------
+constexpr int kHostSlots = 2;  // device slots (a third measured no faster: the copies are PCIe-bound)
+
+struct HostPipe {
+  bool ready = false;
+  cudaStream_t in = nullptr, out = nullptr;
+  cudaEvent_t start = nullptr, ev_in[kHostSlots] = {}, ev_comp[kHostSlots] = {}, ev_out[kHostSlots] = {};
+  // chaining state: the slots of the previous call (same workspace, stream and element size)
+  const void* ws = nullptr;
+  cudaStream_t st = nullptr;
+  size_t bytes = 0;
+  bool used[kHostSlots] = {};
+  int next = 0;
+  std::mutex mu;  // one enqueue at a time per device
+};
+HostPipe g_pipe[64];
+std::mutex g_pipe_mu;
+
+int host_pipe(HostPipe** hp) {
+  int dev = 0;
+  TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return NSPT_ERR_DEVICE;
+  std::lock_guard<std::mutex> lk(g_pipe_mu);
+  HostPipe& h = g_pipe[dev];
+  if (!h.ready) {
+    TRY(cudaStreamCreateWithFlags(&h.in, cudaStreamNonBlocking));
+    TRY(cudaStreamCreateWithFlags(&h.out, cudaStreamNonBlocking));
+    TRY(cudaEventCreateWithFlags(&h.start, cudaEventDisableTiming));
+    for (int s = 0; s < kHostSlots; ++s) {
+      TRY(cudaEventCreateWithFlags(&h.ev_in[s], cudaEventDisableTiming));
+      TRY(cudaEventCreateWithFlags(&h.ev_comp[s], cudaEventDisableTiming));
+      TRY(cudaEventCreateWithFlags(&h.ev_out[s], cudaEventDisableTiming));
+    }
+    h.ready = true;
+  }
+  *hp = &h;
+  return NSPT_OK;
+}
+
+size_t ws_host(const Plan& pc) {
+  const size_t ser = (size_t)(pc.T + 1) * pc.E * sizeof(double2);
+  return 3 * kHostSlots * al256(ser) + al256(ws_mul(pc));
+}
+
+int host_run(const Plan& pc, int batch, const double2* A, const double2* B, double2* C, void* ws, HostPipe& hp,
+             cudaStream_t st) {
+  const size_t bytes = (size_t)(pc.T + 1) * pc.E * sizeof(double2);
+  const long long ser = (long long)(pc.T + 1) * pc.E;
+  char* base = (char*)ws;
+  double2* d[kHostSlots][3];
+  for (int s = 0; s < kHostSlots; ++s)
+    for (int j = 0; j < 3; ++j) d[s][j] = (double2*)(base + (3 * s + j) * al256(bytes));
+  void* mws = base + 3 * kHostSlots * al256(bytes);
+  std::lock_guard<std::mutex> lk(hp.mu);
+  if (!(hp.ws == ws && hp.st == st && hp.bytes == bytes)) {
+    // not a continuation of the previous call: everything already queued on the caller's
+    // stream (earlier users of this workspace) comes first
+    TRY(cudaEventRecord(hp.start, st));
+    TRY(cudaStreamWaitEvent(hp.in, hp.start, 0));
+    TRY(cudaStreamWaitEvent(hp.out, hp.start, 0));
+    for (int k = 0; k < kHostSlots; ++k) hp.used[k] = false;
+    hp.next = 0;
+  }
+  hp.ws = ws;
+  hp.st = st;
+  hp.bytes = bytes;
+  int rc, s = 0;
+  for (int i = 0; i < batch; ++i) {
+    s = hp.next;
+    hp.next = (hp.next + 1) % kHostSlots;
+    if (hp.used[s]) TRY(cudaStreamWaitEvent(hp.in, hp.ev_comp[s], 0));  // slot's A, B consumed
+    TRY(cudaMemcpyAsync(d[s][0], A + i * ser, bytes, cudaMemcpyHostToDevice, hp.in));
+    TRY(cudaMemcpyAsync(d[s][1], B + i * ser, bytes, cudaMemcpyHostToDevice, hp.in));
+    TRY(cudaEventRecord(hp.ev_in[s], hp.in));
+    TRY(cudaStreamWaitEvent(st, hp.ev_in[s], 0));
+    if (hp.used[s]) TRY(cudaStreamWaitEvent(st, hp.ev_out[s], 0));      // slot's C copied out
+    hp.used[s] = true;
+    if ((rc = mul_plan(pc, d[s][0], d[s][1], d[s][2], mws, st))) { hp.ws = nullptr; return rc; }
+    TRY(cudaEventRecord(hp.ev_comp[s], st));
+    TRY(cudaStreamWaitEvent(hp.out, hp.ev_comp[s], 0));
+    TRY(cudaMemcpyAsync(C + i * ser, d[s][2], bytes, cudaMemcpyDeviceToHost, hp.out));
+    TRY(cudaEventRecord(hp.ev_out[s], hp.out));
+  }
+  // the caller's stream continues after the last copy out (the copies out are in order)
+  TRY(cudaStreamWaitEvent(st, hp.ev_out[s], 0));
+  return NSPT_OK;
+}
+
 }  // namespace
 
 void nspt_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
@@ -759,6 +852,30 @@ int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int 
   if ((rc = check_ws(opts, ws_wilson(p, amax)))) return rc;
   if ((rc = nspt_init())) return rc;
   return wilson_run(p, (const double2*)U, flux, amax, (double2*)W, opts->workspace, (cudaStream_t)stream);
+}
+
+size_t nspt_workspace_size_host(int N, int T, int batch, const nspt_opts* opts) {
+  Plan pc;
+  if (batch < 1 || make_plan(N, T, 1, opts, &pc)) return 0;
+  return ws_host(pc);
+}
+
+int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, int batch, const nspt_opts* opts,
+                          void* stream) {
+  Plan p, pc;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if ((rc = make_plan(N, T, 1, opts, &pc))) return rc;
+  if (!A || !B || !C) return NSPT_ERR_ARG;
+  if (pc.rescale_auto) return NSPT_ERR_UNSUPPORTED;  // it synchronises the stream per element
+  const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
+  if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return NSPT_ERR_ALIAS;
+  if ((rc = check_ws(opts, ws_host(pc)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  HostPipe* hp = nullptr;
+  if ((rc = host_pipe(&hp))) return rc;
+  return host_run(pc, batch, (const double2*)A, (const double2*)B, (double2*)C, opts->workspace, *hp,
+                  (cudaStream_t)stream);
 }
 
 int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {

@@ -1,0 +1,47 @@
+"""Products of host-resident series (nspt_polymat_mul_host): the pipelined copies and
+products give the same C as the device-buffer product, for odd and even batches and
+on calls in a row that reuse the device slots."""
+import numpy as np
+import pytest
+import torch
+
+import nspt_synth as syn
+
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nspt():
+    import paper_2001_02835_b300 as n
+    assert n.lib().nspt_init() == 0
+    return n
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+@pytest.mark.parametrize("N,T,batch", [(9, 8, 1), (33, 15, 3), (40, 7, 5), (225, 15, 4)])
+def test_host_product_equals_device_product(nspt, prec, N, T, batch):
+    g = syn.rng(7400 + N + batch)
+    outs = []
+    for rep in range(2):   # two calls in a row through the same device slots
+        A = syn.series_batch(g, N, T, batch)
+        B = syn.series_batch(g, N, T, batch)
+        hA = torch.from_numpy(A).pin_memory()
+        hB = torch.from_numpy(B).pin_memory()
+        hC = torch.full_like(hA, float("nan")).pin_memory()
+        nspt.polymat_mul_host(hA, hB, hC, algo="fft", prec=prec)
+        ref = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec=prec))
+        outs.append((hC, ref))
+    torch.cuda.synchronize()
+    for hC, ref in outs:
+        if prec == "fp64":
+            np.testing.assert_array_equal(hC.numpy(), ref)
+        else:  # the tile width may differ between the batched and the per-element launch
+            assert np.abs(hC.numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_host_product_refuses_auto_rescale(nspt):
+    A = torch.zeros((1, 4, 3, 3), dtype=torch.complex128).pin_memory()
+    with pytest.raises(RuntimeError):
+        nspt.polymat_mul_host(A, A.clone(), prec="split", rescale_log2r=nspt.RESCALE_AUTO)
