@@ -65,3 +65,32 @@ def test_workspace_sizes(L):
     assert n.workspace_size(0, 225, 31, 4, fft) >= 3 * spec
     assert n.workspace_size(1, 225, 31, 4, fft) >= 4 * spec
     assert n.workspace_size(0, 225, 31, 4, n.make_opts(algo="fft", fft_len=128)) >= 6 * spec
+
+
+def test_argument_checks_of_md_wilson_and_host_product(L):
+    import paper_2001_02835_b300 as n
+    o = n.make_opts()
+    # MD: NULL links, N not a square, gcd(flux, L) != 1, eps <= 0, negative steps, momentum aliasing links
+    assert L.nspt_tek_md_trajectory(None, 1 << 30, None, 9, 2, 1, 1, 0.02, 4, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_md_trajectory(1 << 20, 1 << 30, None, 10, 2, 1, 1, 0.02, 4, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_md_trajectory(1 << 20, 1 << 30, None, 9, 2, 1, 3, 0.02, 4, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_md_trajectory(1 << 20, 1 << 30, None, 9, 2, 1, 1, 0.0, 4, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_md_trajectory(1 << 20, 1 << 30, None, 9, 2, 1, 1, 0.02, -1, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_md_trajectory(1 << 20, (1 << 20) + 16, None, 9, 2, 1, 1, 0.02, 4, ctypes.byref(o), None) == -2
+    # Wilson loops: extent out of range, N not a square, gcd(flux, L) != 1, output overlapping the links
+    assert L.nspt_tek_wilson_loops(1 << 20, 9, 2, 1, 1, 0, 1 << 30, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_wilson_loops(1 << 20, 9, 2, 1, 1, 9, 1 << 30, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_wilson_loops(1 << 20, 10, 2, 1, 1, 2, 1 << 30, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_wilson_loops(1 << 20, 9, 2, 1, 3, 2, 1 << 30, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_wilson_loops(1 << 20, 9, 2, 1, 1, 2, (1 << 20) + 16, ctypes.byref(o), None) == -2
+    assert L.nspt_workspace_size_wilson(9, 2, 1, 0, ctypes.byref(o)) == 0
+    assert L.nspt_workspace_size_wilson(9, 2, 1, 2, ctypes.byref(o)) > 0
+    # host product: NULL buffers, C overlapping A, missing workspace, automatic rescale refused
+    assert L.nspt_polymat_mul_host(None, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(o), None) == -1
+    assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, (1 << 20) + 16, 4, 3, 2, ctypes.byref(o), None) == -2
+    assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(o), None) == -4
+    auto = n.make_opts(algo="fft", prec="split", rescale_log2r=n.RESCALE_AUTO)
+    assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(auto), None) == -3
+    # two slots of three series of one element, plus the product workspace of one element
+    ser = 4 * 4 * 16
+    assert L.nspt_workspace_size_host(4, 3, 2, ctypes.byref(o)) >= 6 * ser
