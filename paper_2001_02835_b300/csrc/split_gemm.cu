@@ -43,14 +43,24 @@ namespace {
 
 using namespace sg;
 
+// With S <= 6 slices the A ring holds every slice of a K block (6 stages, still
+// within shared memory next to the B tiles), so that the first K block of a
+// tile can issue its pairs digit group by digit group while the epilogue of
+// the previous tile frees the groups' accumulators one at a time.
+template <int S>
+__host__ __device__ constexpr bool group_overlap() { return S <= 6; }
+template <int S>
+__host__ __device__ constexpr int a_stages() { return group_overlap<S>() ? 6 : NA_STAGES; }
+
 template <int S, int BN>
 struct Smem {
   static constexpr uint32_t B_TILE = BN * KB * 2;  // per part
-  uint8_t a[NA_STAGES][2][A_TILE];  // [stage][re/im]
+  static constexpr int NA = a_stages<S>();
+  uint8_t a[NA][2][A_TILE];         // [stage][re/im]
   uint8_t b[2][S][3][B_TILE];       // [buffer][slice][re, im, -re]
-  uint64_t full_a[NA_STAGES], empty_a[NA_STAGES];
+  uint64_t full_a[NA], empty_a[NA];
   uint64_t full_b[2], empty_b[2];
-  uint64_t acc_full, acc_empty, drain;
+  uint64_t acc_full, acc_empty[NGROUPS], drain;  // acc_empty[g]: group g's accumulator read
   uint32_t tmem_base;
   volatile int abort_flag;
 };
@@ -62,16 +72,19 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
   static_assert(NGROUPS * NACC <= (int)TMEM_COLS, "accumulators exceed TMEM");
   static_assert(BN % 16 == 0 && (BN / 8) * 8 == BN, "tile width");
   constexpr uint32_t B_TILE = Smem<S, BN>::B_TILE;
+  constexpr int NA = Smem<S, BN>::NA;
+  constexpr bool OVL = group_overlap<S>();
+  constexpr int G = S < NGROUPS ? S : NGROUPS;  // digit groups with pairs
   extern __shared__ uint8_t smem_raw[];
   Smem<S, BN>& sm = *reinterpret_cast<Smem<S, BN>*>((((uintptr_t)smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long ntiles = gb.total_tiles;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NA_STAGES; ++s) { tc::mbar_init(&sm.full_a[s], 1); tc::mbar_init(&sm.empty_a[s], 1); }
+    for (int s = 0; s < NA; ++s) { tc::mbar_init(&sm.full_a[s], 1); tc::mbar_init(&sm.empty_a[s], 1); }
     for (int s = 0; s < 2; ++s) { tc::mbar_init(&sm.full_b[s], 1); tc::mbar_init(&sm.empty_b[s], 1); }
     tc::mbar_init(&sm.acc_full, 1);
-    tc::mbar_init(&sm.acc_empty, 256);
+    for (int g = 0; g < NGROUPS; ++g) tc::mbar_init(&sm.acc_empty[g], 256);
     tc::mbar_init(&sm.drain, 1);
     sm.abort_flag = 0;
     tc::fence_mbar_init();
@@ -97,8 +110,8 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     const bool isA = (lane == 0);
     int ia = 0, ib = 0;
     uint32_t pa = 0, pb = 0;
-    uint32_t last_a_parity[NA_STAGES] = {}, last_b_parity[2] = {0, 0};
-    bool issued_a[NA_STAGES] = {}, issued_b[2] = {false, false};
+    uint32_t last_a_parity[NA] = {}, last_b_parity[2] = {0, 0};
+    bool issued_a[NA] = {}, issued_b[2] = {false, false};
     int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
       while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
@@ -127,7 +140,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
               tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
             issued_a[ia] = true;
             last_a_parity[ia] = pa;
-            if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+            if (++ia == NA) { ia = 0; pa ^= 1; }
           }
         }
       }
@@ -135,7 +148,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     }
     // make sure no TMA write into this CTA's shared memory is still in flight
     volatile int no_abort = 0;
-    for (int s = 0; s < NA_STAGES; ++s)
+    for (int s = 0; s < NA; ++s)
       if (issued_a[s]) wait_bar(&sm.full_a[s], last_a_parity[s], &no_abort, err, 7);
     for (int s = 0; s < 2; ++s)
       if (issued_b[s]) wait_bar(&sm.full_b[s], last_b_parity[s], &no_abort, err, 7);
@@ -151,44 +164,86 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       while (pi + 1 < gb.count && t >= gb.p[pi + 1].tile_begin) ++pi;
       const int Nk = gb.p[pi].N;
       const int nK = (Nk + KB - 1) / KB;
-      if (local > 0) {
-        if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
+      bool ok = true;
+      if (!OVL && local > 0) {
+        for (int g = 0; g < G && ok; ++g) ok = wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3);
+        if (!ok) break;
       }
       tc::fence_after_sync();
-      bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
         tc::fence_after_sync();
         // the last K block may hold no more than 16 valid columns: one K = 16 step then
         const bool two_k = (Nk - kb * KB) > 16;
-        for (int i = 0; i < S; ++i) {
-          if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+        const uint64_t b_0 = tc::desc_sw64(tc::smem_u32(sm.b[ib][0][0]));
+        // one slice pair (i, j) into accumulator d: A_re [B_re; B_im] and (-A_im) [B_im; -B_re];
+        // ow: the first MMA overwrites the accumulator (first pair of its group in a tile)
+        auto pair = [&](uint64_t a_re, uint64_t a_im, int j, uint32_t d, bool ow) {
+          const uint64_t b_re = b_0 + (uint64_t)(j * 3 * (B_TILE >> 4));  // rows [re; im]
+          const uint64_t b_im = b_re + (B_TILE >> 4);                      // rows [im; -re]
+          tc::mma_f16(d, a_re, b_re, ID, ow ? 0u : 1u);
+          tc::mma_f16(d, a_im, b_im, IDN, 1u);
+          if (two_k) {  // second K = 16 step: 32 bytes further inside the 64-byte swizzle row
+            tc::mma_f16(d, a_re + 2, b_re + 2, ID, 1u);
+            tc::mma_f16(d, a_im + 2, b_im + 2, IDN, 1u);
+          }
+        };
+        if (OVL && kb == 0) {
+          // first K block: all S slices of A, then the pairs group by group; group g waits
+          // until the previous tile's epilogue has read its accumulator
+          uint64_t dre[OVL ? S : 1], dim[OVL ? S : 1];
+          int stage[OVL ? S : 1];
+          for (int i = 0; i < S && ok; ++i) {
+            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+            stage[i] = ia;
+            dre[i] = tc::desc_sw64(tc::smem_u32(sm.a[ia][0]));
+            dim[i] = tc::desc_sw64(tc::smem_u32(sm.a[ia][1]));
+            if (++ia == NA) { ia = 0; pa ^= 1; }
+          }
+          if (!ok) break;
           tc::fence_after_sync();
-          // descriptors: start addresses differ only in bits 0-13, so they are formed once and
-          // advanced by adding (byte offset >> 4)
-          const uint64_t a_re = tc::desc_sw64(tc::smem_u32(sm.a[ia][0]));
-          const uint64_t a_im = tc::desc_sw64(tc::smem_u32(sm.a[ia][1]));
-          const uint64_t b_0 = tc::desc_sw64(tc::smem_u32(sm.b[ib][0][0]));
-          // in the first K block of a tile, the first pair of each group (i = 0, j = g for g < 4,
-          // and j = 4 for the merged group) overwrites its accumulator
-          const bool first = (kb == 0) && (i == 0);
 #pragma unroll
-          for (int j = 0; j < S; ++j) {
-            if (j + i >= S) break;
-            const int g = min(i + j, NGROUPS - 1);
+          for (int g = 0; g < G; ++g) {
+            if (local > 0 && !wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3)) { ok = false; break; }
+            tc::fence_after_sync();
             const uint32_t d = tmem + (uint32_t)(g * NACC);
-            const uint64_t b_re = b_0 + (uint64_t)(j * 3 * (B_TILE >> 4));  // rows [re; im]
-            const uint64_t b_im = b_re + (B_TILE >> 4);                      // rows [im; -re]
-            tc::mma_f16(d, a_re, b_re, ID, (first && j < NGROUPS) ? 0u : 1u);
-            tc::mma_f16(d, a_im, b_im, IDN, 1u);
-            if (two_k) {  // second K = 16 step: 32 bytes further inside the 64-byte swizzle row
-              tc::mma_f16(d, a_re + 2, b_re + 2, ID, 1u);
-              tc::mma_f16(d, a_im + 2, b_im + 2, IDN, 1u);
+            if (g < NGROUPS - 1) {
+#pragma unroll
+              for (int i = 0; i <= g; ++i) pair(dre[i], dim[i], g - i, d, i == 0);
+            } else {
+              // merged group: every pair with i + j >= NGROUPS - 1, slice by slice
+#pragma unroll
+              for (int i = 0; i < S; ++i)
+#pragma unroll
+                for (int j = (NGROUPS - 1 - i > 0 ? NGROUPS - 1 - i : 0); j + i < S; ++j)
+                  pair(dre[i], dim[i], j, d, i == 0 && j == NGROUPS - 1);
             }
           }
+          if (!ok) break;
           any = true;
-          tc::mma_commit(&sm.empty_a[ia]);
-          if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
+          // every slice of this K block has had its last pair
+          for (int i = 0; i < S; ++i) tc::mma_commit(&sm.empty_a[stage[i]]);
+        } else {
+          for (int i = 0; i < S; ++i) {
+            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+            tc::fence_after_sync();
+            // descriptors: start addresses differ only in bits 0-13, so they are formed once and
+            // advanced by adding (byte offset >> 4)
+            const uint64_t a_re = tc::desc_sw64(tc::smem_u32(sm.a[ia][0]));
+            const uint64_t a_im = tc::desc_sw64(tc::smem_u32(sm.a[ia][1]));
+            // (without the group overlap) in the first K block of a tile, the first pair of each
+            // group (i = 0, j = g for g < 4, and j = 4 for the merged group) overwrites it
+            const bool first = (kb == 0) && (i == 0);
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+              if (j + i >= S) break;
+              const int g = min(i + j, NGROUPS - 1);
+              pair(a_re, a_im, j, tmem + (uint32_t)(g * NACC), first && j < NGROUPS);
+            }
+            any = true;
+            tc::mma_commit(&sm.empty_a[ia]);
+            if (++ia == NA) { ia = 0; pa ^= 1; }
+          }
         }
         if (!ok) break;
         tc::mma_commit(&sm.empty_b[ib]);
@@ -212,7 +267,6 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
     const int half = (warp - 2) >> 2;  // 0: columns [0, BN/2), 1: [BN/2, BN)
     const int row = quarter * 32 + lane;
     uint32_t pacc = 0;
-    constexpr int G = S < NGROUPS ? S : NGROUPS;
     constexpr int HALF = BN / 2;
     int pi = 0;
     for (long long t = blockIdx.x; t < ntiles && !sm.abort_flag; t += gridDim.x) {
@@ -236,47 +290,62 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       pacc ^= 1;
       tc::fence_after_sync();
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + half * HALF;
-#pragma unroll 1
-      for (int ch = 0; ch < HALF / 8; ++ch) {
-        float re[NGROUPS][8], im[NGROUPS][8];
+      // digit groups one at a time, each released as soon as it is read, summed in
+      // double-float in the order of df_sum: TwoSum chain over groups 0-3 into (s, e),
+      // then e += group 4 (the merged group); hi = s + e, lo = e - (hi - s)
+      float sr[HALF], er[HALF], si[HALF], ei[HALF];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          tc::tmem_ld8(lane_base + (uint32_t)(g * NACC) + ch * 8, re[g]);
-          tc::tmem_ld8(lane_base + (uint32_t)(g * NACC + BN) + ch * 8, im[g]);
+      for (int g = 0; g < NGROUPS; ++g) {
+        float re[HALF], im[HALF];
+        if (g < G) {
+#pragma unroll
+          for (int ch = 0; ch < HALF / 8; ++ch) {
+            tc::tmem_ld8(lane_base + (uint32_t)(g * NACC) + ch * 8, re + ch * 8);
+            tc::tmem_ld8(lane_base + (uint32_t)(g * NACC + BN) + ch * 8, im + ch * 8);
+          }
+          tc::tmem_wait_ld();
+          tc::fence_before_sync();
+          tc::mbar_arrive(&sm.acc_empty[g]);  // the next tile may overwrite this group now
+        } else {
+#pragma unroll
+          for (int c = 0; c < HALF; ++c) { re[c] = 0.f; im[c] = 0.f; }
         }
-        tc::tmem_wait_ld();
 #pragma unroll
-        for (int g = G; g < NGROUPS; ++g)
-#pragma unroll
-          for (int c = 0; c < 8; ++c) { re[g][c] = 0.f; im[g][c] = 0.f; }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int n = n0 + ch * 8 + c;
-          if (!mvalid || n >= N) continue;
-          float ar[NGROUPS], ai[NGROUPS];
-#pragma unroll
-          for (int g = 0; g < NGROUPS; ++g) { ar[g] = re[g][c]; ai[g] = im[g][c]; }
-          float rh, rl, ih, il;
-          df_sum(ar, rh, rl);
-          df_sum(ai, ih, il);
-          const int k = ea + __ldg(expB + n) - 14;
-          const int k1 = k / 2, k2 = k - k1;
-          const float f = pow2f(k1) * pow2f(k2);
-          if (plain) {
-            crow[n] = make_float4(rh * f, rl * f, ih * f, il * f);
+        for (int c = 0; c < HALF; ++c) {
+          if (g == 0) {
+            sr[c] = re[c]; er[c] = 0.f; si[c] = im[c]; ei[c] = 0.f;
+          } else if (g < NGROUPS - 1) {
+            float e1, e2;
+            two_sum(sr[c], re[c], sr[c], e1);
+            two_sum(si[c], im[c], si[c], e2);
+            if (g == 1) { er[c] = e1; ei[c] = e2; } else { er[c] = er[c] + e1; ei[c] = ei[c] + e2; }
           } else {
-            cdf v{dfl{rh * f, rl * f}, dfl{ih * f, il * f}};
-            if (use_alpha) v = cdf_mul(v, dfl{alpha.x, alpha.y}, dfl{alpha.z, alpha.w});
-            if (accumulate) {
-              const float4 o = crow[n];
-              v = cdf_add(v, cdf{dfl{o.x, o.y}, dfl{o.z, o.w}});
-            }
-            crow[n] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+            er[c] = er[c] + re[c];
+            ei[c] = ei[c] + im[c];
           }
         }
       }
-      tc::fence_before_sync();
-      tc::mbar_arrive(&sm.acc_empty);
+#pragma unroll
+      for (int c = 0; c < HALF; ++c) {
+        const int n = n0 + c;
+        if (!mvalid || n >= N) continue;
+        const float rh = sr[c] + er[c], rl = er[c] - (rh - sr[c]);
+        const float ih = si[c] + ei[c], il = ei[c] - (ih - si[c]);
+        const int k = ea + __ldg(expB + n) - 14;
+        const int k1 = k / 2, k2 = k - k1;
+        const float f = pow2f(k1) * pow2f(k2);
+        if (plain) {
+          crow[n] = make_float4(rh * f, rl * f, ih * f, il * f);
+        } else {
+          cdf v{dfl{rh * f, rl * f}, dfl{ih * f, il * f}};
+          if (use_alpha) v = cdf_mul(v, dfl{alpha.x, alpha.y}, dfl{alpha.z, alpha.w});
+          if (accumulate) {
+            const float4 o = crow[n];
+            v = cdf_add(v, cdf{dfl{o.x, o.y}, dfl{o.z, o.w}});
+          }
+          crow[n] = make_float4(v.re.h, v.re.l, v.im.h, v.im.l);
+        }
+      }
     }
   }
   tc::fence_before_sync();
