@@ -1,0 +1,95 @@
+"""Timing sweep over the axes of the paper's benchmark (the GPU rows of its parameter
+table: SU(N) for N in {121, 169, 225, 289}, truncation orders 15, 31, 63, trajectories of
+40 MD steps): for every point, one MD trajectory of one configuration (momentum refresh
+plus 40 leapfrog steps, split form) split into its force and link-update phases, and the
+split FFT-CONV product rate at batch 4.  Prints a markdown table.
+
+    python -m paper_2001_02835_b300.sweep [--N 121,169,225,289] [--T 15,31,63] [--md-steps 40]
+
+Inputs are the synthetic, seeded link series of the benchmark (twist eaters at order 0,
+Gaussian orders >= 1); timings are CUDA events on the current stream after one warm-up.
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import sys
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import nspt_synth as syn  # noqa: E402
+import paper_2001_02835_b300 as nspt  # noqa: E402
+
+
+def _time(fn, reps=1):
+    fn()
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        fn()
+    e.record()
+    torch.cuda.synchronize()
+    return s.elapsed_time(e) / reps
+
+
+def flux_for(L):
+    return next(k for k in (1, 2, 3, 4, 5) if math.gcd(k, L) == 1)
+
+
+def md_point(N, T, steps, eps=0.02):
+    L = int(round(math.sqrt(N)))
+    flux = flux_for(L)
+    g = syn.rng(syn.SEED_BASE + 5)
+    U0 = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, flux, T, 1))).cuda()
+    eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, N, 4).reshape(1, 4, N, N))).cuda()
+    U, P = U0.clone(), torch.zeros_like(U0)
+    nspt.tek_md_trajectory(U, P, flux, eps, 2, eta=eta, algo="fft", prec="split")   # warm-up
+    torch.cuda.synchronize()
+    U.copy_(U0)
+    nspt.profile_begin(400000)
+    ms = _time(lambda: nspt.tek_md_trajectory(U, P, flux, eps, steps, eta=eta, algo="fft", prec="split"), 1)
+    ph = nspt.profile_end()
+    # the profile holds the warm-up call of _time and the timed call: halve
+    return ms, ph.get("md_force", (0.0, 0))[0] / 2, ph.get("md_link", (0.0, 0))[0] / 2
+
+
+def product_point(N, T, batch=4):
+    g = syn.rng(syn.SEED_BASE + 6)
+    A = torch.from_numpy(syn.series_batch(g, N, T, batch)).cuda()
+    B = torch.from_numpy(syn.series_batch(g, N, T, batch)).cuda()
+    C = torch.empty_like(A)
+    ms = _time(lambda: nspt.polymat_mul(A, B, C, algo="fft", prec="split"), 5)
+    return batch / (ms * 1e-3)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", default="121,169,225,289")
+    ap.add_argument("--T", default="15,31,63")
+    ap.add_argument("--md-steps", type=int, default=40)
+    a = ap.parse_args(argv)
+    torch.cuda.set_device(0)
+    if nspt.lib().nspt_init() != 0:
+        raise SystemExit("nspt_init failed")
+    Ns = [int(x) for x in a.N.split(",")]
+    Ts = [int(x) for x in a.T.split(",")]
+    print("| N | T | MD trajectory (%d steps) s | force s | link update s | 10 trajectories s | products/s |"
+          % a.md_steps)
+    print("|---|---|---|---|---|---|---|")
+    for N in Ns:
+        for T in Ts:
+            ms, f, lk = md_point(N, T, a.md_steps)
+            pps = product_point(N, T)
+            print("| %d | %d | %.3f | %.3f | %.3f | %.1f | %.0f |" % (N, T, ms / 1e3, f / 1e3, lk / 1e3, ms / 100.0, pps))
+            sys.stdout.flush()
+
+
+if __name__ == "__main__":
+    main()
