@@ -1,0 +1,90 @@
+"""Invariants of the GPU path that hold at any size: associativity of the truncated
+product, 1 x 1 series as scalar polynomials, and unitarity of the link series through
+the Langevin step and MD trajectories (exp_star(i X) is unitary for Hermitian X, i.e.
+exp_star(iX) * exp_star(-iX) = 1 through order T), in every form."""
+import numpy as np
+import pytest
+import torch
+
+import nspt_synth as syn
+from oracle import polymat as pm
+from oracle import tek
+
+from tests.gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+FORMS = [("naive", "fp64"), ("fft", "fp64"), ("fft", "split")]
+
+
+@pytest.fixture(scope="module")
+def nspt():
+    import paper_2001_02835_b300 as n
+    assert n.lib().nspt_init() == 0
+    return n
+
+
+@pytest.mark.parametrize("algo,prec", FORMS)
+def test_product_is_associative(nspt, algo, prec):
+    g = syn.rng(7500)
+    N, T, batch = 33, 15, 2
+    A, B, C = (dev(syn.series_batch(g, N, T, batch)) for _ in range(3))
+    left = nspt.polymat_mul(nspt.polymat_mul(A, B, algo=algo, prec=prec), C, algo=algo, prec=prec)
+    right = nspt.polymat_mul(A, nspt.polymat_mul(B, C, algo=algo, prec=prec), algo=algo, prec=prec)
+    den = torch.linalg.matrix_norm(left).clamp_min(1e-300)
+    err = (torch.linalg.matrix_norm(left - right) / den).max().item()
+    assert err <= (1e-12 if prec == "fp64" else 1e-11)
+
+
+@pytest.mark.parametrize("algo,prec", FORMS)
+def test_one_by_one_series_are_scalar_polynomials(nspt, algo, prec):
+    g = syn.rng(7501)
+    T, batch = 20, 3
+    a = g.normal(size=(batch, T + 1)) + 1j * g.normal(size=(batch, T + 1))
+    b = g.normal(size=(batch, T + 1)) + 1j * g.normal(size=(batch, T + 1))
+    C = host(nspt.polymat_mul(dev(a.reshape(batch, T + 1, 1, 1).copy()), dev(b.reshape(batch, T + 1, 1, 1).copy()),
+                              algo=algo, prec=prec)).reshape(batch, T + 1)
+    for i in range(batch):
+        ref = np.polynomial.polynomial.polymul(a[i], b[i])[:T + 1]
+        assert np.abs(C[i] - ref).max() <= (1e-12 if prec == "fp64" else 1e-11) * np.abs(ref).max()
+
+
+def _unitary_links(rg, L, k, T, streams):
+    """U = exp_star(i H) * Gamma with Hermitian H (H^(0) = 0): a unitary series at every order."""
+    N = L * L
+    out = np.empty((streams, 4, T + 1, N, N), np.complex128)
+    for s in range(streams):
+        H = syn.gaussian(rg, (4, T + 1, N, N), 1.0 / N)
+        H = 0.5 * (H + np.conj(np.swapaxes(H, -1, -2)))
+        H[:, 0] = 0
+        G = np.zeros((4, T + 1, N, N), np.complex128)
+        G[:, 0] = syn.twist_eaters(L, k)
+        out[s] = pm.star(tek.exp_star(1j * H), G)
+    return out
+
+
+def _unitarity_defect(nspt, U):
+    s4 = U.shape[0] * 4
+    Uf = U.reshape(s4, *U.shape[2:]).contiguous()
+    P = nspt.polymat_mul(Uf, Uf.conj().transpose(-1, -2).contiguous(), algo="fft", prec="fp64")
+    I = torch.zeros_like(P)
+    I[:, 0] = torch.eye(U.shape[-1], dtype=P.dtype, device=P.device)
+    return (P - I).abs().max().item()
+
+
+@pytest.mark.parametrize("algo,prec", FORMS)
+def test_langevin_and_md_keep_links_unitary(nspt, algo, prec):
+    rg = syn.rng(7502)
+    L, k, T, streams = 3, 1, 10, 2
+    N = L * L
+    U = dev(_unitary_links(rg, L, k, T, streams))
+    assert _unitarity_defect(nspt, U) < 1e-12
+    eta = dev(np.ascontiguousarray(syn.hermitian_noise(rg, N, 4 * streams).reshape(streams, 4, N, N)))
+    tol = 1e-12 if prec == "fp64" else 1e-10
+    U1 = U.clone()
+    nspt.tek_langevin_step(U1, eta, k, 0.05, algo=algo, prec=prec)
+    assert _unitarity_defect(nspt, U1) < tol
+    assert (U1 - U).abs().max().item() > 1e-3
+    P = torch.zeros_like(U)
+    nspt.tek_md_trajectory(U1, P, k, 0.05, 5, eta=eta, algo=algo, prec=prec)
+    assert _unitarity_defect(nspt, U1) < 5 * tol
