@@ -126,9 +126,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
         if (!isA) {
           if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
-          for (int j = 0; j < S; ++j)
-            for (int c = 0; c < 3; ++c)
-              tc::tma_load_3d(sm.b[ib][j][c], &P.mB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
+          tc::tma_load_4d(sm.b[ib][0][0], &P.mB, &sm.full_b[ib], kb * KB, n0, 0, q * S);  // [S][3][BN][32]
           issued_b[ib] = true;
           last_b_parity[ib] = pb;
           if (++ib == 2) { ib = 0; pb ^= 1; }
@@ -136,8 +134,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           for (int i = 0; i < S; ++i) {
             if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
             tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
-            for (int c = 0; c < 2; ++c)
-              tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
+            tc::tma_load_4d(sm.a[ia][0], &P.mA, &sm.full_a[ia], kb * KB, m0, 0, q * S + i);  // [2][BM][32]
             issued_a[ia] = true;
             last_a_parity[ia] = pa;
             if (++ia == NA) { ia = 0; pa ^= 1; }
@@ -412,12 +409,13 @@ int set_attrs() {
 }  // namespace
 
 // 3-D map over slice planes: (k < N, row < N, plane), row pitch Kp bf16
-int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes, int box_rows) {
-  cuuint64_t dims[3] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)N * Kp * 2};
-  cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, 1};
-  cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, int P, long long nslices, int box_rows,
+                        int box_slices) {
+  cuuint64_t dims[4] = {(cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)P, (cuuint64_t)nslices};
+  cuuint64_t strides[3] = {(cuuint64_t)Kp * 2, (cuuint64_t)N * Kp * 2, (cuuint64_t)P * N * Kp * 2};
+  cuuint32_t box[4] = {(cuuint32_t)KB, (cuuint32_t)box_rows, (cuuint32_t)P, (cuuint32_t)box_slices};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;

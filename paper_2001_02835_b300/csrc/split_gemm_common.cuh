@@ -83,9 +83,11 @@ __device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, flo
 
 }  // namespace sg
 
-// 3-D TMA map over slice planes: (k < N, row < N, plane), row pitch Kp bf16, box (32, box_rows, 1),
+// 4-D TMA map over digit slices: (k < N, row < N, plane < P, slice < nslices), row pitch Kp bf16,
+// box (32, box_rows, P, box_slices): one copy brings every plane of box_slices consecutive slices;
 // 64-byte swizzle (split_gemm.cu)
-int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, long long planes, int box_rows);
+int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, int P, long long nslices, int box_rows,
+                        int box_slices);
 
 namespace sg {
 
@@ -96,8 +98,9 @@ int build_batch(GemmBatch<MAXP>* gb, const SplitGemmArgs* a, int count, int S, i
   for (int i = 0; i < count; ++i) {
     GemmProblem& P = gb->p[i];
     // left operand: planes (re, im) per digit; right operand: (re, im, -re)
-    if (nspt_make_slice_map(&P.mA, a[i].slicesA, a[i].N, a[i].Kp, (long long)a[i].Q * S * 2, BM)) return -5;
-    if (nspt_make_slice_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, (long long)a[i].Q * S * 3, bn)) return -5;
+    // A: one slice (re, im) per copy; B: all S slices (re, im, -re) of a K block in one copy
+    if (nspt_make_slice_map(&P.mA, a[i].slicesA, a[i].N, a[i].Kp, 2, (long long)a[i].Q * S, BM, 1)) return -5;
+    if (nspt_make_slice_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, 3, (long long)a[i].Q * S, bn, S)) return -5;
     P.expA = a[i].expA; P.expB = a[i].expB; P.C = a[i].C;
     P.N = a[i].N; P.Q = a[i].Q;
     P.tilesM = (a[i].N + BM - 1) / BM;

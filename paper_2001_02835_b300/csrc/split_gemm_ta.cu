@@ -97,17 +97,14 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
         tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE_T);
-        for (int j = 0; j < S; ++j)
-          for (int c = 0; c < 3; ++c)
-            tc::tma_load_3d(sm.b[ib][j][c], &P.mB, &sm.full_b[ib], kb * KB, n0, (q * S + j) * 3 + c);
+        tc::tma_load_4d(sm.b[ib][0][0], &P.mB, &sm.full_b[ib], kb * KB, n0, 0, q * S);  // [S][3][BN][32]
         issued_b[ib] = true;
         last_b_parity[ib] = pb;
         if (++ib == 2) { ib = 0; pb ^= 1; }
         for (int i = 0; i < S; ++i) {
           if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
-          for (int c = 0; c < 2; ++c)
-            tc::tma_load_3d(sm.a[ia][c], &P.mA, &sm.full_a[ia], kb * KB, m0, (q * S + i) * 2 + c);
+          tc::tma_load_4d(sm.a[ia][0], &P.mA, &sm.full_a[ia], kb * KB, m0, 0, q * S + i);  // [2][BM][32]
           issued_a[ia] = true;
           last_a_parity[ia] = pa;
           if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
