@@ -64,7 +64,7 @@ fft_fwd64_kernel(const double2* __restrict__ in, long long in_stride, double2* _
   for (int h = M / 4; h >= 1; h >>= 1) {
     const int tstep = M / (2 * h);
     for (int bf = y; bf < M / 2; bf += 8) {
-      const int g = bf / h, j = bf % h;
+      const int g = bf >> (__ffs(h) - 1), j = bf & (h - 1);  // h is a power of two
       const int i0 = g * 2 * h + j, i1 = i0 + h;
       const double2 u = sm[i0 * EB + e], v = sm[i1 * EB + e];
       sm[i0 * EB + e] = cadd(u, v);
@@ -105,7 +105,7 @@ fft_inv64_kernel(const InT* __restrict__ in, double2* __restrict__ out, long lon
   for (int h = 1; h <= M / 4; h <<= 1) {
     const int tstep = M / (2 * h);
     for (int bf = y; bf < M / 2; bf += 8) {
-      const int g = bf / h, j = bf % h;
+      const int g = bf >> (__ffs(h) - 1), j = bf & (h - 1);  // h is a power of two
       const int i0 = g * 2 * h + j, i1 = i0 + h;
       const double2 u = sm[i0 * EB + e];
       double2 v = sm[i1 * EB + e];

@@ -109,7 +109,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   for (; 2 * h <= M / 4; h <<= 2) {
     const int tstep = M / (4 * h);  // w_L^-m = conj(w_M^(m M / L)), L = 4h
     for (int u = y; u < M / 4; u += 8) {
-      const int g = u / h, n = u % h;
+      const int g = u >> (__ffs(h) - 1), n = u & (h - 1);  // h is a power of two
       const int base = g * 4 * h + n;
       cdf a = ld(&sm[base * EB + e]), bq = ld(&sm[(base + h) * EB + e]);
       cdf c = ld(&sm[(base + 2 * h) * EB + e]), d = ld(&sm[(base + 3 * h) * EB + e]);
@@ -131,7 +131,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   if (h <= M / 4) {  // one radix-2 DIT stage of span h left
     const int tstep = M / (2 * h);
     for (int bf = y; bf < M / 2; bf += 8) {
-      const int g = bf / h, j = bf % h;
+      const int g = bf >> (__ffs(h) - 1), j = bf & (h - 1);
       const int i0 = g * 2 * h + j, i1 = i0 + h;
       const cdf u = ld(&sm[i0 * EB + e]);
       cdf v = ld(&sm[i1 * EB + e]);

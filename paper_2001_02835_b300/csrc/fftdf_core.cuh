@@ -98,7 +98,7 @@ __device__ __forceinline__ void fwd_to_smem(float4* sm, const double2* __restric
     const int q4 = h / 2;   // quarter of the group of size L = 2h
     const int tstep = M / (2 * h);
     for (int u = y; u < M / 4; u += 8) {
-      const int g = u / q4, n = u % q4;
+      const int g = u >> (__ffs(q4) - 1), n = u & (q4 - 1);  // q4 is a power of two
       const int base = g * 2 * h + n;
       const cdf x0 = ld(&sm[base * EB + e]), x1 = ld(&sm[(base + q4) * EB + e]);
       const cdf x2 = ld(&sm[(base + 2 * q4) * EB + e]), x3 = ld(&sm[(base + 3 * q4) * EB + e]);
