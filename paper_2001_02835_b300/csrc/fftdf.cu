@@ -75,7 +75,7 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   return df_fast(p, e);
 }
 
-// post: extra real double-float factor (1/n of Horner); add_identity: + 1 on the
+// post: extra real double-float factor on the result; add_identity: + 1 on the
 // diagonal of order 0 (entry e is (e / N, e % N)); orders below kmin are not stored
 template <int M, int EB>
 __global__ void __launch_bounds__(EB * 8)
