@@ -40,7 +40,10 @@ extern "C" {
 
 typedef enum nspt_status {
   NSPT_OK = 0,
-  NSPT_ERR_ARG = -1,          /* bad size, NULL pointer, bad option */
+  NSPT_ERR_ARG = -1,          /* bad size, NULL pointer, bad option, or a buffer in the wrong
+                                 kind of memory (host memory where device memory is expected,
+                                 or the reverse; checked with cudaPointerGetAttributes unless the
+                                 stream is being captured into a graph) */
   NSPT_ERR_ALIAS = -2,        /* an output overlaps an input */
   NSPT_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
   NSPT_ERR_WORKSPACE = -4,    /* opts->workspace missing or too small */
@@ -263,6 +266,17 @@ NSPT_API const char* nspt_stage_name(int stage);
  * set, else NSPT_OK.  Not for use inside graph capture.
  */
 NSPT_API int nspt_device_status(const nspt_opts* opts, void* stream);
+
+/*
+ * Test hook (no counterpart in the paper): budget in ns of the tensor-core
+ * GEMMs' device-side waits that may abandon a launch (default 2 s); applies to
+ * launches enqueued afterwards.  A negative budget makes every such wait give
+ * up at once, so that the launch exits cleanly -- the copies and MMAs already
+ * in flight are still drained -- and nspt_device_status reports
+ * NSPT_ERR_TIMEOUT: the timeout path can be exercised without a hung GPU.
+ * Results of a launch that gave up are undefined.
+ */
+NSPT_API int nspt_debug_wait_budget(long long ns);
 
 /*
  * Stage entry points of the split form, for stage tests and timing.

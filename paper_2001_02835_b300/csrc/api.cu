@@ -687,6 +687,10 @@ int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int ba
   if ((rc = check_ws(opts, ws_mul(p)))) return rc;
   if ((rc = nspt_init())) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const void* ptrs[3] = {A, B, C};
+    if ((rc = nspt_check_ptrs(st, true, ptrs, 3))) return rc;
+  }
   if (p.prec == NSPT_PREC_FP64)
     return mul_fp64(p, (const double2*)A, (const double2*)B, (double2*)C, opts ? opts->workspace : nullptr, st);
   return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, (const double2*)A,
@@ -708,6 +712,10 @@ int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void
   if ((rc = check_ws(opts, ws_bwd(p)))) return rc;
   if ((rc = nspt_init())) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  {
+    const void* ptrs[5] = {A, B, gC, gA, gB};
+    if ((rc = nspt_check_ptrs(st, true, ptrs, 5))) return rc;
+  }
   if (p.prec == NSPT_PREC_FP64)
     return bwd_fp64(p, (const double2*)A, (const double2*)B, (const double2*)gC, (double2*)gA, (double2*)gB,
                     opts ? opts->workspace : nullptr, st);
@@ -733,6 +741,10 @@ int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int 
     return NSPT_ERR_ALIAS;
   if ((rc = check_ws(opts, ws_langevin(p)))) return rc;
   if ((rc = nspt_init())) return rc;
+  {
+    const void* ptrs[3] = {U, eta, F};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
+  }
   if (p.prec != NSPT_PREC_FP64) {
     return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, (double2*)U, (const double2*)eta, (double2*)F, flux,
                                eps, opts->workspace, (cudaStream_t)stream);
@@ -781,6 +793,10 @@ int nspt_polymat_mul_grouped(const nspt_polymat_desc* d, int count, const nspt_o
   if ((rc = check_ws(o, nspt_workspace_size_grouped(d, count, o)))) return rc;
   if ((rc = nspt_init())) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < count; ++i) {
+    const void* ptrs[3] = {d[i].A, d[i].B, d[i].C};
+    if ((rc = nspt_check_ptrs(st, true, ptrs, 3))) return rc;
+  }
   if (p.prec == NSPT_PREC_SPLIT) {
     if (p.rescale_auto) return NSPT_ERR_UNSUPPORTED;
     return nspt_split_mul_grouped(d, count, p.slices, p.log2r, o->workspace, st);
@@ -803,6 +819,10 @@ int nspt_autotune_grouped(const nspt_polymat_desc* d, int count, const nspt_opts
   if (!chosen_bn || p.prec != NSPT_PREC_SPLIT) return NSPT_ERR_ARG;
   if ((rc = check_ws(o, nspt_workspace_size_grouped(d, count, o)))) return rc;
   if ((rc = nspt_init())) return rc;
+  for (int i = 0; i < count; ++i) {
+    const void* ptrs[3] = {d[i].A, d[i].B, d[i].C};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
+  }
   return nspt_split_autotune_grouped(d, count, p.slices, o->workspace, cache_path, chosen_bn, (cudaStream_t)stream);
 }
 
@@ -825,6 +845,10 @@ int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, int N, int
     return NSPT_ERR_ALIAS;
   if ((rc = check_ws(opts, ws_md(p)))) return rc;
   if ((rc = nspt_init())) return rc;
+  {
+    const void* ptrs[3] = {U, P, eta_refresh};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
+  }
   return md_run(p, (double2*)U, (double2*)P, (const double2*)eta_refresh, flux, eps, nsteps, opts->workspace,
                 (cudaStream_t)stream);
 }
@@ -851,6 +875,10 @@ int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int 
   if (overlaps(U, ubytes, W, wbytes)) return NSPT_ERR_ALIAS;
   if ((rc = check_ws(opts, ws_wilson(p, amax)))) return rc;
   if ((rc = nspt_init())) return rc;
+  {
+    const void* ptrs[2] = {U, W};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 2))) return rc;
+  }
   return wilson_run(p, (const double2*)U, flux, amax, (double2*)W, opts->workspace, (cudaStream_t)stream);
 }
 
@@ -872,10 +900,21 @@ int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, i
   if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return NSPT_ERR_ALIAS;
   if ((rc = check_ws(opts, ws_host(pc)))) return rc;
   if ((rc = nspt_init())) return rc;
+  {
+    const void* hptrs[3] = {A, B, C};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, false, hptrs, 3))) return rc;
+    const void* dptrs[1] = {opts->workspace};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, dptrs, 1))) return rc;
+  }
   HostPipe* hp = nullptr;
   if ((rc = host_pipe(&hp))) return rc;
   return host_run(pc, batch, (const double2*)A, (const double2*)B, (double2*)C, opts->workspace, *hp,
                   (cudaStream_t)stream);
+}
+
+int nspt_debug_wait_budget(long long ns) {
+  nspt_split_set_wait_budget(ns);
+  return NSPT_OK;
 }
 
 int nspt_order_fft(const void* A, void* At, int N, int T, int batch, int M, void* stream) {

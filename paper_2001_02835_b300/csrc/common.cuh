@@ -14,6 +14,32 @@
 
 void nspt_set_last_cuda_error(cudaError_t e);
 
+// Pointer kinds of an entry point's buffers, checked on the host before any
+// launch, so that a host pointer where device memory is expected (or the
+// reverse) returns NSPT_ERR_ARG instead of faulting a kernel.  Skipped while
+// `st` is being captured into a graph.  NULL entries are skipped.
+inline int nspt_check_ptrs(cudaStream_t st, bool device, const void* const* ptrs, int n) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return NSPT_ERR_ARG;
+  }
+  if (cs != cudaStreamCaptureStatusNone) return NSPT_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!ptrs[i]) continue;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptrs[i]) != cudaSuccess) {
+      cudaGetLastError();
+      return NSPT_ERR_ARG;
+    }
+    const bool dev_ok = a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    const bool host_ok = a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered ||
+                         a.type == cudaMemoryTypeManaged;
+    if (device ? !dev_ok : !host_ok) return NSPT_ERR_ARG;
+  }
+  return NSPT_OK;
+}
+
 // ---------------------------------------------------------------------------
 // complex double helpers (interleaved re, im = double2)
 // ---------------------------------------------------------------------------

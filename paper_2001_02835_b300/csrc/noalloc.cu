@@ -69,6 +69,10 @@ extern "C" NSPT_API int nspt_polymat_mul_fft_noalloc(const void* A, const void* 
   if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return NSPT_ERR_ALIAS;
   int rc = nspt_init();
   if (rc) return rc;
+  {
+    const void* ptrs[3] = {A, B, C};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
+  }
   void* base = nullptr;
   if ((rc = scratch_address(&base))) return rc;
   double2* At = (double2*)base;

@@ -36,6 +36,7 @@
 #include "dfloat.cuh"
 #include "split_gemm_common.cuh"
 
+#include <atomic>
 #include <cstring>
 #include <memory>
 
@@ -124,7 +125,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
         if (!isA) {
-          if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
+          if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1, gb.wait_ns)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE);
           tc::tma_load_4d(sm.b[ib][0][0], &P.mB, &sm.full_b[ib], kb * KB, n0, 0, q * S);  // [S][3][BN][32]
           issued_b[ib] = true;
@@ -132,7 +133,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           if (++ib == 2) { ib = 0; pb ^= 1; }
         } else {
           for (int i = 0; i < S; ++i) {
-            if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
+            if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2, gb.wait_ns)) { ok = false; break; }
             tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
             tc::tma_load_4d(sm.a[ia][0], &P.mA, &sm.full_a[ia], kb * KB, m0, 0, q * S + i);  // [2][BM][32]
             issued_a[ia] = true;
@@ -163,12 +164,12 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int nK = (Nk + KB - 1) / KB;
       bool ok = true;
       if (!OVL && local > 0) {
-        for (int g = 0; g < G && ok; ++g) ok = wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3);
+        for (int g = 0; g < G && ok; ++g) ok = wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3, gb.wait_ns);
         if (!ok) break;
       }
       tc::fence_after_sync();
       for (int kb = 0; kb < nK && ok; ++kb) {
-        if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
+        if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4, gb.wait_ns)) { ok = false; break; }
         tc::fence_after_sync();
         // the last K block may hold no more than 16 valid columns: one K = 16 step then
         const bool two_k = (Nk - kb * KB) > 16;
@@ -191,7 +192,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           uint64_t dre[OVL ? S : 1], dim[OVL ? S : 1];
           int stage[OVL ? S : 1];
           for (int i = 0; i < S && ok; ++i) {
-            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5, gb.wait_ns)) { ok = false; break; }
             stage[i] = ia;
             dre[i] = tc::desc_sw64(tc::smem_u32(sm.a[ia][0]));
             dim[i] = tc::desc_sw64(tc::smem_u32(sm.a[ia][1]));
@@ -201,7 +202,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           tc::fence_after_sync();
 #pragma unroll
           for (int g = 0; g < G; ++g) {
-            if (local > 0 && !wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3)) { ok = false; break; }
+            if (local > 0 && !wait_bar(&sm.acc_empty[g], pacc ^ 1, &sm.abort_flag, err, 3, gb.wait_ns)) { ok = false; break; }
             tc::fence_after_sync();
             const uint32_t d = tmem + (uint32_t)(g * NACC);
             if (g < NGROUPS - 1) {
@@ -222,7 +223,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           for (int i = 0; i < S; ++i) tc::mma_commit(&sm.empty_a[stage[i]]);
         } else {
           for (int i = 0; i < S; ++i) {
-            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5)) { ok = false; break; }
+            if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5, gb.wait_ns)) { ok = false; break; }
             tc::fence_after_sync();
             // descriptors: start addresses differ only in bits 0-13, so they are formed once and
             // advanced by adding (byte offset >> 4)
@@ -283,7 +284,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const bool mvalid = m < N;
       const int ea = mvalid ? __ldg(P.expA + (long long)q * N + m) : 0;
       float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
-      if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6)) break;
+      if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + half * HALF;
@@ -420,6 +421,13 @@ int nspt_make_slice_map(CUtensorMap* map, const void* base, int N, int Kp, int P
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? NSPT_OK : NSPT_ERR_CUDA;
 }
+
+namespace {
+std::atomic<long long> g_wait_budget{(long long)WAIT_LIMIT_NS};
+}  // namespace
+
+long long nspt_split_wait_budget() { return g_wait_budget.load(); }
+void nspt_split_set_wait_budget(long long ns) { g_wait_budget.store(ns); }
 
 int nspt_split_gemm_init() {
   if (!g_encode) {

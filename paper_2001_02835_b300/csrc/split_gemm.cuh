@@ -25,3 +25,6 @@ int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int 
 // variant with the left operand in tensor memory (tile 128 x 40), selected by bn = 40
 int nspt_split_gemm_ta_init();
 int nspt_split_gemm_ta_batch(const SplitGemmArgs* a, int count, int S, int num_sms, cudaStream_t st);
+// budget of the tensor GEMMs' abortable waits (ns; < 0: give up at once)
+long long nspt_split_wait_budget();
+void nspt_split_set_wait_budget(long long ns);

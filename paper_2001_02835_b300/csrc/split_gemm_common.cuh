@@ -37,17 +37,26 @@ struct GemmBatch {
   GemmProblem p[MAXP];
   int count;
   long long total_tiles;
+  long long wait_ns;  // budget of the abortable device-side waits
 };
 
+// limit_ns: budget of this wait; the waits that may abandon the tile loop take the launch's
+// budget (GemmBatch::wait_ns, < 0: give up at once, a test hook), the final drains of copies and
+// MMAs already in flight always take WAIT_LIMIT_NS
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                         int code) {
+                                         int code, long long limit_ns = (long long)WAIT_LIMIT_NS) {
+  if (limit_ns < 0) {
+    *abort_flag = 1;
+    atomicCAS(err, 0, code);
+    return false;
+  }
   if (tc::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = tc::globaltimer();
   uint32_t n = 0;
   while (!tc::mbar_try_wait(bar, parity)) {
     if ((++n & 255) == 0) {
       if (*abort_flag) return false;
-      if (tc::globaltimer() - t0 > WAIT_LIMIT_NS) {
+      if (tc::globaltimer() - t0 > (uint64_t)limit_ns) {
         *abort_flag = 1;
         atomicCAS(err, 0, code);
         return false;
@@ -114,6 +123,7 @@ int build_batch(GemmBatch<MAXP>* gb, const SplitGemmArgs* a, int count, int S, i
   }
   gb->count = count;
   gb->total_tiles = tiles;
+  gb->wait_ns = nspt_split_wait_budget();
   return 0;
 }
 

@@ -95,14 +95,14 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int nK = (P.N + KB - 1) / KB;
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
-        if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1)) { ok = false; break; }
+        if (!wait_bar(&sm.empty_b[ib], pb ^ 1, &sm.abort_flag, err, 1, gb.wait_ns)) { ok = false; break; }
         tc::mbar_arrive_expect_tx(&sm.full_b[ib], S * 3 * B_TILE_T);
         tc::tma_load_4d(sm.b[ib][0][0], &P.mB, &sm.full_b[ib], kb * KB, n0, 0, q * S);  // [S][3][BN][32]
         issued_b[ib] = true;
         last_b_parity[ib] = pb;
         if (++ib == 2) { ib = 0; pb ^= 1; }
         for (int i = 0; i < S; ++i) {
-          if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2)) { ok = false; break; }
+          if (!wait_bar(&sm.empty_a[ia], pa ^ 1, &sm.abort_flag, err, 2, gb.wait_ns)) { ok = false; break; }
           tc::mbar_arrive_expect_tx(&sm.full_a[ia], 2 * A_TILE);
           tc::tma_load_4d(sm.a[ia][0], &P.mA, &sm.full_a[ia], kb * KB, m0, 0, q * S + i);  // [2][BM][32]
           issued_a[ia] = true;
@@ -130,17 +130,17 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int Nk = gb.p[pi].N;
       const int nK = (Nk + KB - 1) / KB;
       if (local > 0) {
-        if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3)) break;
+        if (!wait_bar(&sm.acc_empty, pacc ^ 1, &sm.abort_flag, err, 3, gb.wait_ns)) break;
       }
       tc::fence_after_sync();
       bool ok = true;
       for (int kb = 0; kb < nK && ok; ++kb) {
-        if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4)) { ok = false; break; }
+        if (!wait_bar(&sm.full_b[ib], pb, &sm.abort_flag, err, 4, gb.wait_ns)) { ok = false; break; }
         tc::fence_after_sync();
         const bool two_k = (Nk - kb * KB) > 16;
         const uint64_t b_0 = tc::desc_sw64(tc::smem_u32(sm.b[ib][0][0]));
         for (int i = 0; i < S; ++i) {
-          if (!wait_bar(&sm.ta_full[is], ps, &sm.abort_flag, err, 5)) { ok = false; break; }
+          if (!wait_bar(&sm.ta_full[is], ps, &sm.abort_flag, err, 5, gb.wait_ns)) { ok = false; break; }
           tc::fence_after_sync();
           const uint32_t a_re = tmem + ASLOT0 + (uint32_t)(2 * is) * 16;
           const uint32_t a_im = a_re + 16;
@@ -195,7 +195,7 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       // ---- A slices of this tile into TMEM ----
       for (int kb = 0; kb < nK && ok; ++kb) {
         for (int i = 0; i < S; ++i) {
-          if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 9)) { ok = false; break; }
+          if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 9, gb.wait_ns)) { ok = false; break; }
           // row `row` of the 64-byte-swizzled tile: 16-byte chunk c sits at chunk c ^ ((row >> 1) & 3)
           const uint8_t* src = sm.a[ia][part] + row * 64;
           uint32_t v[16];
@@ -207,7 +207,7 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&sm.empty_a[ia]);  // shared-memory stage read
           if (++ia == NA_STAGES) { ia = 0; pa ^= 1; }
-          if (!wait_bar(&sm.ta_empty[is], ps ^ 1, &sm.abort_flag, err, 10)) { ok = false; break; }
+          if (!wait_bar(&sm.ta_empty[is], ps ^ 1, &sm.abort_flag, err, 10, gb.wait_ns)) { ok = false; break; }
           tc::fence_after_sync();
           tc::tmem_st16(lane_base + ASLOT0 + (uint32_t)(2 * is + part) * 16, v);
           tc::tmem_wait_st();
@@ -234,7 +234,7 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const bool mvalid = m < N;
       const int ea = mvalid ? __ldg(P.expA + (long long)q * N + m) : 0;
       float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
-      if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6)) break;
+      if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();
 #pragma unroll 1
