@@ -1,4 +1,5 @@
-// Launch counting and per-stage CUDA-event timing of the library's kernels.
+// Launch counting, per-stage CUDA-event timing and NVTX ranges of the library's
+// kernels.
 //
 // Every kernel launch of the library goes through a ProfScope, which counts
 // it and, while profiling is on, records a CUDA event pair around it on the
@@ -8,6 +9,8 @@
 #include <atomic>
 #include <mutex>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "prof.cuh"
@@ -26,6 +29,8 @@ const char* kNames[NSPT_STAGE_COUNT] = {"fft_fwd", "slice",   "gemm_mode", "fft_
 
 ProfScope::ProfScope(int stage, cudaStream_t st, int nlaunch) : idx_(-1), st_(st) {
   g_launches.fetch_add(nlaunch, std::memory_order_relaxed);
+  // a named range for timeline tools (no cost beyond a check when none is attached)
+  nvtxRangePushA((stage >= 0 && stage < NSPT_STAGE_COUNT) ? kNames[stage] : "nspt");
   if (!g_on) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (g_n >= g_cap) return;
@@ -36,6 +41,7 @@ ProfScope::ProfScope(int stage, cudaStream_t st, int nlaunch) : idx_(-1), st_(st
 
 ProfScope::~ProfScope() {
   if (idx_ >= 0) cudaEventRecord(g_ev[2 * idx_ + 1], st_);
+  nvtxRangePop();
 }
 
 extern "C" {
