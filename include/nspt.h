@@ -270,10 +270,11 @@ NSPT_API int nspt_device_status(const nspt_opts* opts, void* stream);
 /*
  * Test hook (no counterpart in the paper): budget in ns of the tensor-core
  * GEMMs' device-side waits that may abandon a launch (default 2 s); applies to
- * launches enqueued afterwards.  A negative budget makes every such wait give
- * up at once, so that the launch exits cleanly -- the copies and MMAs already
- * in flight are still drained -- and nspt_device_status reports
- * NSPT_ERR_TIMEOUT: the timeout path can be exercised without a hung GPU.
+ * launches enqueued afterwards.  With a negative budget such a wait gives up
+ * as soon as its barrier is not ready at the first try, so that the launch
+ * exits cleanly -- the copies and MMAs already in flight are still drained --
+ * and nspt_device_status reports NSPT_ERR_TIMEOUT: the timeout path can be
+ * exercised without a hung GPU.
  * Results of a launch that gave up are undefined.
  */
 NSPT_API int nspt_debug_wait_budget(long long ns);

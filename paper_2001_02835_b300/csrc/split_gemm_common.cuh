@@ -41,16 +41,16 @@ struct GemmBatch {
 };
 
 // limit_ns: budget of this wait; the waits that may abandon the tile loop take the launch's
-// budget (GemmBatch::wait_ns, < 0: give up at once, a test hook), the final drains of copies and
-// MMAs already in flight always take WAIT_LIMIT_NS
+// budget (GemmBatch::wait_ns; < 0, a test hook: give up as soon as the barrier is not ready at the
+// first try), the final drains of copies and MMAs already in flight always take WAIT_LIMIT_NS
 __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
                                          int code, long long limit_ns = (long long)WAIT_LIMIT_NS) {
+  if (tc::mbar_try_wait(bar, parity)) return true;
   if (limit_ns < 0) {
     *abort_flag = 1;
     atomicCAS(err, 0, code);
     return false;
   }
-  if (tc::mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = tc::globaltimer();
   uint32_t n = 0;
   while (!tc::mbar_try_wait(bar, parity)) {
