@@ -41,7 +41,7 @@ def test_order_fft_and_ifft_match_direct_dft(nspt, N, T, M):
 
 @pytest.mark.parametrize("algo", ["naive", "fft"])
 @pytest.mark.parametrize("N,T,batch", [(1, 0, 1), (1, 5, 2), (2, 1, 3), (3, 2, 1), (9, 8, 4), (33, 7, 2),
-                                       (65, 3, 2), (130, 2, 1)])
+                                       (65, 3, 2), (130, 2, 1), (9, 100, 1), (6, 200, 1)])
 def test_mul_fp64_matches_oracle(nspt, algo, N, T, batch):
     g = syn.rng(2000 + N * 13 + T)
     A = syn.series_batch(g, N, T, batch)
