@@ -250,21 +250,14 @@ def fp64_peak_tflops(torch):
     return 2.0 * 4096 ** 3 / (best * 1e-3) / 1e12
 
 
-GROUP_N = (49, 121, 169, 225, 289)
-GROUP_T = (15, 31, 63)
-
-
 def grouped_leg(torch, nspt, barrier, count=64, reps=5):
     """64 independent products, N from {49,121,169,225,289}, T from {15,31,63} (seeded),
     split form, tile width from the autotuner, one CUDA graph replayed per step."""
-    g = syn.rng(syn.SEED_BASE + 3)
-    Ns = g.choice(GROUP_N, count)
-    Ts = g.choice(GROUP_T, count)
-    As, Bs = [], []
-    for N, T in zip(Ns, Ts):
-        A, B = inputs(int(N), int(T), 1, int(g.integers(1 << 30)))
-        As.append(torch.from_numpy(A).cuda())
-        Bs.append(torch.from_numpy(B).cuda())
+    pairs = syn.uneven_group(count)
+    As = [torch.from_numpy(A).cuda() for A, _ in pairs]
+    Bs = [torch.from_numpy(B).cuda() for _, B in pairs]
+    Ns = [A.shape[-1] for A, _ in pairs]
+    Ts = [A.shape[1] - 1 for A, _ in pairs]
     Cs = [torch.empty_like(A) for A in As]
     bn = nspt.autotune_grouped(As, Bs, cache_path=os.path.join(tempfile.gettempdir(), "nspt_tiles.txt"))
     nspt.polymat_mul_grouped(As, Bs, Cs, prec="split")

@@ -128,3 +128,22 @@ def integer_series(g: np.random.Generator, N: int, T: int, batch: int, lo: int =
     re = g.integers(lo, hi + 1, (batch, T + 1, N, N))
     im = g.integers(lo, hi + 1, (batch, T + 1, N, N))
     return (re + 1j * im).astype(np.complex128)
+
+
+GROUP_N = (49, 121, 169, 225, 289)
+GROUP_T = (15, 31, 63)
+
+
+def uneven_group(count: int = 64, seed: int = SEED_BASE + 3):
+    """The batched-uneven-products workload: `count` independent products with N drawn
+    from GROUP_N and T from GROUP_T, each a batch of one pair (A, B) of series as in
+    series_batch (Haar order 0, Gaussian orders >= 1), every pair from its own seed.
+    Returns a list of (A, B)."""
+    g = rng(seed)
+    Ns = g.choice(GROUP_N, count)
+    Ts = g.choice(GROUP_T, count)
+    out = []
+    for N, T in zip(Ns, Ts):
+        gp = rng(int(g.integers(1 << 30)))
+        out.append((series_batch(gp, int(N), int(T), 1), series_batch(gp, int(N), int(T), 1)))
+    return out
