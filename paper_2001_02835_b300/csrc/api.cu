@@ -1,9 +1,12 @@
 // C ABI, planner and orchestration of the NSPT polynomial-matrix library.
 //
 // Every entry point validates its arguments on the host, carves the caller's
-// workspace, and enqueues kernels on the caller's stream; nothing is allocated,
-// synchronised or read back.  The FFT-CONV orchestration follows Sec. 2
-// Steps 1-5; the Langevin step follows Eqs. 1-3 (see include/nspt.h).
+// workspace, and enqueues kernels on the caller's stream.  No device memory is
+// allocated; nothing is synchronised or read back except where a declaration
+// says so (the automatic per-order rescale, the tile autotuner, the status
+// read).  The host-buffer product creates its two copy streams and its events
+// once per device.  The FFT-CONV orchestration follows Sec. 2 Steps 1-5; the
+// Langevin step and the MD integrator follow Eqs. 1-3 (see include/nspt.h).
 #include <cmath>
 #include <cstdio>
 #include <cstring>

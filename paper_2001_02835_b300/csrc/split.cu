@@ -1,14 +1,18 @@
-// Split-precision product path: FP64 spectra -> BF16 digit slices -> tensor-core
-// mode GEMMs with exact FP32 digit groups -> double-float spectrum -> inverse
-// FFT in FP64 (Sec. 2 Steps 1-5 with Step 3 on the tensor cores).
+// Split-precision product path (Sec. 2 Steps 1-5 with Step 3 on the tensor
+// cores): FP64 series -> double-float spectra (fftdf.cu; the right operand's
+// spectra written transposed) -> BF16 digit slices -> tensor-core mode GEMMs
+// with exact FP32 digit groups -> double-float spectrum -> inverse transform
+// to FP64.  Also the backward, the grouped launch with its tile autotuner,
+// and the split-form Langevin step / MD phases.
 //
 // Slicing (an error-free split in the spirit of Ozaki et al.): each row r of
 // an operand gets e_r with |x| < 2^e_r for all of its real and imaginary
-// parts; x * 2^(W - e_r), W = 8S - 1, is rounded to an integer X <= 2^W read
-// straight from the FP64 bit pattern, and X is cut into S balanced base-256
-// digits d_0..d_{S-1} (|d_i| <= 128), so x = 2^(e_r - 7) sum_i d_i 2^(-8i) up to
-// 2^(e_r - W - 1).  Digit i is stored as the BF16 value d_i * 2^(-8i) (exact).
-// No FP64 arithmetic is used: on B300 the FP64 pipe is about 1/58 of FP32.
+// parts, and x 2^-e_r is cut into S balanced base-256 digits d_0..d_{S-1}
+// (|d_i| <= 128 for the leading digits), so x = 2^(e_r - 7) sum_i d_i 2^(-8i)
+// up to 2^(e_r - 8S); digit i is stored as the BF16 value d_i * 2^(-8i)
+// (exact).  The digits of FP64 values come from the bit pattern, those of
+// double-float values from FP32 rounding steps (digits.cuh); no FP64
+// arithmetic is used, since on B300 the FP64 pipe is about 1/58 of FP32.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
