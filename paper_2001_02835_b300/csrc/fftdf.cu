@@ -3,10 +3,13 @@
 //
 // Same structure as the FP64 transforms (fft64.cu): a CTA stages a strip of
 // EB consecutive entries of one batch element for all orders in shared memory
-// and runs radix-2 butterflies there -- decimation in frequency for the
-// forward transform (first stage pruned: the upper half of the zero-padded
-// input is zero), decimation in time for the inverse (last stage pruned to the
-// kept orders 0..T).  Arithmetic is double-float (about 48 significant bits),
+// and runs radix-2^2 butterflies there -- decimation in frequency for the
+// forward transform (first step pruned: the upper half of the zero-padded
+// input is zero; the body is in fftdf_core.cuh), decimation in time for the
+// inverse (last stage pruned to the kept orders 0..T).  Every thread requests
+// all of its inputs before the first butterfly.  The forward transform can
+// write the spectra transposed (blocks of 8 x EB/8 entries) for the right
+// operand of a product.  Arithmetic is double-float (about 48 significant bits),
 // so the FP64 pipe is used only for the final hi + lo of each output of the
 // inverse transform.  Spectra are float4 (re_hi, re_lo, im_hi, im_lo) per
 // entry, 16 bytes like complex128.  Twiddles (cos, sin) come from the same

@@ -22,13 +22,19 @@
 // 2^(e_A[m] + e_B[n] - 14) and writes float4 (re_hi, re_lo, im_hi, im_lo).
 //
 // Roles (one CTA per SM, persistent over tiles): warp 0 lanes 0 and 1 issue the
-// TMA loads of A and B, warp 1 lane 0 issues tcgen05.mma, warps 2-9 drain TMEM (two per lane
-// quarter, each half of the columns).  Per K block
-// of 32, all S slices of the B tile (re, im, -re) are loaded once and the A
-// slices stream through a 4-stage ring; the triangle of slice pairs
-// i + j < S is issued against the resident B slices.  Every wait is bounded
-// (globaltimer); on time-out the kernel records an error, drains its own TMA
-// and MMA work and frees TMEM.
+// TMA loads of A and B (4-D maps: one copy per A slice (re, im), one per B K
+// block with all its slices and planes), warp 1 lane 0 issues tcgen05.mma,
+// warps 2-9 drain TMEM (two per lane quarter, each half of the columns).  Per
+// K block of 32, all S slices of the B tile (re, im, -re) are loaded once and
+// the A slices stream through a ring (6 stages for S <= 6, else 4); the
+// triangle of slice pairs i + j < S is issued against the resident B slices.
+// With S <= 6 the epilogue frees the digit groups one at a time and the first
+// K block of the next tile issues its pairs group by group, so the TMEM drain
+// overlaps the MMAs (all 480 accumulator columns are in use, so the
+// accumulators cannot be double-buffered).  Every wait is bounded
+// (globaltimer; the budget of the abortable waits is a launch parameter); on
+// time-out the kernel records an error, drains its own TMA and MMA work and
+// frees TMEM.
 #include "common.cuh"
 #include "prof.cuh"
 #include "split_gemm.cuh"

@@ -1,4 +1,6 @@
-// Elementwise kernels of the TEK Langevin step (Eqs. 2-3 in rescaled time).
+// Elementwise kernels of the TEK Langevin step and MD integrator (Eqs. 2-3 in
+// rescaled time), of exp_star by Paterson-Stockmeyer (block combination), and
+// of the Wilson-loop measurement (trace of the last product as a correlation).
 //
 // From the staple series S_mu (Eq. 3, plus sign on the second term) of every
 // link of every stream:
