@@ -10,6 +10,14 @@ inputs (2 x 207 MB) and the spectra exceed the 126 MB L2, so no flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The end-to-end figure (`e2e`) is the same metric through nspt_polymat_mul_host
+with pinned host buffers: every step copies A and B in and C out inside the
+timed region (the copies of one batch element overlap the product of the next).
+Unless --no-extras, the line also carries comparison legs: the FP64 form, the
+O(g^31) timing point, the naive form, the backward, 64 uneven products in one
+graph-captured launch, the Langevin step at SU(121), a 40-step MD trajectory at
+SU(225), O(g^31) with its force / link-update split, and its Wilson loops.
+
 Under torchrun (N > 1) every rank runs an independent replica on its own batch
 (weak scaling; the products are independent, no data-path collective); rank 0
 prints the JSON line with the max-over-ranks time.  `--impl reference` times the
@@ -57,7 +65,7 @@ def parse():
     ap.add_argument("--prec", choices=["split", "fp64"], default=None)
     ap.add_argument("--T", type=int, default=T_DEF)
     ap.add_argument("--N", type=int, default=N_DEF)
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64/T=31 comparison legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparison legs (FP64, T=31, MD, ...)")
     return ap.parse_args()
 
 
