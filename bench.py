@@ -456,6 +456,17 @@ def run_ours(args):
             kw64 = dict(algo="fft", prec="fp64")
             ms64 = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kw64), 3, 1, barrier)
             extras["fp64_fft_T%d" % T] = {"products_per_s": BATCH * 3 / (ms64 * 1e-3), "ms_per_step": ms64 / 3}
+            # accuracy against speed: the split form with 5 and 6 slices, per-order relative error
+            # (Frobenius) against the FP64 form on the same inputs
+            ref64 = nspt.polymat_mul(dA, dB, algo="fft", prec="fp64")
+            den = torch.linalg.matrix_norm(ref64).clamp_min(1e-300)
+            for S in (5, 6):
+                kwS = dict(algo="fft", prec="split", slices=S)
+                msS = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kwS), 5, 1, barrier) / 5
+                err = (torch.linalg.matrix_norm(dC - ref64) / den).max().item()
+                extras["split_S%d_T%d" % (S, T)] = {"products_per_s": BATCH / (msS * 1e-3), "ms_per_step": msS,
+                                                    "max_per_order_rel_err_vs_fp64": err}
+            del ref64, den
         A31, B31 = inputs(N, 31, BATCH, syn.SEED_BASE + 1)
         a31, b31 = torch.from_numpy(A31).cuda(), torch.from_numpy(B31).cuda()
         c31 = torch.empty_like(a31)
