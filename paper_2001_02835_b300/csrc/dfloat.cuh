@@ -37,6 +37,21 @@ __device__ __forceinline__ dfl df_sub(dfl a, dfl b) { return df_add(a, df_neg(b)
 __device__ __forceinline__ dfl df_scale(dfl a, float p2) { return dfl{a.h * p2, a.l * p2}; }
 
 __device__ __forceinline__ cdf cdf_add(cdf a, cdf b) { return cdf{df_add(a.re, b.re), df_add(a.im, b.im)}; }
+
+// Sum whose result is only fed to another df_add: the exact TwoSum of the high
+// parts is kept, but the final FastTwoSum renormalisation is skipped (|lo| may
+// then exceed ulp(hi)/2 by a few units; the next df_add renormalises).
+__device__ __forceinline__ dfl df_add_lazy(dfl a, dfl b) {
+  float s, e;
+  df_two_sum(a.h, b.h, s, e);
+  return dfl{s, e + (a.l + b.l)};
+}
+__device__ __forceinline__ cdf cdf_add_lazy(cdf a, cdf b) {
+  return cdf{df_add_lazy(a.re, b.re), df_add_lazy(a.im, b.im)};
+}
+__device__ __forceinline__ cdf cdf_sub_lazy(cdf a, cdf b) {
+  return cdf{df_add_lazy(a.re, dfl{-b.re.h, -b.re.l}), df_add_lazy(a.im, dfl{-b.im.h, -b.im.l})};
+}
 __device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
 
 // a * w with w = (c, s) given as double-float pairs (a twiddle factor)

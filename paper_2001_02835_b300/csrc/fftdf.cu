@@ -122,7 +122,9 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
         tw(n * tstep, M, true, cw, sw);     c = cdf_mul(c, cw, sw);
         tw(3 * n * tstep, M, true, cw, sw); d = cdf_mul(d, cw, sw);
       }
-      const cdf apb = cdf_add(a, bq), amb = cdf_sub(a, bq), cpd = cdf_add(c, d), cmd = cdf_sub(c, d);
+      // first-layer sums feed only the second layer, which renormalises
+      const cdf apb = cdf_add_lazy(a, bq), amb = cdf_sub_lazy(a, bq);
+      const cdf cpd = cdf_add_lazy(c, d), cmd = cdf_sub_lazy(c, d);
       const cdf mi = cdf{cmd.im, df_neg(cmd.re)};  // (-i)(c - d)
       st(&sm[base * EB + e], cdf_add(apb, cpd));
       st(&sm[(base + h) * EB + e], cdf_add(amb, mi));

@@ -102,7 +102,9 @@ __device__ __forceinline__ void fwd_to_smem(float4* sm, const double2* __restric
       const int base = g * 2 * h + n;
       const cdf x0 = ld(&sm[base * EB + e]), x1 = ld(&sm[(base + q4) * EB + e]);
       const cdf x2 = ld(&sm[(base + 2 * q4) * EB + e]), x3 = ld(&sm[(base + 3 * q4) * EB + e]);
-      const cdf s0 = cdf_add(x0, x2), s1 = cdf_add(x1, x3), d0 = cdf_sub(x0, x2), d1 = cdf_sub(x1, x3);
+      // first-layer sums feed only the second layer, which renormalises
+      const cdf s0 = cdf_add_lazy(x0, x2), s1 = cdf_add_lazy(x1, x3);
+      const cdf d0 = cdf_sub_lazy(x0, x2), d1 = cdf_sub_lazy(x1, x3);
       const cdf id1 = cdf{df_neg(d1.im), d1.re};
       cdf o0 = cdf_add(s0, s1), o1 = cdf_sub(s0, s1), o2 = cdf_add(d0, id1), o3 = cdf_sub(d0, id1);
       if (n != 0) {
