@@ -165,7 +165,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
       tw(k, M, true, c, s);
       v = cdf_mul(v, c, s);
     }
-    cdf r = cdf_add(u, v);
+    cdf r = cdf_add_lazy(u, v);  // converted to FP64 as hi + lo, exact either way
     float f1, f2;
     pow2_pair(log2u - k * log2r - LOGM, f1, f2);
     r = cdf{df_scale(df_scale(r.re, f1), f2), df_scale(df_scale(r.im, f1), f2)};
