@@ -54,8 +54,11 @@ __device__ __forceinline__ cdf cdf_sub_lazy(cdf a, cdf b) {
 }
 __device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
 
-// a * w with w = (c, s) given as double-float pairs (a twiddle factor)
-__device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
+// a * w with w = (c, s) given as double-float pairs (a twiddle factor), without
+// the final renormalisation: (hi, lo) is the exact sum of the high products
+// plus the rounded residuals and cross terms, so |lo| may exceed ulp(hi)/2 when
+// the high products cancel.  For results that only feed further sums.
+__device__ __forceinline__ cdf cdf_mul_lazy(cdf a, dfl c, dfl s) {
   // re = a.re c - a.im s
   float p1 = a.re.h * c.h, e1 = fmaf(a.re.h, c.h, -p1);
   float p2 = a.im.h * s.h, e2 = fmaf(a.im.h, s.h, -p2);
@@ -66,7 +69,6 @@ __device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
   lo = fmaf(a.re.l, c.h, lo);
   lo = fmaf(-a.im.h, s.l, lo);
   lo = fmaf(-a.im.l, s.h, lo);
-  const dfl re = df_fast(sr, lo);
   // im = a.re s + a.im c
   float q1 = a.re.h * s.h, f1 = fmaf(a.re.h, s.h, -q1);
   float q2 = a.im.h * c.h, f2 = fmaf(a.im.h, c.h, -q2);
@@ -77,7 +79,11 @@ __device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
   lo2 = fmaf(a.re.l, s.h, lo2);
   lo2 = fmaf(a.im.h, c.l, lo2);
   lo2 = fmaf(a.im.l, c.h, lo2);
-  return cdf{re, df_fast(si, lo2)};
+  return cdf{dfl{sr, lo}, dfl{si, lo2}};
+}
+__device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
+  const cdf r = cdf_mul_lazy(a, c, s);
+  return cdf{df_fast(r.re.h, r.re.l), df_fast(r.im.h, r.im.l)};
 }
 
 // 2^k as a float for -252 <= k <= 254 (two factors keep it exact)

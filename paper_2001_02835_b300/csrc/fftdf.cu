@@ -118,9 +118,9 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
       cdf c = ld(&sm[(base + 2 * h) * EB + e]), d = ld(&sm[(base + 3 * h) * EB + e]);
       if (n != 0) {
         dfl cw, sw;
-        tw(2 * n * tstep, M, true, cw, sw); bq = cdf_mul(bq, cw, sw);
-        tw(n * tstep, M, true, cw, sw);     c = cdf_mul(c, cw, sw);
-        tw(3 * n * tstep, M, true, cw, sw); d = cdf_mul(d, cw, sw);
+        tw(2 * n * tstep, M, true, cw, sw); bq = cdf_mul_lazy(bq, cw, sw);
+        tw(n * tstep, M, true, cw, sw);     c = cdf_mul_lazy(c, cw, sw);
+        tw(3 * n * tstep, M, true, cw, sw); d = cdf_mul_lazy(d, cw, sw);
       }
       // first-layer sums feed only the second layer, which renormalises
       const cdf apb = cdf_add_lazy(a, bq), amb = cdf_sub_lazy(a, bq);
@@ -143,7 +143,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
       if (j != 0) {
         dfl c, s;
         tw(j * tstep, M, true, c, s);
-        v = cdf_mul(v, c, s);
+        v = cdf_mul_lazy(v, c, s);
       }
       st(&sm[i0 * EB + e], cdf_add(u, v));
       st(&sm[i1 * EB + e], cdf_sub(u, v));
@@ -163,7 +163,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
     if (k != 0) {
       dfl c, s;
       tw(k, M, true, c, s);
-      v = cdf_mul(v, c, s);
+      v = cdf_mul_lazy(v, c, s);
     }
     cdf r = cdf_add_lazy(u, v);  // converted to FP64 as hi + lo, exact either way
     float f1, f2;

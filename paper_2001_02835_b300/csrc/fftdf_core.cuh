@@ -72,9 +72,9 @@ __device__ __forceinline__ void fwd_to_smem(float4* sm, const double2* __restric
       cdf o0 = cdf_add(x0, x1), o1 = cdf_sub(x0, x1), o2 = cdf_add(x0, ix1), o3 = cdf_sub(x0, ix1);
       if (n != 0) {
         dfl c, s;
-        tw(2 * n, M, false, c, s); o1 = cdf_mul(o1, c, s);
-        tw(n, M, false, c, s);     o2 = cdf_mul(o2, c, s);
-        tw(3 * n, M, false, c, s); o3 = cdf_mul(o3, c, s);
+        tw(2 * n, M, false, c, s); o1 = cdf_mul_lazy(o1, c, s);
+        tw(n, M, false, c, s);     o2 = cdf_mul_lazy(o2, c, s);
+        tw(3 * n, M, false, c, s); o3 = cdf_mul_lazy(o3, c, s);
       }
       st(&sm[n * EB + e], o0);
       st(&sm[(n + M / 4) * EB + e], o1);
@@ -109,9 +109,9 @@ __device__ __forceinline__ void fwd_to_smem(float4* sm, const double2* __restric
       cdf o0 = cdf_add(s0, s1), o1 = cdf_sub(s0, s1), o2 = cdf_add(d0, id1), o3 = cdf_sub(d0, id1);
       if (n != 0) {
         dfl c, s;
-        tw(2 * n * tstep, M, false, c, s); o1 = cdf_mul(o1, c, s);
-        tw(n * tstep, M, false, c, s);     o2 = cdf_mul(o2, c, s);
-        tw(3 * n * tstep, M, false, c, s); o3 = cdf_mul(o3, c, s);
+        tw(2 * n * tstep, M, false, c, s); o1 = cdf_mul_lazy(o1, c, s);
+        tw(n * tstep, M, false, c, s);     o2 = cdf_mul_lazy(o2, c, s);
+        tw(3 * n * tstep, M, false, c, s); o3 = cdf_mul_lazy(o3, c, s);
       }
       st(&sm[base * EB + e], o0);
       st(&sm[(base + q4) * EB + e], o1);
