@@ -24,10 +24,17 @@
 // Roles (one CTA per SM, persistent over tiles): warp 0 lanes 0 and 1 issue the
 // TMA loads of A and B (4-D maps: one copy per A slice (re, im), one per B K
 // block with all its slices and planes), warp 1 lane 0 issues tcgen05.mma,
-// warps 2-9 drain TMEM (two per lane quarter, each half of the columns).  Per
-// K block of 32, all S slices of the B tile (re, im, -re) are loaded once and
-// the A slices stream through a ring (6 stages for S <= 6, else 4); the
-// triangle of slice pairs i + j < S is issued against the resident B slices.
+// warps 2-9 drain TMEM (two per lane quarter: for a plain product one sums the
+// real parts of the tile's columns and the other the imaginary parts, each
+// group read in two wide loads; with alpha or accumulation each takes half of
+// the columns, real and imaginary).  Per K block of 32, all S slices of the B
+// tile (re, im, -re) are loaded once and the A slices stream through a ring
+// (6 stages for S <= 6, else 4); the triangle of slice pairs i + j < S is
+// issued against the resident B slices, each A operand (slice, plane, K step)
+// against all its B slices in a row, so that the tensor core reads it from
+// shared memory once (collector fill / use / last use); the issuing loop is
+// unrolled over the slices, since every instruction between two MMAs of the
+// single issuing thread lengthens the MMA interval.
 // With S <= 6 the epilogue frees the digit groups one at a time and the first
 // K block of the next tile issues its pairs group by group, so the TMEM drain
 // overlaps the MMAs (all 480 accumulator columns are in use, so the
@@ -49,6 +56,19 @@
 namespace {
 
 using namespace sg;
+
+// the real (part 0) or imaginary (part 1) columns of one digit group's accumulator,
+// in loads of 32 and 16 columns that start at multiples of their width
+template <int BN>
+__device__ __forceinline__ void ld_part(uint32_t group_base, int part, float* v) {
+  static_assert(BN == 32 || BN == 48, "tile width");
+  if (BN == 48) {
+    if (part == 0) { tc::tmem_ld32(group_base, v); tc::tmem_ld16(group_base + 32, v + 32); }
+    else { tc::tmem_ld16(group_base + 48, v); tc::tmem_ld32(group_base + 64, v + 16); }
+  } else {
+    tc::tmem_ld32(group_base + (uint32_t)(part * 32), v);
+  }
+}
 
 // With S <= 6 slices the A ring holds every slice of a K block (6 stages, still
 // within shared memory next to the B tiles), so that the first K block of a
@@ -215,12 +235,29 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
 #pragma unroll
               for (int i = 0; i <= g; ++i) pair(dre[i], dim[i], g - i, d, i == 0);
             } else {
-              // merged group: every pair with i + j >= NGROUPS - 1, slice by slice
+              // merged group: every pair with i + j >= NGROUPS - 1, slice by slice, each A
+              // operand against its B slices in a row (collector reuse, as below)
 #pragma unroll
-              for (int i = 0; i < S; ++i)
+              for (int i = 0; i < S; ++i) {
+                const int j0 = NGROUPS - 1 - i > 0 ? NGROUPS - 1 - i : 0, nj = S - i - j0;
+                auto run = [&](uint64_t a, bool im, int ks) {
 #pragma unroll
-                for (int j = (NGROUPS - 1 - i > 0 ? NGROUPS - 1 - i : 0); j + i < S; ++j)
-                  pair(dre[i], dim[i], j, d, i == 0 && j == NGROUPS - 1);
+                  for (int jj = 0; jj < nj; ++jj) {
+                    const int j = j0 + jj;
+                    const uint64_t b = b_0 + (uint64_t)(j * 3 * (B_TILE >> 4)) + (im ? (B_TILE >> 4) : 0) + 2 * ks;
+                    const bool ow = i == 0 && j == NGROUPS - 1 && !im && ks == 0;
+                    const int coll = nj == 1 ? tc::COLL_DISCARD
+                                     : jj == 0 ? tc::COLL_FILL : (jj == nj - 1 ? tc::COLL_LASTUSE : tc::COLL_USE);
+                    tc::mma_f16_coll(coll, d, a, b, im ? IDN : ID, ow ? 0u : 1u);
+                  }
+                };
+                run(dre[i], false, 0);
+                run(dim[i], true, 0);
+                if (two_k) {
+                  run(dre[i] + 2, false, 1);
+                  run(dim[i] + 2, true, 1);
+                }
+              }
             }
           }
           if (!ok) break;
@@ -228,6 +265,10 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           // every slice of this K block has had its last pair
           for (int i = 0; i < S; ++i) tc::mma_commit(&sm.empty_a[stage[i]]);
         } else {
+          // unrolled over the slices: every loop bound, accumulator offset and collector use
+          // below is a compile-time constant, so the issuing thread spends no instructions
+          // on them between MMAs
+#pragma unroll
           for (int i = 0; i < S; ++i) {
             if (!wait_bar(&sm.full_a[ia], pa, &sm.abort_flag, err, 5, gb.wait_ns)) { ok = false; break; }
             tc::fence_after_sync();
@@ -238,11 +279,26 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
             // (without the group overlap) in the first K block of a tile, the first pair of each
             // group (i = 0, j = g for g < 4, and j = 4 for the merged group) overwrites it
             const bool first = (kb == 0) && (i == 0);
+            // slice i meets B slices j < S - i: the four A operands (re, -im) x (K step 0, 1)
+            // are each issued against all of them in a row, so that the tensor core reads
+            // each A operand from shared memory once (collector fill, use ..., last use)
+            const int nj = S - i;
+            auto run = [&](uint64_t a, bool im, int ks) {
 #pragma unroll
-            for (int j = 0; j < S; ++j) {
-              if (j + i >= S) break;
-              const int g = min(i + j, NGROUPS - 1);
-              pair(a_re, a_im, j, tmem + (uint32_t)(g * NACC), first && j < NGROUPS);
+              for (int j = 0; j < nj; ++j) {
+                const int g = min(i + j, NGROUPS - 1);
+                const uint64_t b = b_0 + (uint64_t)(j * 3 * (B_TILE >> 4)) + (im ? (B_TILE >> 4) : 0) + 2 * ks;
+                const bool ow = first && !im && ks == 0 && j < NGROUPS;
+                const int coll = nj == 1 ? tc::COLL_DISCARD
+                                 : j == 0 ? tc::COLL_FILL : (j == nj - 1 ? tc::COLL_LASTUSE : tc::COLL_USE);
+                tc::mma_f16_coll(coll, tmem + (uint32_t)(g * NACC), a, b, im ? IDN : ID, ow ? 0u : 1u);
+              }
+            };
+            run(a_re, false, 0);
+            run(a_im, true, 0);
+            if (two_k) {
+              run(a_re + 2, false, 1);
+              run(a_im + 2, true, 1);
             }
             any = true;
             tc::mma_commit(&sm.empty_a[ia]);
@@ -293,6 +349,49 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();
+      if (plain) {
+        // warps of half 0 sum the real parts of all BN columns, half 1 the imaginary parts:
+        // each group is read in two loads per warp
+        const uint32_t qbase = tmem + ((uint32_t)(quarter * 32) << 16);
+        const int nb = (r % tn) * BN;
+        float s_[BN], e_[BN];
+#pragma unroll
+        for (int g = 0; g < NGROUPS; ++g) {
+          float v[BN];
+          if (g < G) {
+            ld_part<BN>(qbase + (uint32_t)(g * NACC), half, v);
+            tc::tmem_wait_ld();
+            tc::fence_before_sync();
+            tc::mbar_arrive(&sm.acc_empty[g]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < BN; ++c) v[c] = 0.f;
+          }
+#pragma unroll
+          for (int c = 0; c < BN; ++c) {
+            if (g == 0) {
+              s_[c] = v[c]; e_[c] = 0.f;
+            } else if (g < NGROUPS - 1) {
+              float e1;
+              two_sum(s_[c], v[c], s_[c], e1);
+              e_[c] = (g == 1) ? e1 : e_[c] + e1;
+            } else {
+              e_[c] = e_[c] + v[c];
+            }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < BN; ++c) {
+          const int n = nb + c;
+          if (!mvalid || n >= N) continue;
+          const float h = s_[c] + e_[c], l = e_[c] - (h - s_[c]);
+          const int k = ea + __ldg(expB + n) - 14;
+          const int k1 = k / 2, k2 = k - k1;
+          const float f = pow2f(k1) * pow2f(k2);
+          reinterpret_cast<float2*>(crow + n)[half] = make_float2(h * f, l * f);
+        }
+        continue;
+      }
       const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + half * HALF;
       // digit groups one at a time, each released as soon as it is read, summed in
       // double-float in the order of df_sum: TwoSum chain over groups 0-3 into (s, e),

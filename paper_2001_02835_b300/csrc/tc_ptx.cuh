@@ -88,6 +88,29 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
       ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// Collector use of the A operand (the .collector::a qualifiers of tcgen05.mma):
+// FILL reads A from shared memory and keeps it in the tensor core's collector
+// buffer, USE reads it from there, LASTUSE reads it and releases the buffer,
+// DISCARD (the default) keeps nothing.  A run FILL, USE..., LASTUSE of MMAs
+// with one A descriptor reads that A tile from shared memory once.
+enum CollA { COLL_DISCARD = 0, COLL_FILL = 1, COLL_USE = 2, COLL_LASTUSE = 3 };
+#define NSPT_MMA_F16_COLL(Q)                                                   \
+  asm volatile(                                                                \
+      "{\n\t.reg .pred p;\n\t"                                                 \
+      "setp.ne.b32 p, %4, 0;\n\t"                                              \
+      "tcgen05.mma.cta_group::1.kind::f16" Q " [%0], %1, %2, %3, p;\n\t}"      \
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)       \
+      : "memory")
+__device__ __forceinline__ void mma_f16_coll(int coll, uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate) {
+  switch (coll) {
+    case COLL_FILL: NSPT_MMA_F16_COLL(".collector::a::fill"); break;
+    case COLL_USE: NSPT_MMA_F16_COLL(".collector::a::use"); break;
+    case COLL_LASTUSE: NSPT_MMA_F16_COLL(".collector::a::lastuse"); break;
+    default: NSPT_MMA_F16_COLL(""); break;
+  }
+}
+#undef NSPT_MMA_F16_COLL
 // D[tmem] (+)= A[tmem] * B[smem desc]^T, kind::f16: A's M = 128 rows in lanes 0-127,
 // two consecutive K elements packed per 32-bit column
 __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
@@ -113,6 +136,20 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+// 32 lanes x 32 columns of 32-bit accumulators
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 // 32 lanes x 16 columns of 32-bit accumulators: thread i of the warp gets lane (base lane + i)
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
