@@ -311,24 +311,32 @@ def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     """One MD trajectory of the paper's length (40 leapfrog steps, momentum refreshed at its
     start) of one SU(225) configuration at O(g^31) in the split form, with the time split
     into the force phase (drift plus momentum kicks) and the link-update phase, and the
-    measurement of its Wilson loops up to 2 x 2."""
+    measurement of its Wilson loops up to 2 x 2.  The configuration starts at the twisted
+    vacuum and is thermalised by one untimed trajectory; the timed trajectory follows it
+    with fresh momenta."""
     g = syn.rng(syn.SEED_BASE + 5)
     N = L * L
-    tU = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, flux, T, 1))).cuda()
-    tE = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, N, 4).reshape(1, 4, N, N))).cuda()
+    tU = torch.from_numpy(np.ascontiguousarray(syn.vacuum_links(L, flux, T, 1))).cuda()
+    tE0 = torch.from_numpy(np.ascontiguousarray(syn.md_momenta(g, N, 1))).cuda()
+    tE = torch.from_numpy(np.ascontiguousarray(syn.md_momenta(g, N, 1))).cuda()
     tP = torch.zeros_like(tU)
-    nspt.tek_md_trajectory(tU, tP, flux, eps, 2, eta=tE, algo="fft", prec="split")   # warm-up
+    kw = dict(algo="fft", prec="split", rescale_log2r=nspt.RESCALE_AUTO)   # orders decay from the vacuum
+    nspt.tek_md_trajectory(tU, tP, flux, eps, nsteps, eta=tE0, **kw)   # thermalisation
     nspt.profile_begin(200000)
-    ms = time_steps(torch, lambda: nspt.tek_md_trajectory(tU, tP, flux, eps, nsteps, eta=tE, algo="fft",
-                                                          prec="split"), 1, 0, barrier)
+    ms = time_steps(torch, lambda: nspt.tek_md_trajectory(tU, tP, flux, eps, nsteps, eta=tE, **kw), 1, 0, barrier)
     ph = nspt.profile_end()
+    finite = bool(torch.isfinite(torch.view_as_real(tU)).all().item())
+    umax = [float(x) for x in tU.abs()[0].amax(dim=(0, 2, 3)).cpu()]
     msw = time_steps(torch, lambda: nspt.tek_wilson_loops(tU, flux, 2, algo="fft", prec="split"), 2, 1, barrier) / 2
     out = {"ms_per_trajectory": ms, "md_steps": nsteps, "ms_per_md_step": ms / nsteps,
            "wilson_loops_amax2_ms": msw,
            "force_ms": ph.get("md_force", (0.0, 0))[0], "link_update_ms": ph.get("md_link", (0.0, 0))[0],
            "kernel_stages_ms": {k: v[0] for k, v in ph.items() if k not in ("md_force", "md_link")},
-           "note": "one configuration (4 links), split form; 10 trajectories = 10 x ms_per_trajectory"}
-    del tU, tE, tP
+           "links_finite": finite, "max_abs_link_order_0_8_16_24_31": [umax[k] for k in (0, 8, 16, 24, T)],
+           "note": "one configuration (4 links) from the twisted vacuum after one thermalising trajectory, "
+                   "momenta of variance 1/N, split form with the per-order rescale fitted at every phase; "
+                   "10 trajectories = 10 x ms_per_trajectory"}
+    del tU, tE, tE0, tP
     return out
 
 

@@ -74,13 +74,21 @@ typedef struct nspt_opts {
                           >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
   int complex_mode;    /* split form: 4 (four real products per complex product); 0 = 4 */
-  int rescale_log2r;   /* split form: per-order rescale A_k, B_k -> r^k A_k, r^k B_k with
-                          r = 2^rescale_log2r, undone exactly on C (not part of the paper);
-                          NSPT_RESCALE_AUTO (nspt_polymat_mul only): r = 2^round(-sigma/2)
-                          with sigma the least-squares slope over k of
-                          log2 max|A_k| + log2 max|B_k| -- this reads per-order maxima
-                          back and synchronises the stream, so never inside graph
-                          capture; default 0 */
+  int rescale_log2r;   /* per-order rescale A_k, B_k -> r^k A_k, r^k B_k with r = 2^rescale_log2r,
+                          undone exactly on C (not part of the paper): split form of the
+                          products; split and FP64 FFT forms of nspt_tek_langevin_step and
+                          nspt_tek_md_trajectory, where it applies to every order transform
+                          of the step (the map X_k -> r^k X_k commutes with every product and
+                          sum of the step, so the result is the same in exact arithmetic and
+                          small high orders keep their relative precision).
+                          NSPT_RESCALE_AUTO: the integer log2r (|log2r| <= 60, smallest among
+                          equals) minimising the spread over the nonzero orders k of
+                          y_k + 2 k log2r, y_k = log2 max|A_k| + log2 max|B_k| (the worst
+                          order's relative error grows with that spread; a geometric decay
+                          is flattened); TEK step: A = B = U; MD link update: A = U,
+                          B = i eps P; refitted at every step or phase -- this reads
+                          per-order maxima back and synchronises the stream, so never inside
+                          graph capture; default 0 */
   void* workspace;     /* device scratch, >= nspt_workspace_size() bytes */
   size_t workspace_bytes;
 } nspt_opts;

@@ -123,6 +123,23 @@ def link_series(g: np.random.Generator, L: int, flux: int, T: int, streams: int)
     return U
 
 
+def vacuum_links(L: int, flux: int, T: int, streams: int) -> np.ndarray:
+    """The twisted vacuum as a link series, shape (streams, 4, T+1, N, N): the twist eaters at
+    order 0, every higher order zero.  MD trajectories of the benchmark start here (the
+    Gaussian orders of link_series are not a unitary series, and under MD their unphysical
+    directions grow without bound at N >= 121)."""
+    N = L * L
+    U = np.zeros((streams, 4, T + 1, N, N), np.complex128)
+    U[:, :, 0] = twist_eaters(L, flux)[None]
+    return U
+
+
+def md_momenta(g: np.random.Generator, N: int, streams: int) -> np.ndarray:
+    """Order-1 momenta of an MD refresh, shape (streams, 4, N, N): traceless Hermitian Gaussian
+    with E|P_ij|^2 = 1/N, the 't Hooft normalisation matching the 1/N variance of the series."""
+    return hermitian_noise(g, N, 4 * streams).reshape(streams, 4, N, N) / np.sqrt(N)
+
+
 def integer_series(g: np.random.Generator, N: int, T: int, batch: int, lo: int = -8, hi: int = 8) -> np.ndarray:
     """Series with small integer real and imaginary parts (for bit-exact tests)."""
     re = g.integers(lo, hi + 1, (batch, T + 1, N, N))

@@ -184,7 +184,7 @@ int pair_index(int a, int b) {  // a < b
 }
 int ordered_index(int mu, int nu) { return mu * 3 + (nu < mu ? nu : nu - 1); }  // 0..11
 
-size_t ws_langevin(const Plan& p) {
+size_t ws_langevin_core(const Plan& p) {
   if (p.prec == NSPT_PREC_SPLIT) return nspt_split_ws_langevin(p.N, p.T, p.batch, p.M, p.slices);
   const long long E = p.E;
   const long long T1 = p.T + 1, M = p.M;
@@ -199,10 +199,24 @@ size_t ws_langevin(const Plan& p) {
   return (size_t)p.batch * mats * E * sizeof(double2) + (size_t)p.batch * 4 * T1 * sizeof(double) + 8 * 256;
 }
 
+// a TEK step's workspace: the pipeline's, then the scratch of the per-order rescale fit
+constexpr size_t kFitScratch = 2 * 513 * sizeof(int);
+size_t ws_langevin(const Plan& p) { return ((ws_langevin_core(p) + 255) & ~(size_t)255) + kFitScratch; }
+void* fit_scratch(const Plan& p, void* ws) { return (char*)ws + ((ws_langevin_core(p) + 255) & ~(size_t)255); }
+
+// exponent of the per-order rescale of a TEK step's order transforms (FFT forms only): fixed, or
+// with NSPT_RESCALE_AUTO fitted to the per-order maxima of A and B (synchronises the stream)
+int tek_log2r(const Plan& p, const double2* A, const double2* B, void* ws, cudaStream_t st, int* lr) {
+  *lr = 0;
+  if (p.algo != NSPT_ALGO_FFT) return NSPT_OK;
+  if (!p.rescale_auto) { *lr = p.log2r; return NSPT_OK; }
+  return nspt_split_fit_rescale(A, B, p.N, p.T, p.batch * 4, fit_scratch(p, ws), lr, st);
+}
+
 // mode: NSPT_LMODE_STEP (drift, increment, update), NSPT_LMODE_DRIFT (drift F only),
 // NSPT_LMODE_UPDATE (U <- exp_star(Yin) U with the caller's Yin = i X, X^(0) = 0)
 int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int flux, double eps, void* ws,
-                  cudaStream_t st, int mode = NSPT_LMODE_STEP, const double2* Yin = nullptr) {
+                  cudaStream_t st, int mode = NSPT_LMODE_STEP, const double2* Yin = nullptr, int lr = 0) {
   const int N = p.N, T = p.T, nb = p.batch;
   const long long E = p.E, T1 = T + 1;
   int L = (int)llround(sqrt((double)N));
@@ -231,7 +245,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     double* imtr = w.take<double>((size_t)nb * 4 * T1);
     const long long sm = (long long)M;  // matrices per spectrum
     // 1. spectra of the four links
-    TRY(nspt_fft_fwd64(U, T1, specU, (int)E, T, nb * 4, M, 0, 0, st));
+    TRY(nspt_fft_fwd64(U, T1, specU, (int)E, T, nb * 4, M, 0, lr, st));
     auto specOf = [&](double2* base, int slot) { return base + (long long)slot * M * E; };
     if (mode != NSPT_LMODE_UPDATE) {
     // 2. P1(mu,nu) = U_nu * U_mu^+ (mu<nu), Q(mu,nu) = U_mu * U_nu (mu != nu)
@@ -250,8 +264,8 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
         TRY(nspt_zgemm64(P, nb, st));
       }
     // truncate (Step 5) and return to the frequency domain
-    TRY(nspt_fft_inv64(specAcc, serTmp, T1, (int)E, N, T, nb * 18, M, 0, 0, 1.0, 0, st));
-    TRY(nspt_fft_fwd64(serTmp, T1, specPQ, (int)E, T, nb * 18, M, 0, 0, st));
+    TRY(nspt_fft_inv64(specAcc, serTmp, T1, (int)E, N, T, nb * 18, M, 0, lr, 1.0, 0, st));
+    TRY(nspt_fft_fwd64(serTmp, T1, specPQ, (int)E, T, nb * 18, M, 0, lr, st));
     // 3. inner_mu = sum_nu z P1(mu,nu) U_nu^+ + conj(z) P2(mu,nu) U_nu,  P2(mu,nu) = Q(mu,nu)^+
     for (int mu = 0; mu < 4; ++mu) {
       bool first = true;
@@ -279,15 +293,15 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
       }
     }
     // truncate inner_mu and return it to the frequency domain (in place in specIn)
-    TRY(nspt_fft_inv64(specIn, serTmp, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st));
-    TRY(nspt_fft_fwd64(serTmp, T1, specIn, (int)E, T, nb * 4, M, 0, 0, st));
+    TRY(nspt_fft_inv64(specIn, serTmp, T1, (int)E, N, T, nb * 4, M, 0, lr, 1.0, 0, st));
+    TRY(nspt_fft_fwd64(serTmp, T1, specIn, (int)E, T, nb * 4, M, 0, lr, st));
     // 4. S_mu = U_mu * inner_mu
     for (int mu = 0; mu < 4; ++mu) {
       ZgemmParams P = zg(ZG_MODE, specOf(specU, mu), 4 * sm, specOf(specIn, mu), 4 * sm, specOf(specAcc, mu), 4 * sm,
                          N, M, T);
       TRY(nspt_zgemm64(P, nb, st));
     }
-    TRY(nspt_fft_inv64(specAcc, serS, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st));
+    TRY(nspt_fft_inv64(specAcc, serS, T1, (int)E, N, T, nb * 4, M, 0, lr, 1.0, 0, st));
     // 5. drift and the Langevin increment Y = i X
     TRY(nspt_tek_drift(serS, imtr, eta, F, serY, N, T, (long long)nb * 4, eps, st));
     }
@@ -301,11 +315,11 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     // c^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
     auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
       const int Mt = next_pow2(2 * (t + 1));
-      TRY(nspt_fft_fwd64(a, T1, spY, (int)E, t, nb * 4, Mt, 0, 0, st));
-      TRY(nspt_fft_fwd64(b, T1, spR, (int)E, t, nb * 4, Mt, 0, 0, st));
+      TRY(nspt_fft_fwd64(a, T1, spY, (int)E, t, nb * 4, Mt, 0, lr, st));
+      TRY(nspt_fft_fwd64(b, T1, spR, (int)E, t, nb * 4, Mt, 0, lr, st));
       ZgemmParams P = zg(ZG_MODE, spY, Mt, spR, Mt, spC, Mt, N, Mt, t);
       TRY(nspt_zgemm64(P, nb * 4, st));
-      TRY(nspt_fft_inv64(spC, c, T1, (int)E, N, t, nb * 4, Mt, 0, 0, 1.0, 0, st));
+      TRY(nspt_fft_inv64(spC, c, T1, (int)E, N, t, nb * 4, Mt, 0, lr, 1.0, 0, st));
       return NSPT_OK;
     };
     const int sb = nspt_ps_block(T), r = T / sb;
@@ -339,10 +353,10 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     }
     // 7. U <- exp_star(i X) * U  (spectrum of the old U is still in specU);
     //    order 0 is exactly U^(0) since X^(0) = 0, so it is not rewritten
-    TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, T, nb * 4, M, 0, 0, st));
+    TRY(nspt_fft_fwd64(serR[cur], T1, spR, (int)E, T, nb * 4, M, 0, lr, st));
     ZgemmParams P = zg(ZG_MODE, spR, M, specU, M, spC, M, N, M, T);
     TRY(nspt_zgemm64(P, nb * 4, st));
-    TRY(nspt_fft_inv64(spC, U, T1, (int)E, N, T, nb * 4, M, 0, 0, 1.0, 0, st, /*kmin=*/1));
+    TRY(nspt_fft_inv64(spC, U, T1, (int)E, N, T, nb * 4, M, 0, lr, 1.0, 0, st, /*kmin=*/1));
     return NSPT_OK;
   }
   // ---------------- naive form ----------------
@@ -432,9 +446,13 @@ size_t ws_md(const Plan& p) {
 }
 
 int md_phase(const Plan& p, double2* U, double2* F, const double2* Y, int flux, void* lws, cudaStream_t st, int mode) {
+  int lr = 0;
+  // the force phase multiplies links only; the link update also powers of the increment Y
+  const int rc = tek_log2r(p, U, mode == NSPT_LMODE_UPDATE ? Y : U, lws, st, &lr);
+  if (rc) return rc;
   if (p.prec == NSPT_PREC_SPLIT)
-    return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, U, nullptr, F, flux, 0.0, lws, st, mode, Y);
-  return langevin_fp64(p, U, nullptr, F, flux, 0.0, lws, st, mode, Y);
+    return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, U, nullptr, F, flux, 0.0, lws, st, mode, Y, lr);
+  return langevin_fp64(p, U, nullptr, F, flux, 0.0, lws, st, mode, Y, lr);
 }
 
 int md_run(const Plan& p, double2* U, double2* P, const double2* eta, int flux, double eps, int nsteps, void* ws,
@@ -748,12 +766,16 @@ int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int 
     const void* ptrs[3] = {U, eta, F};
     if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
   }
+  int lr = 0;
+  if ((rc = tek_log2r(p, (const double2*)U, (const double2*)U, opts ? opts->workspace : nullptr, (cudaStream_t)stream,
+                      &lr)))
+    return rc;
   if (p.prec != NSPT_PREC_FP64) {
     return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, (double2*)U, (const double2*)eta, (double2*)F, flux,
-                               eps, opts->workspace, (cudaStream_t)stream);
+                               eps, opts->workspace, (cudaStream_t)stream, NSPT_LMODE_STEP, nullptr, lr);
   }
   return langevin_fp64(p, (double2*)U, (const double2*)eta, (double2*)F, flux, eps, opts ? opts->workspace : nullptr,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, NSPT_LMODE_STEP, nullptr, lr);
 }
 
 static int check_group(const nspt_polymat_desc* d, int count, const nspt_opts* o, Plan* first) {

@@ -378,21 +378,29 @@ int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int
   std::vector<int> h(2 * (T + 1));
   TRYC(cudaMemcpyAsync(h.data(), d, sizeof(int) * 2 * (T + 1), cudaMemcpyDeviceToHost, st));
   TRYC(cudaStreamSynchronize(st));
-  // exponent fields: log2 max|A_k| + log2 max|B_k| ~ (eA - 1023) + (eB - 1023)
-  double sx = 0, sy = 0, sxx = 0, sxy = 0;
-  int n = 0;
-  for (int k = 0; k <= T; ++k) {
-    if (h[k] == 0 || h[T + 1 + k] == 0) continue;
-    const double y = (double)(h[k] - 1023) + (double)(h[T + 1 + k] - 1023);
-    sx += k; sy += y; sxx += (double)k * k; sxy += k * y; ++n;
-  }
+  // exponent fields: y_k = log2 max|A_k| + log2 max|B_k| ~ (eA - 1023) + (eB - 1023).  The
+  // relative error of order k grows with max_j(y_j + 2 j log2r) - (y_k + 2 k log2r): take the
+  // log2r that minimises the spread of y_k + 2 k log2r over the nonzero orders (for a geometric
+  // decay this flattens it; for a faster, factorial one it balances the first and last orders),
+  // the smallest |log2r| among equals
+  std::vector<std::pair<int, double>> y;
+  for (int k = 0; k <= T; ++k)
+    if (h[k] != 0 && h[T + 1 + k] != 0) y.push_back({k, (double)(h[k] - 1023) + (double)(h[T + 1 + k] - 1023)});
   *log2r = 0;
-  if (n >= 2) {
-    const double den = n * sxx - sx * sx;
-    if (den > 0) {
-      const double sigma = (n * sxy - sx * sy) / den;
-      *log2r = (int)std::lround(-sigma / 2.0);
-      *log2r = std::max(-60, std::min(60, *log2r));
+  if (y.size() >= 2) {
+    double best = 1e300;
+    for (int a = 0; a <= 120; ++a) {
+      const int lr = (a % 2) ? (a + 1) / 2 : -(a / 2);  // 0, 1, -1, 2, -2, ...
+      double lo = 1e300, hi = -1e300;
+      for (const auto& kv : y) {
+        const double v = kv.second + 2.0 * kv.first * lr;
+        lo = std::min(lo, v);
+        hi = std::max(hi, v);
+      }
+      if (hi - lo < best - 1e-9) {
+        best = hi - lo;
+        *log2r = lr;
+      }
     }
   }
   return NSPT_OK;
@@ -661,7 +669,18 @@ struct LangevinWs {
   double* imtr;
   __nv_bfloat16 *slA[kMaxJobs], *slB[kMaxJobs];
   int *expA[kMaxJobs], *expB[kMaxJobs];
+  // slices of the link spectra, kept for a whole force evaluation: left operand U_x (lkA[x]),
+  // right operands U_x^+ (lkB[x]) and U_x (lkB[4 + x], from the transposed spectra)
+  __nv_bfloat16 *lkA[4], *lkB[8];
+  int *lkEA[4], *lkEB[8];
   size_t total;
+};
+
+// which link slices of a force evaluation are already made (host side, reset per call)
+struct LinkCache {
+  const LangevinWs* w;
+  long long specE, bs;
+  bool okA[4], okB[8];
 };
 
 LangevinWs carve_langevin(void* base, int N, int T, int nb, int M, int S) {
@@ -698,13 +717,37 @@ LangevinWs carve_langevin(void* base, int N, int T, int nb, int M, int S) {
     w.expA[j] = base ? poolEA + j * se : nullptr;
     w.expB[j] = base ? poolEB + j * se : nullptr;
   }
+  __nv_bfloat16* lkPoolA = c.take<__nv_bfloat16>(4 * sa);
+  __nv_bfloat16* lkPoolB = c.take<__nv_bfloat16>(8 * sb);
+  int* lkPoolEA = c.take<int>(4 * se);
+  int* lkPoolEB = c.take<int>(8 * se);
+  for (int x = 0; x < 8; ++x) {
+    if (x < 4) {
+      w.lkA[x] = base ? lkPoolA + x * sa : nullptr;
+      w.lkEA[x] = base ? lkPoolEA + x * se : nullptr;
+    }
+    w.lkB[x] = base ? lkPoolB + x * sb : nullptr;
+    w.lkEB[x] = base ? lkPoolEB + x * se : nullptr;
+  }
   w.total = c.off;
   return w;
 }
 
+// Link operand of a job: the index of its cached slices (left: x for U_x; right: x for U_x^+, 4 + x
+// for U_x from the transposed spectra), or -1
+int link_slot(const LinkCache* lc, const SpecRef& r, bool right) {
+  if (!lc || r.bs != lc->bs) return -1;
+  for (int x = 0; x < 4; ++x) {
+    if (!right && r.p == lc->w->specU + x * lc->specE && !r.dag && !r.tr) return x;
+    if (right && r.p == lc->w->specU + x * lc->specE && r.dag && !r.tr) return x;
+    if (right && r.p == lc->w->specUT + x * lc->specE && !r.dag && r.tr) return 4 + x;
+  }
+  return -1;
+}
+
 int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int M, int S, cudaStream_t st,
              __nv_bfloat16* slA_big = nullptr, __nv_bfloat16* slB_big = nullptr, int* eA_big = nullptr,
-             int* eB_big = nullptr) {
+             int* eB_big = nullptr, LinkCache* lc = nullptr) {
   std::vector<SplitGemmArgs> args;
   std::vector<std::pair<int, int>> sig;
   for (int j = 0; j < count; ++j) {
@@ -713,10 +756,17 @@ int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int
     __nv_bfloat16* sb = slB_big ? slB_big : w.slB[j];
     int* ea = eA_big ? eA_big : w.expA[j];
     int* eb = eB_big ? eB_big : w.expB[j];
+    // a link operand is sliced once per force evaluation and its slices reused
+    const int xa = link_slot(lc, J.a, false), xb = link_slot(lc, J.b, true);
+    bool slice_a = true, slice_b = true;
+    if (xa >= 0) { sa = w.lkA[xa]; ea = w.lkEA[xa]; slice_a = !lc->okA[xa]; lc->okA[xa] = true; }
+    if (xb >= 0) { sb = w.lkB[xb]; eb = w.lkEB[xb]; slice_b = !lc->okB[xb]; lc->okB[xb] = true; }
     // left operand: rows of A (dagger: conjugated columns of the reversed spectrum)
-    TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag ^ J.a.tr, J.a.dag, N, nb * M, 2, sa, ea, st));
+    if (slice_a)
+      TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag ^ J.a.tr, J.a.dag, N, nb * M, 2, sa, ea, st));
     // right operand: rows of B^T (dagger: conjugated rows of the reversed spectrum)
-    TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, (!J.b.dag) ^ J.b.tr, J.b.dag, N, nb * M, 3, sb, eb, st));
+    if (slice_b)
+      TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, (!J.b.dag) ^ J.b.tr, J.b.dag, N, nb * M, 3, sb, eb, st));
     SplitGemmArgs a;
     a.slicesA = sa; a.slicesB = sb; a.expA = ea; a.expB = eb; a.C = J.c;
     a.N = N; a.Kp = kpad(N); a.Q = nb * M; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
@@ -734,7 +784,7 @@ size_t nspt_split_ws_langevin(int N, int T, int nb, int M, int S) {
 }
 
 int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const double2* eta, double2* F, int flux,
-                        double eps, void* ws, cudaStream_t st, int mode, const double2* Yin) {
+                        double eps, void* ws, cudaStream_t st, int mode, const double2* Yin, int log2r) {
   const int E = N * N;
   const long long T1 = T + 1;
   const long long specE = (long long)M * E;  // one spectrum
@@ -749,12 +799,13 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // 1. spectra of the four links, [nb][4][M], and their transposes (right
   //    operands that are not daggered are sliced by rows of those)
-  if (mode != NSPT_LMODE_UPDATE) TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, 0, st));
-  TRYC(nspt_fft_fwd_df(U, T1, w.specUT, E, T, nb * 4, M, 0, 0, st, N));
+  if (mode != NSPT_LMODE_UPDATE) TRYC(nspt_fft_fwd_df(U, T1, w.specU, E, T, nb * 4, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd_df(U, T1, w.specUT, E, T, nb * 4, M, 0, log2r, st, N));
   auto link = [&](int mu, int dag) { return SpecRef{w.specU + mu * specE, 4LL * M, dag}; };
   auto linkT = [&](int mu) { return SpecRef{w.specUT + mu * specE, 4LL * M, 0, 1}; };
   auto slot = [&](float4* base, int s) { return base + (long long)s * nb * specE; };
   Job jobs[kMaxJobs];
+  LinkCache lc{&w, specE, 4LL * M, {}, {}};
   if (mode != NSPT_LMODE_UPDATE) {
   // 2. P1(mu,nu) = U_nu U_mu^+ (mu < nu) and Q(mu,nu) = U_mu U_nu: one launch of 18 products
   for (int i = 0; i < 6; ++i) {
@@ -766,10 +817,10 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
       if (mu != nu)
         jobs[6 + ord_idx(mu, nu)] = Job{link(mu, 0), linkT(nu), slot(w.specAcc, 6 + ord_idx(mu, nu)),
                                         make_double2(1, 0), 0, 0};
-  TRYS(run_jobs(w, jobs, 18, N, nb, M, S, st));
+  TRYS(run_jobs(w, jobs, 18, N, nb, M, S, st, nullptr, nullptr, nullptr, nullptr, &lc));
   // truncate (Step 5) and return to the frequency domain
-  TRYC(nspt_fft_inv_df(w.specAcc, w.serTmp, T1, E, T, 18 * nb, M, 0, 0, st));
-  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specPQ, E, T, 18 * nb, M, 0, 0, st));
+  TRYC(nspt_fft_inv_df(w.specAcc, w.serTmp, T1, E, T, 18 * nb, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specPQ, E, T, 18 * nb, M, 0, log2r, st));
   auto pq = [&](int s, int dag) { return SpecRef{slot(w.specPQ, s), (long long)M, dag}; };
   // 3. inner_mu = sum_nu z P1(mu,nu) U_nu^+ + conj(z) Q(mu,nu)^+ U_nu, six accumulating terms
   for (int tt = 0; tt < 6; ++tt) {
@@ -790,17 +841,17 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
       J.use_alpha = 1;
       J.accumulate = tt > 0;
     }
-    TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
+    TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st, nullptr, nullptr, nullptr, nullptr, &lc));
   }
-  TRYC(nspt_fft_inv_df(w.specIn, w.serTmp, T1, E, T, 4 * nb, M, 0, 0, st));
-  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specIn, E, T, 4 * nb, M, 0, 0, st, N));  // transposed
+  TRYC(nspt_fft_inv_df(w.specIn, w.serTmp, T1, E, T, 4 * nb, M, 0, log2r, st));
+  TRYC(nspt_fft_fwd_df(w.serTmp, T1, w.specIn, E, T, 4 * nb, M, 0, log2r, st, N));  // transposed
   // 4. S_mu = U_mu inner_mu
   for (int mu = 0; mu < 4; ++mu)
     jobs[mu] = Job{link(mu, 0), SpecRef{slot(w.specIn, mu), (long long)M, 0, 1}, slot(w.specAcc, mu),
                    make_double2(1, 0), 0, 0};
-  TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st));
+  TRYS(run_jobs(w, jobs, 4, N, nb, M, S, st, nullptr, nullptr, nullptr, nullptr, &lc));
   for (int mu = 0; mu < 4; ++mu)
-    TRYC(nspt_fft_inv_df(slot(w.specAcc, mu), w.serS + mu * T1 * E, 4 * T1, E, T, nb, M, 0, 0, st));
+    TRYC(nspt_fft_inv_df(slot(w.specAcc, mu), w.serS + mu * T1 * E, 4 * T1, E, T, nb, M, 0, log2r, st));
   // 5. drift and Y = i X
   TRYC(nspt_tek_drift(w.serS, w.imtr, eta, F, w.serY, N, T, (long long)nb * 4, eps, st));
   }
@@ -814,11 +865,11 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   // C^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
   auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
     const int Mt = nspt_pow2_at_least(2 * (t + 1));
-    TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, t, nb * 4, Mt, 0, 0, st));
-    TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, 0, st, N));  // transposed: sliced by rows
+    TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, t, nb * 4, Mt, 0, log2r, st));
+    TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, log2r, st, N));  // transposed: sliced by rows
     Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0, 1}, w.spC, make_double2(1, 0), 0, 0};
     TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
-    TRYC(nspt_fft_inv_df(w.spC, c, T1, E, t, nb * 4, Mt, 0, 0, st));
+    TRYC(nspt_fft_inv_df(w.spC, c, T1, E, t, nb * 4, Mt, 0, log2r, st));
     return NSPT_OK;
   };
   const int sb = nspt_ps_block(T), r = T / sb;
@@ -852,9 +903,9 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   }
   double2* const expY = Qs[cur];
   // 7. U <- exp_star(i X) U, order 0 untouched
-  TRYC(nspt_fft_fwd_df(expY, T1, w.spR, E, T, nb * 4, M, 0, 0, st));
+  TRYC(nspt_fft_fwd_df(expY, T1, w.spR, E, T, nb * 4, M, 0, log2r, st));
   Job J{SpecRef{w.spR, (long long)M, 0}, SpecRef{w.specUT, (long long)M, 0, 1}, w.spC, make_double2(1, 0), 0, 0};
   TRYS(run_jobs(w, &J, 1, N, nb * 4, M, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
-  TRYC(nspt_fft_inv_df(w.spC, U, T1, E, T, nb * 4, M, 0, 0, st, 1.0, 0, N, 1));
+  TRYC(nspt_fft_inv_df(w.spC, U, T1, E, T, nb * 4, M, 0, log2r, st, 1.0, 0, N, 1));
   return NSPT_OK;
 }

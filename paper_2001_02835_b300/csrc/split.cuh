@@ -12,9 +12,12 @@ int nspt_split_mul(int N, int T, int batch, int M, int slices, int log2r, bool r
                    const double2* B, double2* C, void* ws, cudaStream_t st);
 int nspt_split_bwd(int N, int T, int batch, int M, int slices, int log2r, const double2* A, const double2* B,
                    const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
-// mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE
+// mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE; log2r: every order transform of the
+// step scales order k by 2^(k log2r) and its inverse undoes it (exact, and the same result in exact
+// arithmetic: the ring map X_k -> r^k X_k commutes with every product and sum of the step)
 int nspt_split_langevin(int N, int T, int batch, int M, int slices, double2* U, const double2* eta, double2* F,
-                        int flux, double eps, void* ws, cudaStream_t st, int mode = 0, const double2* Yin = nullptr);
+                        int flux, double eps, void* ws, cudaStream_t st, int mode = 0, const double2* Yin = nullptr,
+                        int log2r = 0);
 // slices of Q planes of X (see slice_kernel): out bf16 [Q][S][2][N][Kp], exps [Q][N]
 int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
                      int P, void* out, int* exps, cudaStream_t st);
@@ -23,6 +26,11 @@ int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int re
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st);
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st);
+// least-squares fit of the per-order rescale exponent: log2r = round(-sigma/2), sigma the slope over k
+// of log2 max|A_k| + log2 max|B_k| (A, B: `batch` series [T+1][N][N]); scratch: 2 (T+1) ints of device
+// memory; reads the maxima back and synchronises `st`
+int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int batch, void* scratch, int* log2r,
+                           cudaStream_t st);
 size_t nspt_split_ws_grouped(const nspt_polymat_desc* d, int count, int S);
 int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log2r, void* ws, cudaStream_t st);
 int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,
