@@ -81,14 +81,16 @@ typedef struct nspt_opts {
                           of the step (the map X_k -> r^k X_k commutes with every product and
                           sum of the step, so the result is the same in exact arithmetic and
                           small high orders keep their relative precision).
-                          NSPT_RESCALE_AUTO: the integer log2r (|log2r| <= 60, smallest among
+                          NSPT_RESCALE_AUTO: the integer log2r (smallest |log2r| among
                           equals) minimising the spread over the nonzero orders k of
                           y_k + 2 k log2r, y_k = log2 max|A_k| + log2 max|B_k| (the worst
                           order's relative error grows with that spread; a geometric decay
-                          is flattened); TEK step: A = B = U; MD link update: A = U,
-                          B = i eps P; refitted at every step or phase -- this reads
-                          per-order maxima back and synchronises the stream, so never inside
-                          graph capture; default 0 */
+                          is flattened), among those that lift no order of A or B above
+                          max(1, its largest order) and, in the split form, keep the scale
+                          factors 2^(k log2r) within 2^+-120; TEK step: A = B = U; MD link
+                          update: A = U, B = i eps P; refitted at every step or phase --
+                          this reads per-order maxima back and synchronises the stream, so
+                          never inside graph capture; default 0 */
   void* workspace;     /* device scratch, >= nspt_workspace_size() bytes */
   size_t workspace_bytes;
 } nspt_opts;

@@ -210,7 +210,7 @@ int tek_log2r(const Plan& p, const double2* A, const double2* B, void* ws, cudaS
   *lr = 0;
   if (p.algo != NSPT_ALGO_FFT) return NSPT_OK;
   if (!p.rescale_auto) { *lr = p.log2r; return NSPT_OK; }
-  return nspt_split_fit_rescale(A, B, p.N, p.T, p.batch * 4, fit_scratch(p, ws), lr, st);
+  return nspt_split_fit_rescale(A, B, p.N, p.T, p.batch * 4, fit_scratch(p, ws), lr, st, p.prec == NSPT_PREC_SPLIT);
 }
 
 // mode: NSPT_LMODE_STEP (drift, increment, update), NSPT_LMODE_DRIFT (drift F only),

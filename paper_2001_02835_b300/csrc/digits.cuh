@@ -61,16 +61,19 @@ __device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
 }
 
 // smallest e with |x| < 2^e for every part, from the exponent field
+// (a subnormal part has |x| < 2^-1022, resp. 2^-126; only a row of exact zeros gets -100000)
 __device__ __forceinline__ int exp_bound(double2 v) {
   const int a = (int)((__double_as_longlong(v.x) >> 52) & 0x7FF), b = (int)((__double_as_longlong(v.y) >> 52) & 0x7FF);
   const int m = max(a, b);
-  return m == 0 ? -100000 : m - 1022;
+  if (m != 0) return m - 1022;
+  return ((__double_as_longlong(v.x) | __double_as_longlong(v.y)) << 1) ? -1022 : -100000;
 }
 __device__ __forceinline__ int exp_bound(float4 v) {
   // |hi + lo| < 2^(exponent(hi) + 1) since |lo| <= ulp(hi)/2
   const int a = (int)((__float_as_uint(v.x) >> 23) & 0xFF), b = (int)((__float_as_uint(v.z) >> 23) & 0xFF);
   const int m = max(a, b);
-  return m == 0 ? -100000 : m - 126;
+  if (m != 0) return m - 126;
+  return ((__float_as_uint(v.x) | __float_as_uint(v.z)) << 1) ? -126 : -100000;
 }
 __device__ __forceinline__ double2 conj_of(double2 v) { return make_double2(v.x, -v.y); }
 __device__ __forceinline__ float4 conj_of(float4 v) { return make_float4(v.x, v.y, -v.z, -v.w); }

@@ -368,7 +368,7 @@ __global__ void order_maxexp_kernel(const double2* __restrict__ A, const double2
 // against k gives r = 2^round(-sigma / 2), one r for both operands so that
 // C_k = r^-k (A' * B')_k.  Reads a few integers back: synchronises the stream.
 int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int batch, void* scratch, int* log2r,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool float_range) {
   int* d = (int*)scratch;
   TRYC(cudaMemsetAsync(d, 0, sizeof(int) * 2 * (T + 1), st));
   const long long E = (long long)N * N;
@@ -384,13 +384,30 @@ int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int
   // decay this flattens it; for a faster, factorial one it balances the first and last orders),
   // the smallest |log2r| among equals
   std::vector<std::pair<int, double>> y;
-  for (int k = 0; k <= T; ++k)
+  int maxA = -100000, maxB = -100000;  // log2 of the largest order of each operand
+  for (int k = 0; k <= T; ++k) {
+    if (h[k] != 0) maxA = std::max(maxA, h[k] - 1023);
+    if (h[T + 1 + k] != 0) maxB = std::max(maxB, h[T + 1 + k] - 1023);
     if (h[k] != 0 && h[T + 1 + k] != 0) y.push_back({k, (double)(h[k] - 1023) + (double)(h[T + 1 + k] - 1023)});
+  }
   *log2r = 0;
   if (y.size() >= 2) {
     double best = 1e300;
     for (int a = 0; a <= 120; ++a) {
       const int lr = (a % 2) ? (a + 1) / 2 : -(a / 2);  // 0, 1, -1, 2, -2, ...
+      // the double-float transforms work in the FP32 exponent range: scale factors 2^(k lr)
+      // within 2^+-120
+      if (float_range && (long long)std::abs(lr) * T > 120) continue;
+      // no scaled order may exceed max(1, the largest unscaled order): the rescale lifts small
+      // orders but never makes a series larger than it was or than 1, so products and powers
+      // of the scaled series (staples, exp_star's powers) stay in range
+      const int capA = std::max(maxA, 0), capB = std::max(maxB, 0);
+      bool ok = true;
+      for (int k = 0; k <= T && ok; ++k) {
+        if (h[k] != 0 && h[k] - 1023 + k * lr > capA) ok = false;
+        if (h[T + 1 + k] != 0 && h[T + 1 + k] - 1023 + k * lr > capB) ok = false;
+      }
+      if (!ok) continue;
       double lo = 1e300, hi = -1e300;
       for (const auto& kv : y) {
         const double v = kv.second + 2.0 * kv.first * lr;

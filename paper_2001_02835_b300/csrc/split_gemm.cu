@@ -345,9 +345,15 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int m = m0 + row;
       const bool mvalid = m < N;
       const int ea = mvalid ? __ldg(P.expA + (long long)q * N + m) : 0;
-      // the scale 2^(e_A + e_B - 14) of an output is fa * 2^(e_B - 7): two powers of two, so
-      // the product is exact (each clamped to the normal range, like the values they scale)
+      // the scale 2^(e_A + e_B - 14) of an output: fa * 2^(e_B - 7) when both factors are normal
+      // floats (then the product is exact), else as two halves of the exponent (tiny or huge rows)
       const float fa = pow2f(ea - 7);
+      const bool fa_ok = (unsigned)(ea - 7 + 126) <= 253u;
+      auto out_scale = [&](int eb) -> float {
+        if (fa_ok && (unsigned)(eb - 7 + 126) <= 253u) return fa * pow2f(eb - 7);
+        const int k = ea + eb - 14, k1 = k / 2;
+        return pow2f(k1) * pow2f(k - k1);
+      };
       float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
@@ -388,7 +394,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
           const int n = nb + c;
           if (!mvalid || n >= N) continue;
           const float h = s_[c] + e_[c], l = e_[c] - (h - s_[c]);
-          const float f = fa * pow2f(__ldg(expB + n) - 7);
+          const float f = out_scale(__ldg(expB + n));
           reinterpret_cast<float2*>(crow + n)[half] = make_float2(h * f, l * f);
         }
         continue;
@@ -435,7 +441,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
         if (!mvalid || n >= N) continue;
         const float rh = sr[c] + er[c], rl = er[c] - (rh - sr[c]);
         const float ih = si[c] + ei[c], il = ei[c] - (ih - si[c]);
-        const float f = fa * pow2f(__ldg(expB + n) - 7);
+        const float f = out_scale(__ldg(expB + n));
         if (plain) {
           crow[n] = make_float4(rh * f, rl * f, ih * f, il * f);
         } else {

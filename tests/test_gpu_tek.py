@@ -57,3 +57,24 @@ def test_langevin_generic_vacuum_drift(nspt):
     _, F = nspt.tek_langevin_step(tU, dev(eta), flux, 0.02, want_drift=True, algo="fft")
     assert max_order_rel(host(F)[0], refF) <= TOL
     assert max_order_rel(host(tU)[0], refU) <= TOL
+
+
+@pytest.mark.parametrize("T", [32, 40, 47, 63])
+def test_split_langevin_high_orders_match_fp64(nspt, T):
+    """O(g^40) and beyond: exp_star's coefficients 1/k! fall below the FP32 normal range
+    (k >= 35), so spectrum rows whose entries are all subnormal reach the slicer; they must get
+    an exponent bound, not the empty-row marker (which once scaled them by 2^254 into inf).
+    The split Langevin step matches the FP64 form per order there too."""
+    g = syn.rng(9100 + T)
+    L, flux = 3, 1
+    N = L * L
+    U = syn.link_series(g, L, flux, T, 1)
+    eta = dev(np.ascontiguousarray(syn.md_momenta(g, N, 1)))
+    res = {}
+    for prec in ("fp64", "split"):
+        tU = dev(U)
+        nspt.tek_langevin_step(tU, eta, flux, 0.01, algo="fft", prec=prec)
+        res[prec] = host(tU)
+    assert np.all(np.isfinite(res["split"]))
+    tol = 2.0 ** 10 * np.sqrt(N) * (2.0 ** -47 + 2.0 ** -44)
+    assert max_order_rel(res["split"][:, :, 1:], res["fp64"][:, :, 1:]) <= tol
