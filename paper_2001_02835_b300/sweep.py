@@ -5,6 +5,7 @@ plus 40 leapfrog steps, split form) split into its force and link-update phases,
 split FFT-CONV product rate at batch 4.  Prints a markdown table.
 
     python -m paper_2001_02835_b300.sweep [--N 121,169,225,289] [--T 15,31,63] [--md-steps 40]
+    python -m paper_2001_02835_b300.sweep --accuracy    # per-order accuracy from the vacuum
 
 Each configuration starts at the twisted vacuum (twist eaters at order 0, higher orders
 zero) with seeded momenta of variance 1/N; one untimed trajectory thermalises it, then the
@@ -72,15 +73,52 @@ def product_point(N, T, batch=4):
     return batch / (ms * 1e-3)
 
 
+def accuracy_table(L=11, T=15, flux=1, eps=0.02, steps=(1, 10, 40)):
+    """Per-order error of MD trajectories from the twisted vacuum (momenta of variance 1/N)
+    against the naive FP64 form, which computes every order on its own: the FFT-CONV forms
+    (FP64 and split) with and without the per-order rescale fitted at every phase."""
+    N = L * L
+    g = syn.rng(syn.SEED_BASE + 9)
+    U0 = syn.vacuum_links(L, flux, T, 1)
+    eta = torch.from_numpy(np.ascontiguousarray(syn.md_momenta(g, N, 1))).cuda()
+
+    def run(algo, prec, r, n):
+        U = torch.from_numpy(U0).cuda()
+        P = torch.zeros_like(U)
+        nspt.tek_md_trajectory(U, P, flux, eps, n, eta=eta, algo=algo, prec=prec, rescale_log2r=r)
+        return U.cpu().numpy()[0]
+
+    ks = (1, T // 3, 2 * T // 3, T)
+    print("| steps | form | rescale | %s | max over orders 1..%d |" % (" | ".join("order %d" % k for k in ks), T))
+    print("|---|---|---|%s---|" % ("---|" * len(ks)))
+    for n in steps:
+        ref = run("naive", "fp64", 0, n)
+        den = np.sqrt(np.sum(np.abs(ref) ** 2, axis=(0, 2, 3)))
+        for prec in ("fp64", "split"):
+            for r, name in ((0, "none"), (nspt.RESCALE_AUTO, "fitted per phase")):
+                X = run("fft", prec, r, n)
+                e = np.sqrt(np.sum(np.abs(X - ref) ** 2, axis=(0, 2, 3))) / np.where(den == 0, 1, den)
+                print("| %d | FFT-CONV %s | %s | %s | %.1e |" % (n, prec, name, " | ".join("%.1e" % e[k] for k in ks),
+                                                              e[1:].max()))
+        mx = np.abs(ref).max(axis=(0, 2, 3))
+        print("| %d | max abs U_k (naive) | | %s | |" % (n, " | ".join("%.1e" % mx[k] for k in ks)))
+        sys.stdout.flush()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", default="121,169,225,289")
     ap.add_argument("--T", default="15,31,63")
     ap.add_argument("--md-steps", type=int, default=40)
+    ap.add_argument("--accuracy", action="store_true",
+                    help="print the per-order accuracy table of trajectories from the vacuum instead")
     a = ap.parse_args(argv)
     torch.cuda.set_device(0)
     if nspt.lib().nspt_init() != 0:
         raise SystemExit("nspt_init failed")
+    if a.accuracy:
+        accuracy_table()
+        return
     Ns = [int(x) for x in a.N.split(",")]
     Ts = [int(x) for x in a.T.split(",")]
     print("| N | T | MD trajectory (%d steps) s | force s | link update s | 10 trajectories s | products/s |"
