@@ -246,7 +246,8 @@ def polymat_mul_backward(A, B, gC, need_gA=True, need_gB=True, **kw):
 
 def tek_langevin_step(U: torch.Tensor, eta: torch.Tensor, flux: int, eps: float, want_drift: bool = False, **kw):
     """One Langevin step in place on U (batch, 4, T+1, N, N) with noise eta (batch, 4, N, N).
-    Returns (U, F) with F the drift of the input links when want_drift."""
+    Returns (U, F) with F the drift of the input links when want_drift.  kw: algo, prec, fft_len,
+    slices, rescale_log2r (per-order rescale of the step's order transforms; RESCALE_AUTO fits it)."""
     _check_tensor(U, "U")
     _check_tensor(eta, "eta")
     if U.dim() != 5 or U.shape[1] != 4:
@@ -266,7 +267,9 @@ def tek_langevin_step(U: torch.Tensor, eta: torch.Tensor, flux: int, eps: float,
 def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, nsteps: int,
                       eta: Optional[torch.Tensor] = None, **kw):
     """Leapfrog molecular dynamics in place on U and P (batch, 4, T+1, N, N); with eta
-    (batch, 4, N, N) the momentum is refreshed to P^(1) = eta first.  Returns (U, P)."""
+    (batch, 4, N, N) the momentum is refreshed to P^(1) = eta first.  Returns (U, P).  kw as for
+    tek_langevin_step; with rescale_log2r=RESCALE_AUTO every phase fits its own rescale (one
+    stream synchronisation per phase)."""
     _check_tensor(U, "U")
     _check_tensor(P, "P")
     if U.shape != P.shape or U.dim() != 5 or U.shape[1] != 4:
