@@ -82,6 +82,24 @@ def test_split_per_order_rescale(nspt):
     np.testing.assert_array_equal(Ca, C)
 
 
+@pytest.mark.parametrize("rescale", [0, "auto"])
+def test_split_orders_below_fp32_range_stay_finite(nspt, rescale):
+    """Orders falling off like 2^-3k reach 2^-189 at O(g^63), below the FP32 range of the
+    double-float transforms: whole spectrum rows are then subnormal or zero.  The product stays
+    finite, and the orders the transforms still resolve (here 0..6) match the oracle."""
+    g = syn.rng(5250)
+    N, T = 12, 63
+    A = syn.series_batch(g, N, T, 1)
+    B = syn.series_batch(g, N, T, 1)
+    s = (2.0 ** (-3 * np.arange(T + 1)))[None, :, None, None]
+    A, B = A * s, B * s
+    ref = pm.star(A, B)
+    r = nspt.RESCALE_AUTO if rescale == "auto" else 0
+    C = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split", rescale_log2r=r))
+    assert np.all(np.isfinite(C))
+    assert max_order_rel(C[:, :7], ref[:, :7]) <= 1e3 * bound(6, N)
+
+
 @pytest.mark.parametrize("N,T,batch", [(3, 2, 1), (9, 8, 2), (70, 5, 1)])
 def test_split_backward_matches_oracle(nspt, N, T, batch):
     g = syn.rng(5300 + N)
