@@ -75,8 +75,9 @@ typedef struct nspt_opts {
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
   int complex_mode;    /* split form: 4 (four real products per complex product); 0 = 4 */
   int rescale_log2r;   /* per-order rescale A_k, B_k -> r^k A_k, r^k B_k with r = 2^rescale_log2r,
-                          undone exactly on C (not part of the paper): split form of the
-                          products; split and FP64 FFT forms of nspt_tek_langevin_step and
+                          undone exactly on C (not part of the paper): FFT-CONV products (split
+                          and FP64 forms, the FP64 backward excepted); split and FP64 FFT forms
+                          of nspt_tek_langevin_step and
                           nspt_tek_md_trajectory, where it applies to every order transform
                           of the step (the map X_k -> r^k X_k commutes with every product and
                           sum of the step, so the result is the same in exact arithmetic and

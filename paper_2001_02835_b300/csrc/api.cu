@@ -101,7 +101,7 @@ cudaError_t add_identity(double2* X, long long stride_mats, int N, long long cou
 size_t ws_mul(const Plan& p) {
   if (p.algo == NSPT_ALGO_NAIVE) return 0;
   const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
-  if (p.prec == NSPT_PREC_FP64) return 3 * ((spec + 255) & ~(size_t)255);
+  if (p.prec == NSPT_PREC_FP64) return 3 * ((spec + 255) & ~(size_t)255) + 2 * 513 * sizeof(int);  // + fit scratch
   return nspt_split_ws_mul(p.N, p.T, p.batch, p.M, p.slices);
 }
 
@@ -116,11 +116,18 @@ int mul_fp64(const Plan& p, const double2* A, const double2* B, double2* C, void
   double2* At = w.take<double2>((size_t)b * M * p.E);
   double2* Bt = w.take<double2>((size_t)b * M * p.E);
   double2* Ct = w.take<double2>((size_t)b * M * p.E);
-  TRY(nspt_fft_fwd64(A, T + 1, At, (int)p.E, T, b, M, 0, 0, st));
-  TRY(nspt_fft_fwd64(B, T + 1, Bt, (int)p.E, T, b, M, 0, 0, st));
+  int* fit = w.take<int>(2 * 513);
+  // per-order rescale A_k, B_k -> r^k A_k, r^k B_k, undone on C (exact; as in the split form)
+  int lr = p.log2r;
+  if (p.rescale_auto) {
+    const int rc = nspt_split_fit_rescale(A, B, N, T, b, fit, &lr, st, false);
+    if (rc) return rc;
+  }
+  TRY(nspt_fft_fwd64(A, T + 1, At, (int)p.E, T, b, M, 0, lr, st));
+  TRY(nspt_fft_fwd64(B, T + 1, Bt, (int)p.E, T, b, M, 0, lr, st));
   ZgemmParams P = zg(ZG_MODE, At, M, Bt, M, Ct, M, N, M, T);
   TRY(nspt_zgemm64(P, b, st));
-  TRY(nspt_fft_inv64(Ct, C, T + 1, (int)p.E, N, T, b, M, 0, 0, 1.0, 0, st));
+  TRY(nspt_fft_inv64(Ct, C, T + 1, (int)p.E, N, T, b, M, 0, lr, 1.0, 0, st));
   return NSPT_OK;
 }
 

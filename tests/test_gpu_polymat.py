@@ -149,3 +149,22 @@ def test_su225_fft_vs_naive_and_sampled_oracle(nspt, T):
     scale = np.sqrt(np.mean(np.abs(Cn) ** 2))
     assert np.abs(got_f - ref).max() <= 1e-12 * scale * 10
     assert np.abs(got_n - ref).max() <= 1e-12 * scale * 10
+
+
+def test_fp64_fft_per_order_rescale(nspt):
+    """FFT-CONV mixes the orders in one spectrum: with orders growing like 4^k the low orders of
+    the FP64 form drown (relative error far above 1e-12); the per-order rescale r = 1/4 (exact,
+    undone on C) or the fitted one restores every order to FP64 accuracy."""
+    g = syn.rng(4400)
+    N, T = 16, 31
+    A = syn.series_batch(g, N, T, 2)
+    B = syn.series_batch(g, N, T, 2)
+    s = (4.0 ** np.arange(T + 1))[None, :, None, None]
+    A, B = A * s, B * s
+    ref = pm.star(A, B)
+    C0 = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="fp64", rescale_log2r=0))
+    C2 = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="fp64", rescale_log2r=-2))
+    Ca = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="fp64", rescale_log2r=nspt.RESCALE_AUTO))
+    assert max_order_rel(C2, ref) <= 1e-12
+    assert max_order_rel(Ca, ref) <= 1e-12
+    assert max_order_rel(C0, ref) > 1e3 * max_order_rel(C2, ref)
