@@ -133,6 +133,14 @@ def cpu_model():
     return "unknown"
 
 
+def arm_config(N, T, prec, ngpu, note):
+    """The workload both arms report (the same config object; `note` says how it ran)."""
+    M = 1 << (2 * (T + 1) - 1).bit_length()
+    return {"workload": "SU(%d) O(g^%d) FFT-CONV M=%d batch %d, %s form" % (N, T, M, BATCH, prec),
+            "N": N, "T": T, "M": M, "batch_per_gpu": BATCH, "prec": prec,
+            "parallelism": "replicas" if ngpu > 1 else "single", "l2": note}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -150,8 +158,8 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": {"workload": "SU(%d) O(g^%d) FFT-CONV (oracle direct DFT)" % (N, T), "N": N, "T": T,
-                   "batch": BATCH, "sample": "the whole batch of 4 products per step"},
+        "config": arm_config(N, T, args.prec or "split", args.gpus,
+                             "oracle's direct-DFT FFT-CONV in FP64 on the host cores, the whole batch per step"),
         "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
                          "sample": "batch of 4 products (N=%d, T=%d) per step, numpy FP64 oracle, %s"
                                    % (N, T, cpu_model())},
@@ -510,10 +518,7 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "c128 in/out; " + ("bf16 slices x6, fp32 exact partials" if prec == "split" else "f64"),
             "data": "synthetic (Haar SU(N) order 0, Gaussian var 1/N orders >= 1, seed 200102837)",
-            "config": {"workload": "SU(%d) O(g^%d) FFT-CONV M=%d batch %d, %s form" % (N, T, M, BATCH, prec),
-                       "N": N, "T": T, "M": M, "batch_per_gpu": BATCH, "prec": prec,
-                       "parallelism": "replicas" if ws > 1 else "single",
-                       "l2": "inputs 2 x %.0f MB > 126 MB L2, no flush" % (nbytes / 1e6)},
+            "config": arm_config(N, T, prec, ws, "inputs 2 x %.0f MB > 126 MB L2, no flush" % (nbytes / 1e6)),
             "eff_tflops": fft_flops(N, M) * value / 1e12,
             "roofline": roof,
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
