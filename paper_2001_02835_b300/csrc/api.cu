@@ -56,6 +56,8 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p) {
   p->log2r = p->rescale_auto ? 0 : o->rescale_log2r;
   if (!p->rescale_auto && (p->log2r < -60 || p->log2r > 60)) return NSPT_ERR_ARG;
   if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE) return NSPT_ERR_UNSUPPORTED;
+  // the split form's slicers hold up to 8 spectrum rows of N entries in shared memory
+  if (p->prec == NSPT_PREC_SPLIT && N > 1024) return NSPT_ERR_UNSUPPORTED;
   return NSPT_OK;
 }
 

@@ -50,6 +50,9 @@ def test_argument_checks_need_no_gpu(L):
     # FFT form without a workspace
     o4 = n.make_opts(algo="fft")
     assert L.nspt_polymat_mul(1 << 20, 1 << 24, 1 << 28, 4, 3, 1, ctypes.byref(o4), None) == -4
+    # split form beyond the slicers' shared-memory rows
+    o5 = n.make_opts(algo="fft", prec="split")
+    assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, 1025, 3, 1, ctypes.byref(o5), None) == -3
     # Langevin: N must be L^2 with gcd(flux, L) = 1, eps > 0
     assert L.nspt_tek_langevin_step(1 << 20, 1 << 30, None, 10, 2, 1, 1, 0.01, ctypes.byref(o), None) == -1
     assert L.nspt_tek_langevin_step(1 << 20, 1 << 30, None, 9, 2, 1, 3, 0.01, ctypes.byref(o), None) == -1
