@@ -45,3 +45,37 @@ def test_random_sizes_fft_forms_match_naive(nspt, N, T, batch):
     Cs = host(nspt.polymat_mul(dev(A), dev(B), algo="fft", prec="split"))
     assert np.all(np.isfinite(Cs))
     assert max_order_rel(Cs, ref) <= 2.0 ** 10 * math.sqrt(N) * (2.0 ** -47 + 2.0 ** -44)
+
+
+def _tek_cases(count=12, seed=4242):
+    g = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        L = int(g.choice([2, 3, 5, 7]))
+        flux = int(g.choice([k for k in range(1, L) if math.gcd(k, L) == 1] or [1]))
+        out.append((L, flux, int(g.integers(0, 71)), int(g.integers(1, 3))))
+    return out
+
+
+@pytest.mark.parametrize("L,flux,T,streams", _tek_cases())
+def test_random_sizes_tek_split_matches_fp64(nspt, L, flux, T, streams):
+    """One Langevin step and a 3-step MD trajectory at random (L, T): split form against the
+    FP64 FFT form per order (T up to 70 crosses the orders where exp_star's 1/k! leaves the FP32
+    normal range)."""
+    import torch
+    g = syn.rng(8800 + 10 * L + T)
+    N = L * L
+    U = syn.link_series(g, L, flux, T, streams)
+    eta = dev(np.ascontiguousarray(syn.md_momenta(g, N, streams)))
+    out = {}
+    for prec in ("fp64", "split"):
+        tU = dev(U)
+        nspt.tek_langevin_step(tU, eta, flux, 0.01, algo="fft", prec=prec)
+        tV, tP = dev(U), torch.zeros_like(dev(U))
+        nspt.tek_md_trajectory(tV, tP, flux, 0.02, 3, eta=eta, algo="fft", prec=prec)
+        out[prec] = (host(tU), host(tV))
+    tol = 2.0 ** 10 * math.sqrt(N) * (2.0 ** -47 + 2.0 ** -44)
+    for i in range(2):
+        assert np.all(np.isfinite(out["split"][i]))
+        if T > 0:
+            assert max_order_rel(out["split"][i][:, :, 1:], out["fp64"][i][:, :, 1:]) <= 10 * tol
