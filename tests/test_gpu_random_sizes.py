@@ -79,3 +79,18 @@ def test_random_sizes_tek_split_matches_fp64(nspt, L, flux, T, streams):
         assert np.all(np.isfinite(out["split"][i]))
         if T > 0:
             assert max_order_rel(out["split"][i][:, :, 1:], out["fp64"][i][:, :, 1:]) <= 10 * tol
+
+
+@pytest.mark.parametrize("N,T,batch", _cases(count=8, seed=777))
+def test_random_sizes_backward_forms_match_naive(nspt, N, T, batch):
+    """The backward (truncated correlations) at random sizes: FFT forms against the naive FP64
+    form."""
+    g = syn.rng(8500 + N + 1000 * T)
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    W = syn.gaussian(g, A.shape, 1.0)
+    rA, rB = (host(x) for x in nspt.polymat_mul_backward(dev(A), dev(B), dev(W), algo="naive", prec="fp64"))
+    for prec, tol in (("fp64", 1e-12), ("split", 2.0 ** 10 * math.sqrt(N) * (2.0 ** -47 + 2.0 ** -44))):
+        gA, gB = (host(x) for x in nspt.polymat_mul_backward(dev(A), dev(B), dev(W), algo="fft", prec=prec))
+        assert max_order_rel(gA, rA) <= tol
+        assert max_order_rel(gB, rB) <= tol
