@@ -154,7 +154,10 @@ NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, in
  * Split form: the mode GEMMs of all products run in ONE persistent
  * tensor-core launch whose per-product tensor maps travel in the kernel
  * parameters, so the call needs no device-side table and can be captured in
- * a CUDA graph (after nspt_init).  FP64 form: the products run one after
+ * a CUDA graph (after nspt_init).  The products' transforms and slicing (before)
+ * and inverse transforms (after) run on library-owned side streams forked from
+ * and joined back to `stream` by events (graph edges under capture); work
+ * queued on `stream` after the call starts after all of it.  FP64 form: the products run one after
  * another.  `descs` is a HOST array; pointers inside are device pointers with
  * the layout of nspt_polymat_mul.  Workspace: nspt_workspace_size_grouped().
  */

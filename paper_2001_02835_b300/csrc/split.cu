@@ -315,10 +315,64 @@ int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int re
   return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, P, out, exps, st);
 }
 
+// Library-owned side streams of a device: the independent per-product chains of a grouped call
+// (transforms and slicing before the one GEMM launch, inverse transforms after it) run on them,
+// forked from and joined back to the caller's stream by events, so that the small launches of
+// different products overlap.  Under graph capture the fork and join become graph edges.  Made in
+// nspt_init (never inside a capture); a mutex orders the enqueue of concurrent calls.
+constexpr int kSideStreams = 4;
+struct SideStreams {
+  std::mutex mu;
+  bool ok = false;
+  cudaStream_t s[kSideStreams];
+  cudaEvent_t fork, join[kSideStreams];
+};
+SideStreams g_side[64];
+
+SideStreams* side_streams() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  return g_side[dev].ok ? &g_side[dev] : nullptr;
+}
+
+// enqueues chain(i, stream) for i < count, spread over the side streams between a fork from and a
+// join back to st; without side streams the chains run on st
+template <typename F>
+int fork_join(int count, cudaStream_t st, F chain) {
+  SideStreams* ss = side_streams();
+  if (!ss) {
+    for (int i = 0; i < count; ++i) TRYS(chain(i, st));
+    return NSPT_OK;
+  }
+  std::lock_guard<std::mutex> lk(ss->mu);
+  const int k = std::min(count, kSideStreams);
+  TRYC(cudaEventRecord(ss->fork, st));
+  for (int j = 0; j < k; ++j) TRYC(cudaStreamWaitEvent(ss->s[j], ss->fork, 0));
+  int rc = NSPT_OK;
+  for (int i = 0; i < count && rc == NSPT_OK; ++i) rc = chain(i, ss->s[i % k]);
+  // join even after a failed enqueue, so that st never runs ahead of work already queued
+  for (int j = 0; j < k; ++j) {
+    TRYC(cudaEventRecord(ss->join[j], ss->s[j]));
+    TRYC(cudaStreamWaitEvent(st, ss->join[j], 0));
+  }
+  return rc;
+}
+
 int nspt_split_init() {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (dev >= 0 && dev < 64) {
+    SideStreams& ss = g_side[dev];
+    std::lock_guard<std::mutex> lk(ss.mu);
+    if (!ss.ok) {
+      bool good = cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
+      for (int j = 0; j < kSideStreams && good; ++j)
+        good = cudaStreamCreateWithFlags(&ss.s[j], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&ss.join[j], cudaEventDisableTiming) == cudaSuccess;
+      ss.ok = good;   // on failure the grouped calls run their chains on the caller's stream
+    }
+  }
   return nspt_split_gemm_init();
 }
 
@@ -539,16 +593,20 @@ int group_prepare(const nspt_polymat_desc* d, int count, int S, int log2r, const
   TRYC(cudaMemsetAsync(g.err, 0, sizeof(int), st));
   args.clear();
   for (int i = 0; i < count; ++i) {
+    const int N = d[i].N, M = pow2_at_least(2 * (d[i].T + 1));
+    args.push_back(gemm_args(g.ws[i], N, d[i].batch * M, S));
+  }
+  // every product's transforms and slicing: independent chains (own workspace regions)
+  return fork_join(count, st, [&](int i, cudaStream_t s) -> int {
     const int N = d[i].N, T = d[i].T, b = d[i].batch, M = pow2_at_least(2 * (T + 1));
     const int E = N * N, Q = b * M;
     const SplitWs& w = g.ws[i];
-    TRYC(nspt_fft_fwd_df((const double2*)d[i].A, T + 1, w.At, E, T, b, M, 0, log2r, st));
-    TRYC(nspt_fft_fwd_df((const double2*)d[i].B, T + 1, w.Bt, E, T, b, M, 0, log2r, st, N));
-    TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
-    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, st));
-    args.push_back(gemm_args(w, N, Q, S));
-  }
-  return NSPT_OK;
+    TRYC(nspt_fft_fwd_df((const double2*)d[i].A, T + 1, w.At, E, T, b, M, 0, log2r, s));
+    TRYC(nspt_fft_fwd_df((const double2*)d[i].B, T + 1, w.Bt, E, T, b, M, 0, log2r, s, N));
+    TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, s));
+    TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, s));
+    return NSPT_OK;
+  });
 }
 
 }  // namespace
@@ -562,11 +620,11 @@ int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log
   std::vector<SplitGemmArgs> args;
   TRYS(group_prepare(d, count, S, log2r, g, args, st));
   TRYS(nspt_split_gemm_batch(args.data(), count, S, choose_bn(group_signature(d, count, S)), g_num_sms, st));
-  for (int i = 0; i < count; ++i) {
+  return fork_join(count, st, [&](int i, cudaStream_t s) -> int {
     const int N = d[i].N, T = d[i].T, M = pow2_at_least(2 * (T + 1));
-    TRYC(nspt_fft_inv_df(g.ws[i].Ct, (double2*)d[i].C, T + 1, N * N, T, d[i].batch, M, 0, log2r, st));
-  }
-  return NSPT_OK;
+    TRYC(nspt_fft_inv_df(g.ws[i].Ct, (double2*)d[i].C, T + 1, N * N, T, d[i].batch, M, 0, log2r, s));
+    return NSPT_OK;
+  });
 }
 
 int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,
