@@ -485,11 +485,18 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
   // (B's spectra are written transposed, so that both operands are sliced by rows)
-  TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, st));
-  TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, st, N));
-  // a2: slices of A~_q (rows) and of B~_q^T (rows of the transposed spectra)
-  TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, st));
-  TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, st));
+  // a2: slices of A~_q (rows) and of B~_q^T (rows of the transposed spectra); the two operands'
+  // chains run on side streams, so that one operand's transform overlaps the other's slicing
+  TRYS(fork_join(2, st, [&](int i, cudaStream_t s) -> int {
+    if (i == 0) {
+      TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, s));
+      TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, s));
+    } else {
+      TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, s, N));
+      TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, s));
+    }
+    return NSPT_OK;
+  }));
   // a3: mode GEMMs on the tensor cores
   TRYS(gemm(w, N, Q, S, st));
   // a4: inverse transform, truncation, unscale 2^(-k log2r)
