@@ -832,23 +832,18 @@ int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int
              int* eB_big = nullptr, LinkCache* lc = nullptr) {
   std::vector<SplitGemmArgs> args;
   std::vector<std::pair<int, int>> sig;
+  std::vector<char> slice_a(count, 1), slice_b(count, 1);
   for (int j = 0; j < count; ++j) {
     const Job& J = jobs[j];
     __nv_bfloat16* sa = slA_big ? slA_big : w.slA[j];
     __nv_bfloat16* sb = slB_big ? slB_big : w.slB[j];
     int* ea = eA_big ? eA_big : w.expA[j];
     int* eb = eB_big ? eB_big : w.expB[j];
-    // a link operand is sliced once per force evaluation and its slices reused
+    // a link operand is sliced once per force evaluation (by the first job that takes it) and
+    // its slices reused
     const int xa = link_slot(lc, J.a, false), xb = link_slot(lc, J.b, true);
-    bool slice_a = true, slice_b = true;
-    if (xa >= 0) { sa = w.lkA[xa]; ea = w.lkEA[xa]; slice_a = !lc->okA[xa]; lc->okA[xa] = true; }
-    if (xb >= 0) { sb = w.lkB[xb]; eb = w.lkEB[xb]; slice_b = !lc->okB[xb]; lc->okB[xb] = true; }
-    // left operand: rows of A (dagger: conjugated columns of the reversed spectrum)
-    if (slice_a)
-      TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag ^ J.a.tr, J.a.dag, N, nb * M, 2, sa, ea, st));
-    // right operand: rows of B^T (dagger: conjugated rows of the reversed spectrum)
-    if (slice_b)
-      TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, (!J.b.dag) ^ J.b.tr, J.b.dag, N, nb * M, 3, sb, eb, st));
+    if (xa >= 0) { sa = w.lkA[xa]; ea = w.lkEA[xa]; slice_a[j] = !lc->okA[xa]; lc->okA[xa] = true; }
+    if (xb >= 0) { sb = w.lkB[xb]; eb = w.lkEB[xb]; slice_b[j] = !lc->okB[xb]; lc->okB[xb] = true; }
     SplitGemmArgs a;
     a.slicesA = sa; a.slicesB = sb; a.expA = ea; a.expB = eb; a.C = J.c;
     a.N = N; a.Kp = kpad(N); a.Q = nb * M; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
@@ -856,6 +851,21 @@ int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int
     args.push_back(a);
     sig.push_back({N, nb * M});
   }
+  // the jobs' slicings write disjoint slots: independent chains on the side streams, joined
+  // before the one GEMM launch
+  TRYS(fork_join(count, st, [&](int j, cudaStream_t s) -> int {
+    const Job& J = jobs[j];
+    const SplitGemmArgs& a = args[j];
+    // left operand: rows of A (dagger: conjugated columns of the reversed spectrum)
+    if (slice_a[j])
+      TRYS(nspt_split_slice_df(S, J.a.p, J.a.bs, M, J.a.dag, J.a.dag ^ J.a.tr, J.a.dag, N, nb * M, 2,
+                               (void*)a.slicesA, (int*)a.expA, s));
+    // right operand: rows of B^T (dagger: conjugated rows of the reversed spectrum)
+    if (slice_b[j])
+      TRYS(nspt_split_slice_df(S, J.b.p, J.b.bs, M, J.b.dag, (!J.b.dag) ^ J.b.tr, J.b.dag, N, nb * M, 3,
+                               (void*)a.slicesB, (int*)a.expB, s));
+    return NSPT_OK;
+  }));
   return nspt_split_gemm_batch(args.data(), count, S, choose_bn(signature(S, sig)), g_num_sms, st);
 }
 
