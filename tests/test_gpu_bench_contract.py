@@ -31,6 +31,7 @@ def test_bench_line_contract():
     r = d["roofline"]
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s" and 0 < r["frac"] < 1.5
     assert abs(r["frac"] - r["achieved"] / r["peak"]) <= 1e-9
+    assert 0 < r["frac_of_burst"] <= r["frac"]
     c = d["cpu_baseline"]
     assert c["kind"] == "oracle" and c["value"] > 0 and c["cores"] >= 1
     e = d["e2e"]
