@@ -105,14 +105,20 @@ def accuracy_table(L=11, T=15, flux=1, eps=0.02, steps=(1, 10, 40)):
         sys.stdout.flush()
 
 
-def main(argv=None):
+def parser():
+    """Command line; the default axes are the GPU rows of the paper's benchmark parameters
+    (Sec. 3, Table "Parameters": 40 MD steps, SU(121..289), N_trunc 15, 31, 63)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--N", default="121,169,225,289")
     ap.add_argument("--T", default="15,31,63")
     ap.add_argument("--md-steps", type=int, default=40)
     ap.add_argument("--accuracy", action="store_true",
                     help="print the per-order accuracy table of trajectories from the vacuum instead")
-    a = ap.parse_args(argv)
+    return ap
+
+
+def main(argv=None):
+    a = parser().parse_args(argv)
     torch.cuda.set_device(0)
     if nspt.lib().nspt_init() != 0:
         raise SystemExit("nspt_init failed")
