@@ -40,6 +40,10 @@ def test_argument_checks_need_no_gpu(L):
     assert L.nspt_polymat_mul(None, None, None, 4, 3, 1, ctypes.byref(o), None) == -1
     assert L.nspt_polymat_mul(1 << 20, 2 << 20, 3 << 20, 0, 3, 1, ctypes.byref(o), None) == -1
     assert L.nspt_polymat_mul(1 << 20, 2 << 20, 3 << 20, 4, -1, 1, ctypes.byref(o), None) == -1
+    # an empty batch is refused, not treated as a no-op
+    assert L.nspt_polymat_mul(1 << 20, 2 << 20, 3 << 20, 4, 3, 0, ctypes.byref(o), None) == -1
+    assert L.nspt_polymat_mul_backward(1 << 20, 2 << 20, 3 << 20, 4 << 20, 5 << 20, 4, 3, 0, ctypes.byref(o),
+                                       None) == -1
     # output overlapping an input
     assert L.nspt_polymat_mul(1 << 20, 1 << 24, (1 << 20) + 16, 4, 3, 1, ctypes.byref(o), None) == -2
     # FFT length not a power of two / too short for wrap-free convolution

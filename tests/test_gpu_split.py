@@ -35,8 +35,9 @@ def nspt():
 
 @pytest.mark.parametrize("N,T,batch", [(1, 0, 1), (3, 2, 2), (9, 8, 4), (33, 15, 2), (48, 7, 1), (49, 3, 2),
                                        (130, 5, 1), (225, 3, 1),
-                                       # N > 512: rows sliced through shared memory
-                                       (600, 1, 1),
+                                       # N > 512: rows sliced through shared memory; N = 1024 is the
+                                       # largest split size (K = 1024 per digit-group dot product)
+                                       (600, 1, 1), (1024, 1, 1),
                                        # M = 256 and 512: 16 and 8 entries per transform CTA
                                        (9, 100, 1), (17, 127, 2), (6, 200, 1)])
 def test_split_mul_matches_oracle(nspt, N, T, batch):
