@@ -199,13 +199,14 @@ size_t ws_langevin_core(const Plan& p) {
   const long long T1 = p.T + 1, M = p.M;
   size_t mats;
   if (p.algo == NSPT_ALGO_FFT) {
-    // spectra: U(4) PQ(18) Acc(18) In(4); series: tmp(18) S(4) Y(4) R(8); exp spectra Y,R,C (12)
-    mats = (size_t)(4 + 18 + 18 + 4 + 12) * M + (size_t)(18 + 4 + 4 + 8) * T1;
+    // spectra: U(4) PQ(18) Acc(18) In(4); series: tmp S(4) Y(4) R(8); exp spectra Y,R,C (12)
+    mats = (size_t)(4 + 18 + 18 + 4 + 12) * M + (size_t)(nspt_tmp_series(p.T) + 4 + 4 + 8) * T1;
   } else {
     // series: P1(6) Q(12) inner(4) S(4) Y(4) R(8) U0(4)
     mats = (size_t)(6 + 12 + 4 + 4 + 4 + 8 + 4) * T1;
   }
-  return (size_t)p.batch * mats * E * sizeof(double2) + (size_t)p.batch * 4 * T1 * sizeof(double) + 8 * 256;
+  // + up to 255 bytes of alignment per carved buffer (at most 16 buffers)
+  return (size_t)p.batch * mats * E * sizeof(double2) + (size_t)p.batch * 4 * T1 * sizeof(double) + 16 * 256;
 }
 
 // a TEK step's workspace: the pipeline's, then the scratch of the per-order rescale fit
@@ -237,14 +238,14 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
       const double ang = 2.0 * M_PI * flux * sgn / L;
       z[mu][nu] = (mu == nu) ? make_double2(0, 0) : make_double2(cos(ang), sin(ang));
     }
-  WsCarver w(ws, SIZE_MAX);
+  WsCarver w(ws, ws_langevin_core(p));
   if (p.algo == NSPT_ALGO_FFT) {
     const int M = p.M;
     double2* specU = w.take<double2>((size_t)nb * 4 * M * E);
     double2* specPQ = w.take<double2>((size_t)nb * 18 * M * E);
     double2* specAcc = w.take<double2>((size_t)nb * 18 * M * E);
     double2* specIn = w.take<double2>((size_t)nb * 4 * M * E);
-    double2* serTmp = w.take<double2>((size_t)nb * 18 * T1 * E);
+    double2* serTmp = w.take<double2>((size_t)nb * nspt_tmp_series(T) * T1 * E);
     double2* serS = w.take<double2>((size_t)nb * 4 * T1 * E);
     double2* serY = w.take<double2>((size_t)nb * 4 * T1 * E);
     double2* serR[2] = {w.take<double2>((size_t)nb * 4 * T1 * E), w.take<double2>((size_t)nb * 4 * T1 * E)};
@@ -252,6 +253,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     double2* spR = w.take<double2>((size_t)nb * 4 * M * E);
     double2* spC = w.take<double2>((size_t)nb * 4 * M * E);
     double* imtr = w.take<double>((size_t)nb * 4 * T1);
+    if (!w.fits()) return NSPT_ERR_WORKSPACE;  // the carve outgrew ws_langevin_core: a sizing bug
     const long long sm = (long long)M;  // matrices per spectrum
     // 1. spectra of the four links
     TRY(nspt_fft_fwd64(U, T1, specU, (int)E, T, nb * 4, M, 0, lr, st));
@@ -340,7 +342,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
       if ((rc = star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k))) return rc;
       Yp[k] = Pk;
     }
-    double2* prod = serTmp + (NSPT_PS_MAX_BLOCK - 1) * ser4;
+    double2* prod = serTmp + (sb - 1) * ser4;  // the slot after the powers Y^2..Y^s
     auto block = [&](int j) {
       PsTerms tm{};
       double f = 1.0;  // 1 / (j s)!
@@ -377,6 +379,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
   double2* serR[2] = {w.take<double2>((size_t)nb * 4 * T1 * E), w.take<double2>((size_t)nb * 4 * T1 * E)};
   double2* serU0 = w.take<double2>((size_t)nb * 4 * T1 * E);
   double* imtr = w.take<double>((size_t)nb * 4 * T1);
+  if (!w.fits()) return NSPT_ERR_WORKSPACE;  // the carve outgrew ws_langevin_core: a sizing bug
   auto link = [&](const double2* base, int mu) { return base + (long long)mu * T1 * E; };
   auto wlink = [&](double2* base, int mu) { return base + (long long)mu * T1 * E; };
   if (mode != NSPT_LMODE_UPDATE) {

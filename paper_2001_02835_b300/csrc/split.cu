@@ -779,7 +779,7 @@ LangevinWs carve_langevin(void* base, int N, int T, int nb, int M, int S) {
   w.spY = c.take<float4>(4 * spec);
   w.spR = c.take<float4>(4 * spec);
   w.spC = c.take<float4>(4 * spec);
-  w.serTmp = c.take<double2>(18 * ser);
+  w.serTmp = c.take<double2>((long long)nspt_tmp_series(T) * ser);
   w.serS = c.take<double2>(4 * ser);
   w.serY = c.take<double2>(4 * ser);
   w.serR[0] = c.take<double2>(4 * ser);
@@ -972,7 +972,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
     TRYS(star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k));
     Yp[k] = Pk;
   }
-  double2* prod = w.serTmp + (NSPT_PS_MAX_BLOCK - 1) * ser4;
+  double2* prod = w.serTmp + (sb - 1) * ser4;  // the slot after the powers Y^2..Y^s
   double2* Qs[2] = {w.serR[0], w.serR[1]};
   auto block = [&](int j) {
     PsTerms tm{};

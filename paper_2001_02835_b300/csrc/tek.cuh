@@ -15,7 +15,7 @@ enum { NSPT_LMODE_STEP = 0, NSPT_LMODE_DRIFT = 1, NSPT_LMODE_UPDATE = 2 };
 // Y^2 .. Y^s, then Horner in Y^s, Q_j = B_j + Y^s Q_{j+1}, B_j = sum_{i<s} Y^i / (js+i)!.
 // Block size s <= NSPT_PS_MAX_BLOCK minimising the mode-GEMM count when every
 // product runs at its own truncation (Y^k starts at order k).
-constexpr int NSPT_PS_MAX_BLOCK = 4;
+constexpr int NSPT_PS_MAX_BLOCK = 8;
 inline int nspt_pow2_at_least(int x) {
   int m = 1;
   while (m < x) m <<= 1;
@@ -32,6 +32,13 @@ inline int nspt_ps_block(int T) {
   for (int s = 2; s <= NSPT_PS_MAX_BLOCK && s <= T; ++s)
     if (nspt_ps_cost(T, s) < nspt_ps_cost(T, best)) best = s;
   return best;
+}
+// temporary link-series slots (units of batch x (T+1) x N^2 entries) of a step's workspace:
+// 18 for the staple pipeline, reused by exp_star for 4 per power Y^2..Y^s plus 4 for the
+// Horner product
+inline int nspt_tmp_series(int T) {
+  const int ps = 4 * (nspt_ps_block(T) > 1 ? nspt_ps_block(T) : 1);
+  return ps > 18 ? ps : 18;
 }
 // terms of one block: P[i] = Y^i (i >= 1; P[0] unused), c[i] its coefficient, c[0] that of 1
 struct PsTerms {
