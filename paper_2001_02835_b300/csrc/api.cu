@@ -323,10 +323,18 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     //    order-shifted series): Y^2 .. Y^s, then Q_j = B_j + Y^s Q_{j+1} for
     //    j = r-1 .. 0 with B_j = sum_{i<s} Y^i / (js+i)!, Q_j needed to order T - s j
     const long long ns = (long long)nb * 4, ser4 = ns * T1 * E;
-    // c^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
-    auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
+    // c^(0..t) = (a * b)^(0..t) for series a (read to order ta >= t) and b (read to order t);
+    // consecutive products with the same left operand and transform length transform it once,
+    // read to the largest truncation of the run (ta + t < Mt keeps the product wrap-free)
+    const double2* a_done = nullptr;
+    int a_Mt = 0, a_t = -1;
+    auto star_t = [&](const double2* a, int ta, const double2* b, double2* c, int t) -> int {
       const int Mt = next_pow2(2 * (t + 1));
-      TRY(nspt_fft_fwd64(a, T1, spY, (int)E, t, nb * 4, Mt, 0, lr, st));
+      if (ta < t || 2 * (ta + 1) > Mt) ta = t;
+      if (!(a == a_done && Mt == a_Mt && t <= a_t && a_t + t < Mt)) {
+        TRY(nspt_fft_fwd64(a, T1, spY, (int)E, ta, nb * 4, Mt, 0, lr, st));
+        a_done = a; a_Mt = Mt; a_t = ta;
+      }
       TRY(nspt_fft_fwd64(b, T1, spR, (int)E, t, nb * 4, Mt, 0, lr, st));
       ZgemmParams P = zg(ZG_MODE, spY, Mt, spR, Mt, spC, Mt, N, Mt, t);
       TRY(nspt_zgemm64(P, nb * 4, st));
@@ -339,7 +347,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     for (int k = 2; k <= sb; ++k) {
       double2* Pk = serTmp + (k - 2) * ser4;
       TRY(cudaMemsetAsync(Pk, 0, (size_t)ser4 * sizeof(double2), st));  // orders below k stay 0
-      if ((rc = star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k))) return rc;
+      if ((rc = star_t(Ysrc + E, nspt_ps_power_ta(T, sb, k), Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k))) return rc;
       Yp[k] = Pk;
     }
     double2* prod = serTmp + (sb - 1) * ser4;  // the slot after the powers Y^2..Y^s
@@ -358,7 +366,7 @@ int langevin_fp64(const Plan& p, double2* U, const double2* eta, double2* F, int
     TRY(nspt_ps_combine(serR[0], block(r), sb - 1, nullptr, sb, T - sb * r, T, N, ns, st));
     for (int j = r - 1; j >= 0; --j) {
       const int t = T - sb * (j + 1);
-      if ((rc = star_t(Yp[sb] + sb * E, serR[cur], prod, t))) return rc;  // (Y^s Q_{j+1}) from order s
+      if ((rc = star_t(Yp[sb] + sb * E, nspt_ps_horner_ta(T, sb, j), serR[cur], prod, t))) return rc;  // (Y^s Q_{j+1}) from order s
       TRY(nspt_ps_combine(serR[cur ^ 1], block(j), sb - 1, prod, sb, T - sb * j, T, N, ns, st));
       cur ^= 1;
     }

@@ -829,7 +829,7 @@ int link_slot(const LinkCache* lc, const SpecRef& r, bool right) {
 
 int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int M, int S, cudaStream_t st,
              __nv_bfloat16* slA_big = nullptr, __nv_bfloat16* slB_big = nullptr, int* eA_big = nullptr,
-             int* eB_big = nullptr, LinkCache* lc = nullptr) {
+             int* eB_big = nullptr, LinkCache* lc = nullptr, bool a_ready = false) {
   std::vector<SplitGemmArgs> args;
   std::vector<std::pair<int, int>> sig;
   std::vector<char> slice_a(count, 1), slice_b(count, 1);
@@ -844,6 +844,7 @@ int run_jobs(const LangevinWs& w, const Job* jobs, int count, int N, int nb, int
     const int xa = link_slot(lc, J.a, false), xb = link_slot(lc, J.b, true);
     if (xa >= 0) { sa = w.lkA[xa]; ea = w.lkEA[xa]; slice_a[j] = !lc->okA[xa]; lc->okA[xa] = true; }
     if (xb >= 0) { sb = w.lkB[xb]; eb = w.lkEB[xb]; slice_b[j] = !lc->okB[xb]; lc->okB[xb] = true; }
+    if (a_ready) slice_a[j] = 0;  // the caller's left operand is already sliced into sa / ea
     SplitGemmArgs a;
     a.slicesA = sa; a.slicesB = sb; a.expA = ea; a.expB = eb; a.C = J.c;
     a.N = N; a.Kp = kpad(N); a.Q = nb * M; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 0;
@@ -954,13 +955,23 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   //    order-shifted series): Y^2 .. Y^s, then Q_j = B_j + Y^s Q_{j+1} for
   //    j = r-1 .. 0 with B_j = sum_{i<s} Y^i / (js+i)!, Q_j needed to order T - s j
   const long long ns = (long long)nb * 4, ser4 = ns * T1 * E;
-  // C^(0..t) = (a * b)^(0..t) for series a, b read from their orders 0..t
-  auto star_t = [&](const double2* a, const double2* b, double2* c, int t) -> int {
+  // C^(0..t) = (a * b)^(0..t) for series a (read to order ta >= t) and b (read to order t).
+  // Consecutive products with the same left operand and transform length transform and slice
+  // it once, read to the largest truncation ta of the run: with ta + t < Mt the circular
+  // product of length Mt still equals the linear one through order t.
+  const double2* a_done = nullptr;
+  int a_Mt = 0, a_t = -1;
+  auto star_t = [&](const double2* a, int ta, const double2* b, double2* c, int t) -> int {
     const int Mt = nspt_pow2_at_least(2 * (t + 1));
-    TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, t, nb * 4, Mt, 0, log2r, st));
+    if (ta < t || 2 * (ta + 1) > Mt) ta = t;
+    const bool reuse = a == a_done && Mt == a_Mt && t <= a_t && a_t + t < Mt;
+    if (!reuse) {
+      TRYC(nspt_fft_fwd_df(a, T1, w.spY, E, ta, nb * 4, Mt, 0, log2r, st));
+      a_done = a; a_Mt = Mt; a_t = ta;
+    }
     TRYC(nspt_fft_fwd_df(b, T1, w.spR, E, t, nb * 4, Mt, 0, log2r, st, N));  // transposed: sliced by rows
     Job J{SpecRef{w.spY, (long long)Mt, 0}, SpecRef{w.spR, (long long)Mt, 0, 1}, w.spC, make_double2(1, 0), 0, 0};
-    TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0]));
+    TRYS(run_jobs(w, &J, 1, N, nb * 4, Mt, S, st, w.slA[0], w.slB[0], w.expA[0], w.expB[0], nullptr, reuse));
     TRYC(nspt_fft_inv_df(w.spC, c, T1, E, t, nb * 4, Mt, 0, log2r, st));
     return NSPT_OK;
   };
@@ -969,7 +980,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   for (int k = 2; k <= sb; ++k) {
     double2* Pk = w.serTmp + (k - 2) * ser4;
     TRYC(cudaMemsetAsync(Pk, 0, (size_t)ser4 * sizeof(double2), st));  // orders below k stay 0
-    TRYS(star_t(Ysrc + E, Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k));
+    TRYS(star_t(Ysrc + E, nspt_ps_power_ta(T, sb, k), Yp[k - 1] + (k - 1) * E, Pk + k * E, T - k));
     Yp[k] = Pk;
   }
   double2* prod = w.serTmp + (sb - 1) * ser4;  // the slot after the powers Y^2..Y^s
@@ -989,7 +1000,7 @@ int nspt_split_langevin(int N, int T, int nb, int M, int S, double2* U, const do
   TRYC(nspt_ps_combine(Qs[0], block(r), sb - 1, nullptr, sb, T - sb * r, T, N, ns, st));
   for (int j = r - 1; j >= 0; --j) {
     const int t = T - sb * (j + 1);
-    TRYS(star_t(Yp[sb] + sb * E, Qs[cur], prod, t));  // (Y^s Q_{j+1}) from order s
+    TRYS(star_t(Yp[sb] + sb * E, nspt_ps_horner_ta(T, sb, j), Qs[cur], prod, t));  // (Y^s Q_{j+1}) from order s
     TRYC(nspt_ps_combine(Qs[cur ^ 1], block(j), sb - 1, prod, sb, T - sb * j, T, N, ns, st));
     cur ^= 1;
   }

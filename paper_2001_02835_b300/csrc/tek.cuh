@@ -33,6 +33,24 @@ inline int nspt_ps_block(int T) {
     if (nspt_ps_cost(T, s) < nspt_ps_cost(T, best)) best = s;
   return best;
 }
+// Truncation to read the left operand of a Paterson-Stockmeyer product at: the largest
+// truncation among the products of the same phase that share its transform length, so that
+// one transform of the operand serves them all.  Powers: Y^k = Y * Y^(k-1) to order T - k
+// (k = 2..s); Horner: Y^s Q_{j+1} to order T - s (j + 1) (j = T/s - 1 .. 0).
+inline int nspt_ps_power_ta(int T, int s, int k) {
+  const int M = nspt_pow2_at_least(2 * (T - k + 1));
+  int ta = T - k;
+  for (int k2 = 2; k2 <= s; ++k2)
+    if (nspt_pow2_at_least(2 * (T - k2 + 1)) == M && T - k2 > ta) ta = T - k2;
+  return ta;
+}
+inline int nspt_ps_horner_ta(int T, int s, int j) {
+  const int M = nspt_pow2_at_least(2 * (T - s * (j + 1) + 1));
+  int ta = T - s * (j + 1);
+  for (int j2 = T / s - 1; j2 >= 0; --j2)
+    if (nspt_pow2_at_least(2 * (T - s * (j2 + 1) + 1)) == M && T - s * (j2 + 1) > ta) ta = T - s * (j2 + 1);
+  return ta;
+}
 // temporary link-series slots (units of batch x (T+1) x N^2 entries) of a step's workspace:
 // 18 for the staple pipeline, reused by exp_star for 4 per power Y^2..Y^s plus 4 for the
 // Horner product
