@@ -52,10 +52,14 @@ def main(argv=None):
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
         fn = lambda: nspt.tek_wilson_loops(U, 1, a.amax, **kw)  # noqa: E731
     elif a.op == "md":
+        # from the twisted vacuum with momenta of variance 1/N, the rescale fitted per phase
+        # (Gaussian link orders are not a unitary series and blow up under MD)
         L = int(round(a.N ** 0.5))
-        U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
+        U = torch.from_numpy(np.ascontiguousarray(syn.vacuum_links(L, 1, a.T, a.batch))).cuda()
         P = torch.zeros_like(U)
-        eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
+        eta = torch.from_numpy(np.ascontiguousarray(syn.md_momenta(g, a.N, a.batch))).cuda()
+        if a.algo == "fft":
+            kw["rescale_log2r"] = nspt.RESCALE_AUTO
         fn = lambda: nspt.tek_md_trajectory(U, P, 1, 0.02, a.md_steps, eta=eta, **kw)  # noqa: E731
     else:
         A = torch.from_numpy(syn.series_batch(g, a.N, a.T, a.batch)).cuda()
