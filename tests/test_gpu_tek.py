@@ -20,7 +20,9 @@ def nspt():
 
 
 @pytest.mark.parametrize("algo,prec", [("naive", "fp64"), ("fft", "fp64"), ("fft", "split")])
-@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 8, 1), (3, 1, 2, 2), (2, 1, 5, 1), (5, 2, 4, 2)])
+@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 8, 1), (3, 1, 2, 2), (2, 1, 5, 1), (5, 2, 4, 2),
+                                               # exp_star blocks of 5 (T = 40) and 8 (T = 63) powers
+                                               (2, 1, 40, 1), (2, 1, 63, 1)])
 def test_langevin_step_matches_oracle(nspt, algo, prec, L, flux, T, streams):
     g = syn.rng(syn.SEED_BASE + 10 * L + T)
     N = L * L
