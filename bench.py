@@ -123,6 +123,50 @@ def time_oracle_products(N, T, nprod, seed):
     return time.perf_counter() - t0
 
 
+def time_oracle_naive(N, T, nprod, seed):
+    """Wall time of the oracle's naive product (Eq. 5 loops) on `nprod` products."""
+    from oracle import polymat as pm
+    A, B = inputs(N, T, nprod, seed)
+    t0 = time.perf_counter()
+    pm.star(A, B)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(N, T, M):
+    """The oracle as it stands on the host cores, bounded samples: the workload's FFT-CONV on
+    all cores (whole batches until about 10 s, at most 30 s) and on one core (one product),
+    and the naive form (Eq. 5) at the correctness size SU(9), O(g^8), batch 4 and at the
+    paper's timing point SU(225), O(g^31) (one product), on all cores."""
+    done, tcpu = 0, 0.0
+    while tcpu < 10.0 and done < 64:
+        tcpu += time_oracle_products(N, T, BATCH, syn.SEED_BASE + 2)
+        done += BATCH
+        if tcpu > 30.0:
+            break
+    cores = oracle_threads()
+    out = {"value": done / tcpu, "unit": "products/s", "cores": cores, "kind": "oracle",
+           "sample": "%d products (N=%d, T=%d, M=%d) by the numpy FP64 oracle's direct-DFT FFT-CONV on %s"
+                     % (done, N, T, M, cpu_model())}
+    try:
+        from threadpoolctl import threadpool_limits
+        with threadpool_limits(limits=1):
+            t1 = time_oracle_products(N, T, 1, syn.SEED_BASE + 2)
+        out["single_core"] = {"value": 1.0 / t1, "unit": "products/s", "cores": 1,
+                              "sample": "1 product (N=%d, T=%d), direct-DFT FFT-CONV" % (N, T)}
+    except ImportError:  # pragma: no cover
+        out["single_core"] = None
+    t0 = time_oracle_naive(9, 8, BATCH, syn.SEED_BASE)
+    out["naive_su9_T8"] = {"value": BATCH / t0, "unit": "products/s", "cores": cores,
+                           "sample": "batch of 4 products (N=9, T=8), Eq. 5 loops"}
+    tn = time_oracle_naive(225, 31, 1, syn.SEED_BASE + 1)
+    out["naive_su225_T31"] = {"value": 1.0 / tn, "unit": "products/s", "cores": cores,
+                              "sample": "1 product (N=225, T=31), Eq. 5 loops"}
+    tf = time_oracle_products(225, 31, BATCH, syn.SEED_BASE + 1)
+    out["dftconv_su225_T31"] = {"value": BATCH / tf, "unit": "products/s", "cores": cores,
+                                "sample": "batch of 4 products (N=225, T=31), direct-DFT FFT-CONV"}
+    return out
+
+
 def cpu_model():
     try:
         for line in open("/proc/cpuinfo"):
@@ -133,11 +177,12 @@ def cpu_model():
     return "unknown"
 
 
-def arm_config(N, T, prec, ngpu, note):
-    """The workload both arms report (the same config object; `note` says how it ran)."""
+def arm_config(N, T, prec, ngpu, note, who="libnspt"):
+    """The workload both arms report (the same sizes; `prec` and `who` say which arithmetic and
+    which program ran it, `note` how)."""
     M = 1 << (2 * (T + 1) - 1).bit_length()
-    return {"workload": "SU(%d) O(g^%d) FFT-CONV M=%d batch %d, %s form" % (N, T, M, BATCH, prec),
-            "N": N, "T": T, "M": M, "batch_per_gpu": BATCH, "prec": prec,
+    return {"workload": "SU(%d) O(g^%d) FFT-CONV M=%d batch %d" % (N, T, M, BATCH),
+            "N": N, "T": T, "M": M, "batch_per_gpu": BATCH, "prec": prec, "program": who,
             "parallelism": "replicas" if ngpu > 1 else "single", "l2": note}
 
 
@@ -158,8 +203,9 @@ def run_reference(args):
         "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-        "config": arm_config(N, T, args.prec or "split", args.gpus,
-                             "oracle's direct-DFT FFT-CONV in FP64 on the host cores, the whole batch per step"),
+        "config": arm_config(N, T, "fp64", args.gpus,
+                             "oracle's direct-DFT FFT-CONV in FP64 on the host cores, the whole batch per step",
+                             who="numpy FP64 oracle"),
         "cpu_baseline": {"value": value, "unit": "products/s", "cores": cores, "kind": "oracle",
                          "sample": "batch of 4 products (N=%d, T=%d) per step, numpy FP64 oracle, %s"
                                    % (N, T, cpu_model())},
@@ -348,6 +394,30 @@ def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     return out
 
 
+def per_order_vs_oracle(torch, nspt, A, B, dA, dB, dC, T, barrier, extras):
+    """Per-order relative errors of the split form (S = 5, 6) and the FP64 form against the
+    oracle's FFT-CONV (Sec. 2 Steps 1-5, direct DFTs in FP64) on the bench's own inputs, and
+    the split forms' speed."""
+    from oracle import polymat as pm
+    ref = pm.star_dftconv(A, B)
+    den = np.sqrt(np.sum(np.abs(ref) ** 2, axis=(-1, -2)))
+
+    def errs(C):
+        num = np.sqrt(np.sum(np.abs(C - ref) ** 2, axis=(-1, -2)))
+        return (num / np.where(den == 0, 1.0, den)).max(axis=0)
+
+    out = {"oracle": "numpy FP64 direct-DFT FFT-CONV of the same batch",
+           "fp64_form": [float("%.3g" % x) for x in errs(nspt.polymat_mul(dA, dB, algo="fft", prec="fp64").cpu().numpy())]}
+    for S in (5, 6):
+        kwS = dict(algo="fft", prec="split", slices=S)
+        msS = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kwS), 5, 1, barrier) / 5
+        e = errs(dC.cpu().numpy())
+        out["split_S%d" % S] = [float("%.3g" % x) for x in e]
+        extras["split_S%d_T%d" % (S, T)] = {"products_per_s": BATCH / (msS * 1e-3), "ms_per_step": msS,
+                                            "max_per_order_rel_err_vs_oracle": float(e.max())}
+    return out
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -434,18 +504,24 @@ def run_ours(args):
         pairs = slices * (slices + 1) // 2
         launches_per_step = max(1, dom_n // args.steps)
         modes = M * BATCH / launches_per_step
-        # algorithmic work: per mode, the triangle of slice pairs i + j < S, each a complex
-        # N x N x N product = 4 real products of 2 N^3 flops (tile padding not counted)
-        flops = pairs * 4 * 2.0 * N ** 3 * modes
+        # algorithmic work of the method (Step 3): one complex N x N x N product per mode,
+        # 8 N^3 flops; the split's slice pairs and the tile padding are overhead, not work
+        flops = 8.0 * N ** 3 * modes
         achieved = flops / (per_launch_ms * 1e-3) / 1e12
+        # what the tensor cores issue: per mode S(S+1)/2 slice pairs x 4 real products of
+        # 2 N^3 flops (unpadded N), the issued-MMA efficiency of the kernel
+        issued = pairs * 4 * 2.0 * N ** 3 * modes / (per_launch_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
         tpm = gemm_traffic_per_mode(N, slices)
         roof = {"kernel": dom_name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": (tpm * modes if tpm else None),
+                "work": "8 N^3 per mode (Step 3), N=%d, %d modes per launch" % (N, int(modes)),
                 "traffic_source": "profiles/traffic.json (small-case capture scaled per mode)" if tpm else None,
                 "peak_source": "%s bf16_tflops_sustained (of %s)" % (peak_kind, peak_kind),
-                # the same work against the short-burst GEMM peak (taken at full clocks)
-                "frac_of_burst": achieved / peaks["bf16_tflops"]}
+                "frac_of_burst": achieved / peaks["bf16_tflops"],
+                "issued_mma": {"tflops": issued, "frac_of_sustained": issued / peak,
+                               "frac_of_burst": issued / peaks["bf16_tflops"],
+                               "work": "S(S+1)/2 = %d slice pairs x 4 real products x 2 N^3 per mode" % pairs}}
     elif dom_name in ("gemm_mode", "gemm_conv"):
         f64 = fp64_peak_tflops(torch)
         flops = 8.0 * N ** 3 * M * BATCH / max(1, dom_n // args.steps)
@@ -466,17 +542,11 @@ def run_ours(args):
             kw64 = dict(algo="fft", prec="fp64")
             ms64 = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kw64), 3, 1, barrier)
             extras["fp64_fft_T%d" % T] = {"products_per_s": BATCH * 3 / (ms64 * 1e-3), "ms_per_step": ms64 / 3}
-            # accuracy against speed: the split form with 5 and 6 slices, per-order relative error
-            # (Frobenius) against the FP64 form on the same inputs
-            ref64 = nspt.polymat_mul(dA, dB, algo="fft", prec="fp64")
-            den = torch.linalg.matrix_norm(ref64).clamp_min(1e-300)
-            for S in (5, 6):
-                kwS = dict(algo="fft", prec="split", slices=S)
-                msS = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kwS), 5, 1, barrier) / 5
-                err = (torch.linalg.matrix_norm(dC - ref64) / den).max().item()
-                extras["split_S%d_T%d" % (S, T)] = {"products_per_s": BATCH / (msS * 1e-3), "ms_per_step": msS,
-                                                    "max_per_order_rel_err_vs_fp64": err}
-            del ref64, den
+            # accuracy against speed: the split form with 5 and 6 slices and the FP64 form,
+            # per-order relative error (Frobenius, max over the batch) against the FP64 oracle's
+            # FFT-CONV of the same inputs, computed on the host cores
+            extras["per_order_err_vs_oracle"] = per_order_vs_oracle(torch, nspt, A, B, dA, dB, dC, T, barrier,
+                                                                    extras)
         A31, B31 = inputs(N, 31, BATCH, syn.SEED_BASE + 1)
         a31, b31 = torch.from_numpy(A31).cuda(), torch.from_numpy(B31).cuda()
         c31 = torch.empty_like(a31)
@@ -501,24 +571,15 @@ def run_ours(args):
 
     cpu = None
     if rank == 0:
-        # bounded sample: whole batches of the workload through the oracle on the
-        # host cores, repeated until about 10 s of CPU time (at most 30 s)
-        done, tcpu = 0, 0.0
-        while tcpu < 10.0 and done < 64:
-            tcpu += time_oracle_products(N, T, BATCH, syn.SEED_BASE + 2)
-            done += BATCH
-            if tcpu > 30.0:
-                break
-        cpu = {"value": done / tcpu, "unit": "products/s", "cores": oracle_threads(), "kind": "oracle",
-               "sample": "%d products (N=%d, T=%d, M=%d) by the numpy FP64 oracle's direct-DFT FFT-CONV on %s"
-                         % (done, N, T, M, cpu_model())}
+        cpu = cpu_baseline(N, T, M)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "products/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "c128 in/out; " + ("bf16 slices x6, fp32 exact partials" if prec == "split" else "f64"),
+            "dtype": "c128 in/out; " + ("double-float (f32 pair) order transforms, bf16 digit slices x6, "
+                                        "fp32 exact digit-group partials" if prec == "split" else "f64"),
             "data": "synthetic (Haar SU(N) order 0, Gaussian var 1/N orders >= 1, seed 200102837)",
             "config": arm_config(N, T, prec, ws, "inputs 2 x %.0f MB > 126 MB L2, no flush" % (nbytes / 1e6)),
             "eff_tflops": fft_flops(N, M) * value / 1e12,

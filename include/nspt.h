@@ -331,7 +331,9 @@ NSPT_API int nspt_split_mode_gemm(const void* slA, const void* slB, const int* e
  * holds until the process exits; larger problems return NSPT_ERR_WORKSPACE.
  *   A, B : [batch][T+1][N][N] complex128 device inputs;  C : output, no overlap.
  * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  All calls
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture.  A device reset (cudaDeviceReset) between
+ * calls is not supported: the kept address would no longer be valid.  All calls
  * share the one array, which keeps the last call's contents (each call
  * overwrites every entry it reads): calls that can overlap on the GPU -- on
  * different streams without ordering -- race and must not be issued.

@@ -146,19 +146,3 @@ def order_rel_error(X, ref) -> np.ndarray:
     num = np.sqrt(np.sum(np.abs(X - ref) ** 2, axis=(-1, -2)))
     den = np.sqrt(np.sum(np.abs(ref) ** 2, axis=(-1, -2)))
     return num / np.where(den == 0, 1.0, den)
-
-
-def star_entries(A, B, idx) -> np.ndarray:
-    """Selected entries of A star B straight from Eq. 5:
-    C[b, k, i, j] = sum_{l=0}^{k} sum_m A[b, l, i, m] B[b, k-l, m, j]
-    for each (b, k, i, j) in idx (for sampled checks at sizes where the full
-    oracle product is too slow)."""
-    A = np.asarray(A)
-    B = np.asarray(B)
-    out = np.empty(len(idx), np.complex128)
-    for n, (b, k, i, j) in enumerate(idx):
-        acc = 0j
-        for l in range(k + 1):
-            acc += np.dot(A[b, l, i, :], B[b, k - l, :, j])
-        out[n] = acc
-    return out

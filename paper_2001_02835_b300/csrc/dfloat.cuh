@@ -17,14 +17,18 @@ struct cdf {
   dfl re, im;
 };
 
+// The steps whose rounding the error-free transformations rely on are written
+// with __fadd_rn / __fsub_rn / __fmul_rn, which the compiler never contracts
+// into an FMA: TwoSum needs s = fl(a + b) exactly, and the FMA residual of a
+// product needs p = fl(a * b), whatever the surrounding expressions are.
 __device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 __device__ __forceinline__ dfl df_fast(float s, float e) {
-  const float h = s + e;
-  return dfl{h, e - (h - s)};
+  const float h = __fadd_rn(s, e);
+  return dfl{h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 __device__ __forceinline__ dfl df_add(dfl a, dfl b) {
   float s, e;
@@ -60,8 +64,8 @@ __device__ __forceinline__ cdf cdf_sub(cdf a, cdf b) { return cdf{df_sub(a.re, b
 // the high products cancel.  For results that only feed further sums.
 __device__ __forceinline__ cdf cdf_mul_lazy(cdf a, dfl c, dfl s) {
   // re = a.re c - a.im s
-  float p1 = a.re.h * c.h, e1 = fmaf(a.re.h, c.h, -p1);
-  float p2 = a.im.h * s.h, e2 = fmaf(a.im.h, s.h, -p2);
+  float p1 = __fmul_rn(a.re.h, c.h), e1 = fmaf(a.re.h, c.h, -p1);
+  float p2 = __fmul_rn(a.im.h, s.h), e2 = fmaf(a.im.h, s.h, -p2);
   float sr, e3;
   df_two_sum(p1, -p2, sr, e3);
   float lo = (e1 - e2) + e3;
@@ -70,8 +74,8 @@ __device__ __forceinline__ cdf cdf_mul_lazy(cdf a, dfl c, dfl s) {
   lo = fmaf(-a.im.h, s.l, lo);
   lo = fmaf(-a.im.l, s.h, lo);
   // im = a.re s + a.im c
-  float q1 = a.re.h * s.h, f1 = fmaf(a.re.h, s.h, -q1);
-  float q2 = a.im.h * c.h, f2 = fmaf(a.im.h, c.h, -q2);
+  float q1 = __fmul_rn(a.re.h, s.h), f1 = fmaf(a.re.h, s.h, -q1);
+  float q2 = __fmul_rn(a.im.h, c.h), f2 = fmaf(a.im.h, c.h, -q2);
   float si, f3;
   df_two_sum(q1, q2, si, f3);
   float lo2 = (f1 + f2) + f3;

@@ -52,10 +52,10 @@ __device__ __forceinline__ void to_digits(dfl x, int e, float (&s)[S]) {
   const float lo = (x.l * f1) * f2;
 #pragma unroll
   for (int i = 0; i < S; ++i) {
-    if (i == 3) v = v + lo;
+    if (i == 3) v = __fadd_rn(v, lo);
     const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
-    const float t = (v + sig) - sig;
-    v = v - t;
+    const float t = __fsub_rn(__fadd_rn(v, sig), sig);   // rounding to the digit grid
+    v = __fsub_rn(v, t);
     s[i] = t * 128.f;
   }
 }

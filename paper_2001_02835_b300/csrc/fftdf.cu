@@ -71,7 +71,7 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
 // in: [batch][M][E] float4 spectrum; out: FP64 orders 0..T at out + b*out_stride*E,
 // row k scaled by 2^(log2u - k*log2r) / M
 __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
-  const float p = a.h * b.h;
+  const float p = __fmul_rn(a.h, b.h);
   float e = fmaf(a.h, b.h, -p);
   e = fmaf(a.h, b.l, e);
   e = fmaf(a.l, b.h, e);

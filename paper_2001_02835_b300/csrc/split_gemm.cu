@@ -393,7 +393,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
         for (int c = 0; c < BN; ++c) {
           const int n = nb + c;
           if (!mvalid || n >= N) continue;
-          const float h = s_[c] + e_[c], l = e_[c] - (h - s_[c]);
+          const float h = __fadd_rn(s_[c], e_[c]), l = __fsub_rn(e_[c], __fsub_rn(h, s_[c]));  // FastTwoSum
           const float f = out_scale(__ldg(expB + n));
           reinterpret_cast<float2*>(crow + n)[half] = make_float2(h * f, l * f);
         }
@@ -439,8 +439,8 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       for (int c = 0; c < HALF; ++c) {
         const int n = n0 + c;
         if (!mvalid || n >= N) continue;
-        const float rh = sr[c] + er[c], rl = er[c] - (rh - sr[c]);
-        const float ih = si[c] + ei[c], il = ei[c] - (ih - si[c]);
+        const float rh = __fadd_rn(sr[c], er[c]), rl = __fsub_rn(er[c], __fsub_rn(rh, sr[c]));
+        const float ih = __fadd_rn(si[c], ei[c]), il = __fsub_rn(ei[c], __fsub_rn(ih, si[c]));
         const float f = out_scale(__ldg(expB + n));
         if (plain) {
           crow[n] = make_float4(rh * f, rl * f, ih * f, il * f);

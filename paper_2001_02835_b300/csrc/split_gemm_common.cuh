@@ -66,11 +66,12 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, volatil
   return true;
 }
 
-// error-free sum of two floats (Knuth's TwoSum)
+// error-free sum of two floats (Knuth's TwoSum); the _rn intrinsics keep the
+// compiler from contracting any step into an FMA with a neighbouring product
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
 __device__ __forceinline__ float pow2f(int k) {
@@ -85,8 +86,8 @@ __device__ __forceinline__ void df_sum(const float (&a)[NGROUPS], float& hi, flo
   two_sum(h, a[2], s2, e2);
   two_sum(s2, a[3], s3, e3);
   const float l = ((e1 + e2) + e3) + a[4];
-  hi = s3 + l;
-  lo = l - (hi - s3);
+  hi = __fadd_rn(s3, l);
+  lo = __fsub_rn(l, __fsub_rn(hi, s3));
 }
 
 

@@ -1,6 +1,6 @@
 """Runs one library entry point repeatedly on synthetic inputs of a given size.
 
-    python -m paper_2001_02835_b300.run_case --op mul --algo fft --prec split --N 225 --T 15 --batch 4 --reps 3
+    python run_case.py --op mul --algo fft --prec split --N 225 --T 15 --batch 4 --reps 3
 
 Used for profiling single calls (e.g. under ncu) and quick timing; every call
 is a complete call of the entry point.  Prints the mean CUDA-event time per
@@ -15,7 +15,7 @@ import sys
 import numpy as np
 import torch
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -4,8 +4,8 @@ table: SU(N) for N in {121, 169, 225, 289}, truncation orders 15, 31, 63, trajec
 plus 40 leapfrog steps, split form) split into its force and link-update phases, and the
 split FFT-CONV product rate at batch 4.  Prints a markdown table.
 
-    python -m paper_2001_02835_b300.sweep [--N 121,169,225,289] [--T 15,31,63] [--md-steps 40]
-    python -m paper_2001_02835_b300.sweep --accuracy    # per-order accuracy from the vacuum
+    python sweep.py [--N 121,169,225,289] [--T 15,31,63] [--md-steps 40]
+    python sweep.py --accuracy    # per-order accuracy from the vacuum
 
 Each configuration starts at the twisted vacuum (twist eaters at order 0, higher orders
 zero) with seeded momenta of variance 1/N; one untimed trajectory thermalises it, then the
@@ -22,7 +22,7 @@ import sys
 import numpy as np
 import torch
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 

@@ -84,7 +84,7 @@ def test_paper_parameter_table_axes():
             assert pm.default_fft_len(t) == 2 * (t + 1)
         for n in ns:  # SU(N) with N = L^2 (the TEK lattice extent L)
             assert int(round(n ** 0.5)) ** 2 == n
-    from paper_2001_02835_b300 import sweep
+    import sweep
     a = sweep.parser().parse_args([])
     steps, ns, ts = table["GPU(FFT-CONV)"]
     assert a.md_steps == steps

@@ -10,7 +10,7 @@ import nspt_synth as syn
 from oracle import polymat as pm
 from oracle import tek
 
-from tests.gpu_util import dev, host
+from tests.gpu_util import dev, host, record, split_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +33,9 @@ def test_product_is_associative(nspt, algo, prec):
     right = nspt.polymat_mul(A, nspt.polymat_mul(B, C, algo=algo, prec=prec), algo=algo, prec=prec)
     den = torch.linalg.matrix_norm(left).clamp_min(1e-300)
     err = (torch.linalg.matrix_norm(left - right) / den).max().item()
-    assert err <= (1e-12 if prec == "fp64" else 1e-11)
+    record("associativity", algo=algo, prec=prec, err=err)
+    # four products, each within the per-product bound
+    assert err <= (1e-12 if prec == "fp64" else 4 * split_bound(6)), err
 
 
 @pytest.mark.parametrize("algo,prec", FORMS)
@@ -46,7 +48,9 @@ def test_one_by_one_series_are_scalar_polynomials(nspt, algo, prec):
                               algo=algo, prec=prec)).reshape(batch, T + 1)
     for i in range(batch):
         ref = np.polynomial.polynomial.polymul(a[i], b[i])[:T + 1]
-        assert np.abs(C[i] - ref).max() <= (1e-12 if prec == "fp64" else 1e-11) * np.abs(ref).max()
+        err = np.abs(C[i] - ref).max() / np.abs(ref).max()
+        record("one_by_one", algo=algo, prec=prec, err=err)
+        assert err <= (1e-12 if prec == "fp64" else split_bound(6)), err
 
 
 def _unitary_links(rg, L, k, T, streams):
@@ -80,11 +84,15 @@ def test_langevin_and_md_keep_links_unitary(nspt, algo, prec):
     U = dev(_unitary_links(rg, L, k, T, streams))
     assert _unitarity_defect(nspt, U) < 1e-12
     eta = dev(np.ascontiguousarray(syn.hermitian_noise(rg, N, 4 * streams).reshape(streams, 4, N, N)))
-    tol = 1e-12 if prec == "fp64" else 1e-10
+    tol = 1e-12 if prec == "fp64" else split_bound(6, "langevin", T)
     U1 = U.clone()
     nspt.tek_langevin_step(U1, eta, k, 0.05, algo=algo, prec=prec)
-    assert _unitarity_defect(nspt, U1) < tol
+    d1 = _unitarity_defect(nspt, U1)
+    record("unitarity_langevin", algo=algo, prec=prec, defect=d1)
+    assert d1 < tol, d1
     assert (U1 - U).abs().max().item() > 1e-3
     P = torch.zeros_like(U)
     nspt.tek_md_trajectory(U1, P, k, 0.05, 5, eta=eta, algo=algo, prec=prec)
-    assert _unitarity_defect(nspt, U1) < 5 * tol
+    d2 = _unitarity_defect(nspt, U1)
+    record("unitarity_md", algo=algo, prec=prec, defect=d2)
+    assert d2 < 5 * tol, d2

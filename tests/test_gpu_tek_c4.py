@@ -11,7 +11,11 @@ order is F^(k) = -[(Y^(k) + Y^(k)^H)/2]_traceless.  At SU(121), T = 31, flux 3,
 drift against the library's staple-based drift, against the oracle's drift on
 one stream, against central finite differences (h = 1e-6) through the GPU
 forward, and then runs a full Langevin step composed from library products on
-the backward-derived drift against nspt_tek_langevin_step.
+the backward-derived drift against nspt_tek_langevin_step.  The library's step
+itself (FP64 and split forms) is compared with the oracle's step on one stream.
+
+Orders are compared one by one (relative Frobenius error); the drift's order 0,
+zero to rounding at the twisted vacuum, is compared against the largest order.
 """
 import math
 
@@ -22,7 +26,7 @@ import torch
 import nspt_synth as syn
 from oracle import tek
 
-from tests.gpu_util import dev, host
+from tests.gpu_util import dev, host, max_order_rel, record, split_bound
 
 pytestmark = pytest.mark.gpu
 L_SIDE, FLUX, T, STREAMS, EPS = 11, 3, 31, 8, 0.01
@@ -74,10 +78,13 @@ def drift_from_backward(nspt, U, z):
 
 
 def per_order_err(A, B):
-    """max over (stream, link, order) of ||A - B||_F / max(||B||_F, 1e-3 * max ||B||_F)."""
-    num = torch.linalg.matrix_norm(A - B).cpu().numpy()
-    den = torch.linalg.matrix_norm(B).cpu().numpy()
-    return float(np.max(num / np.maximum(den, 1e-3 * den.max())))
+    """max over (stream, link, order >= 1) of ||A - B||_F / ||B||_F, and for order 0 (zero to
+    rounding at the vacuum) ||A - B||_F over the largest order's ||B||_F."""
+    A = A.cpu().numpy() if torch.is_tensor(A) else np.asarray(A)
+    B = B.cpu().numpy() if torch.is_tensor(B) else np.asarray(B)
+    scale = np.sqrt(np.sum(np.abs(B) ** 2, axis=(-1, -2))).max()
+    e0 = np.sqrt(np.sum(np.abs(A[..., 0, :, :] - B[..., 0, :, :]) ** 2, axis=(-1, -2))).max() / scale
+    return max(max_order_rel(A[..., 1:, :, :], B[..., 1:, :, :]), float(e0))
 
 
 @pytest.fixture(scope="module")
@@ -152,18 +159,44 @@ def test_langevin_step_with_backward_drift(nspt, c4):
     Uc = nspt.polymat_mul(R, Uf, algo="fft").reshape(tU.shape)
     U1 = tU.clone()
     nspt.tek_langevin_step(U1, eta, FLUX, EPS, algo="fft")
-    assert per_order_err(Uc[:, :, 1:], U1[:, :, 1:]) <= 1e-10
+    assert max_order_rel(host(Uc), host(U1)) <= 1e-10
     assert torch.equal(U1[:, :, 0], tU[:, :, 0])
 
 
 def test_split_langevin_step_matches_fp64_form(nspt, c4):
     """The split-precision Langevin step (tensor-core staples and exp_star) against the FP64
-    form at SU(121), O(g^31), 8 streams; stated bound 2^10 sqrt(N) (2^-47 + 2^-44)."""
+    form at SU(121), O(g^31), 8 streams, within the stated split bound; 5 slices fail it."""
     eta = dev(c4["eta"])
-    U64, Us = c4["tU"].clone(), c4["tU"].clone()
+    U64, Us, U5 = c4["tU"].clone(), c4["tU"].clone(), c4["tU"].clone()
     _, F64 = nspt.tek_langevin_step(U64, eta, FLUX, EPS, want_drift=True, algo="fft", prec="fp64")
     _, Fs = nspt.tek_langevin_step(Us, eta, FLUX, EPS, want_drift=True, algo="fft", prec="split")
-    tol = 2.0 ** 10 * math.sqrt(N) * (2.0 ** -47 + 2.0 ** -44)
-    assert per_order_err(Fs, F64) <= tol
-    assert per_order_err(Us[:, :, 1:], U64[:, :, 1:]) <= tol
+    _, F5 = nspt.tek_langevin_step(U5, eta, FLUX, EPS, want_drift=True, algo="fft", prec="split", slices=5)
+    tol = split_bound(6, "langevin", T)
+    eF, eU = per_order_err(Fs, F64), max_order_rel(host(Us), host(U64))
+    e5 = max(per_order_err(F5, F64), max_order_rel(host(U5), host(U64)))
+    record("c4_split_vs_fp64", errF=eF, errU=eU, err_S5=e5)
+    assert eF <= tol, eF
+    assert eU <= tol, eU
+    assert e5 > tol, e5
     assert torch.equal(Us[:, :, 0], c4["tU"][:, :, 0])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_langevin_step_matches_oracle_one_stream(nspt, c4, prec):
+    """The library's Langevin step at SU(121), O(g^31), flux 3 against the oracle's step
+    (Eqs. 1-3, Taylor exp_star, Eq. 5 products) on stream 0: updated links and drift per
+    order, within 1e-12 (FP64 form) or the stated split bound."""
+    ref = c4.get("oracle_step")
+    if ref is None:
+        ref = tek.langevin_step(c4["U"][0], c4["eta"][0], c4["z"], EPS)
+        c4["oracle_step"] = ref
+    refU, refF = ref
+    tU = c4["tU"][:1].clone()
+    _, F = nspt.tek_langevin_step(tU, dev(c4["eta"][:1]), FLUX, EPS, want_drift=True, algo="fft", prec=prec)
+    eU = max_order_rel(host(tU)[0], refU)
+    eF = per_order_err(host(F)[0], refF)
+    record("c4_vs_oracle", prec=prec, errU=eU, errF=eF)
+    tol = 1e-12 if prec == "fp64" else split_bound(6, "langevin", T)
+    assert eU <= tol, eU
+    assert eF <= tol, eF
+    np.testing.assert_array_equal(host(tU)[0][:, 0], c4["U"][0][:, 0])

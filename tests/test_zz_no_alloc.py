@@ -6,8 +6,9 @@ plug-in hosts that hand over only the input and output buffers.  For them the
 library keeps the product's scratch (the three spectra) in one fixed device
 array of 32 MiB.  These tests call that entry point through the C ABI twice in
 a row and check both results against nspt_polymat_mul (FFT, FP64) and the
-oracle with the FP64-form tolerance, and check that a problem too large for the
-fixed scratch is refused.  The file is collected last so that a run stopping
+oracle with the FP64-form tolerance, run one problem whose spectra fill the
+fixed scratch to within about 1% (where a layout or rounding slip would write
+past the array), and check that the next larger problem is refused.  The file is collected last so that a run stopping
 at the first failure has already run every other test.
 """
 import ctypes
@@ -64,3 +65,27 @@ def test_noalloc_refuses_problems_beyond_its_scratch(nspt):
                                         torch.cuda.current_stream().cuda_stream)
     assert rc == -4 and b"too small" in L.nspt_status_string(rc)
     assert L.nspt_polymat_mul_fft_noalloc(None, None, None, 4, 3, 1, None) == -1
+
+
+def test_noalloc_problem_that_nearly_fills_its_scratch(nspt):
+    """3 * round256(batch * M * N^2 * 16) <= 32 MiB: at T = 15 (M = 32), batch 1, N = 147 uses
+    33,191,424 of 33,554,432 bytes and is computed correctly; N = 148 (33,644,544 bytes) is
+    refused before any launch."""
+    L = nspt.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    N, T = 147, 15
+    assert 3 * (32 * N * N * 16) <= 32 << 20 < 3 * (32 * (N + 1) ** 2 * 16)
+    g = syn.rng(9200)
+    A = syn.series_batch(g, N, T, 1)
+    B = syn.series_batch(g, N, T, 1)
+    dA, dB = dev(A), dev(B)
+    C = torch.full_like(dA, float("nan"))
+    rc = L.nspt_polymat_mul_fft_noalloc(dA.data_ptr(), dB.data_ptr(), C.data_ptr(), N, T, 1, stream)
+    assert rc == 0, L.nspt_status_string(rc)
+    got = host(C)
+    assert max_order_rel(got, pm.star(A, B)) <= TOL
+    assert max_order_rel(got, host(nspt.polymat_mul(dA, dB, algo="fft", prec="fp64"))) <= TOL
+    big = torch.zeros((1, T + 1, N + 1, N + 1), dtype=torch.complex128, device="cuda")
+    big2, big3 = torch.zeros_like(big), torch.zeros_like(big)
+    rc = L.nspt_polymat_mul_fft_noalloc(big.data_ptr(), big2.data_ptr(), big3.data_ptr(), N + 1, T, 1, stream)
+    assert rc == -4
