@@ -20,8 +20,9 @@ Chained computations (the Langevin step, MD, the Wilson loops) mix the orders in
 product of the chain, and their error grows with the truncation order beyond T ~ 24 in
 the FP64 FFT form as much as in the split form (the split/FP64 error ratio stays near
 100 at every T); the bound for them is CHAIN[kind] * 2^max(0, (T - 24)/8) times the
-product bound, with CHAIN calibrated the same way (largest observed ratio 0.42 for the
-Langevin step, 0.35 for MD, 2.4 for the Wilson loops at SU(121), O(g^31)).
+product bound, with CHAIN calibrated the same way (largest observed ratio to the product
+bound 0.42 for the Langevin step and 0.38 for MD at SU(121), O(g^31), 2.4 for the Wilson
+loops there).
 """
 import json
 import os
