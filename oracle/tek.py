@@ -18,6 +18,10 @@ functions fix (each pinned by a test):
 * Langevin step (Euler-Maruyama in the rescaled time):
   X^(0) = 0, X^(1) = eps F^(1) + sqrt(2 eps) eta, X^(k>=2) = eps F^(k),
   U' = exp_star(i X) star U; order 0 of U is left unchanged;
+* unitarity projection (the paper names a unitarity projection among the NSPT
+  steps but prints no algorithm): the polar factor of the series in the
+  truncated ring, V = U * (U^+ * U)^(-1/2), with order 0 (unitary) kept as it is;
+  see ``unitarize``;
 * Wilson loops: W(a, b) = 1/(12 N) sum over ordered planes of
   z_{mu nu}^(ab) Tr[U_mu^a U_nu^b (U_mu^a)^+ (U_nu^b)^+] (the paper measures Wilson
   loops but does not restate their definition; the z^(ab) factor makes the
@@ -190,3 +194,34 @@ def wilson_loops(U, z, amax: int) -> np.ndarray:
                     X = pm.star(pm.star(pm.star(A, B), pm.dagger(A)), pm.dagger(B))
                     W[..., a - 1, b - 1, :] += z[mu, nu] ** (a * b) * np.trace(X, axis1=-2, axis2=-1)
     return W / (12 * N)
+
+
+def binom_minus_half(n: int) -> float:
+    """Coefficient of x^n in (1 + x)^(-1/2): (-1)^n (2n)! / (4^n (n!)^2)."""
+    return (-1) ** n * math.comb(2 * n, n) / 4.0 ** n
+
+
+def unitarize(U) -> np.ndarray:
+    """Order-by-order projection of a series onto a unitary series: the polar factor
+    V = U * H^(-1/2) with H = U^+ * U (star products), for a series whose order 0 is unitary.
+
+    Then H = 1 + D with D^(0) = U0^+ U0 - 1 = 0, and the inverse square root is the binomial
+    series (1 + D)^(-1/2) = sum_{n=0}^{T} c_n D^{star n}, c_n = binom(-1/2, n), exact through
+    order T because D^{star n} starts at order n.  D^(0) is set to 0 (order 0 is taken as
+    unitary and is left exactly unchanged).  V^+ * V = 1 through order T, and a unitary series
+    is its own projection.  Shape (..., T+1, N, N)."""
+    U = np.asarray(U, np.complex128)
+    N = U.shape[-1]
+    T = U.shape[-3] - 1
+    lead = U.shape[:-3]
+    D = pm.star(pm.dagger(U), U)
+    D[..., 0, :, :] = 0.0
+    Iser = pm.identity_series(N, T, lead)
+    S = np.zeros_like(U)
+    P = Iser.copy()
+    for n in range(T + 1):
+        S = S + binom_minus_half(n) * P
+        P = pm.star(P, D)
+    V = pm.star(U, S)
+    V[..., 0, :, :] = U[..., 0, :, :]
+    return V

@@ -638,3 +638,80 @@ def test_wilson_loops_conjugation_symmetry():
     U = syn.link_series(rg, 3, 1, 3, 1)[0]
     W = tek.wilson_loops(U, tek.twist_phases(3, 1), 3)
     np.testing.assert_allclose(W, np.conj(np.swapaxes(W, 0, 1)), atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# unitarity projection (polar factor in the truncated ring)
+# ----------------------------------------------------------------------------
+def test_binomial_coefficients_are_the_inverse_square_root_series():
+    # (1 + x)^(-1/2) by numpy's polynomial powers: the coefficients square to 1/(1 + x)
+    c = np.array([tek.binom_minus_half(n) for n in range(12)])
+    sq = np.polynomial.polynomial.polymul(c, c)[:12]
+    inv = np.array([(-1.0) ** n for n in range(12)])
+    np.testing.assert_allclose(sq, inv, atol=1e-12)
+    assert [tek.binom_minus_half(n) for n in range(4)] == [1.0, -0.5, 0.375, -0.3125]
+
+
+def test_unitarize_leaves_a_unitary_series_unchanged():
+    rg = syn.rng(70)
+    U = _unitary_series(rg, 3, 1, 5)
+    V = tek.unitarize(U)
+    np.testing.assert_allclose(V, U, atol=1e-13)
+    np.testing.assert_array_equal(V[:, 0], U[:, 0])
+
+
+def test_unitarize_output_is_unitary_and_idempotent():
+    rg = syn.rng(71)
+    L, k, T = 3, 1, 6
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]          # Gaussian higher orders: not unitary
+    I = pm.identity_series(N, T, (4,))
+    assert np.abs(pm.star(pm.dagger(U), U) - I).max() > 1e-2
+    V = tek.unitarize(U)
+    np.testing.assert_allclose(pm.star(pm.dagger(V), V), I, atol=1e-13)
+    np.testing.assert_allclose(pm.star(V, pm.dagger(V)), I, atol=1e-13)
+    np.testing.assert_allclose(tek.unitarize(V), V, atol=1e-13)
+    np.testing.assert_array_equal(V[:, 0], U[:, 0])
+
+
+def test_unitarize_matches_nonperturbative_polar_factor():
+    # sum_k g^k V^(k) = polar factor of U(g) (scipy) + O(g^{T+1})
+    rg = syn.rng(72)
+    L, k, T = 3, 1, 3
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    U[:, 0] = syn.haar_sun(rg, N, 4)
+    V = tek.unitarize(U)
+    errs = []
+    for gc in (5e-3, 1e-2):
+        pw = gc ** np.arange(T + 1)
+        Ug = np.einsum("k,mkij->mij", pw, U)
+        ref = np.stack([sla.polar(Ug[m])[0] for m in range(4)])
+        got = np.einsum("k,mkij->mij", pw, V)
+        errs.append(np.abs(got - ref).max())
+    assert errs[0] < 1e-8
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+
+
+def test_unitarize_1x1_is_the_phase_of_a_scalar_series():
+    # a scalar series u(g) with |u0| = 1: v(g) = u(g) / |u(g)|, Taylor coefficients by exact
+    # rational arithmetic on u(g) = u0 (1 + a g) for real a: v = u0 (1 + a g)/|1 + a g| = u0
+    # (sign of 1 + a g) = u0 for small g, so every order above 0 vanishes
+    T = 6
+    u = np.zeros((T + 1, 1, 1), np.complex128)
+    u[0] = np.exp(0.3j)
+    u[1] = 0.7 * np.exp(0.3j)
+    v = tek.unitarize(u)
+    np.testing.assert_allclose(v[1:], 0, atol=1e-15)
+    # a purely imaginary first order, u = u0 (1 + i b g): v = u0 (1 + i b g) / sqrt(1 + b^2 g^2)
+    b = 0.4
+    u[1] = 1j * b * np.exp(0.3j)
+    v = tek.unitarize(u)[:, 0, 0] / np.exp(0.3j)
+    ref = np.zeros(T + 1, np.complex128)
+    from scipy.special import binom
+    for n in range(T // 2 + 1):       # (1 + b^2 g^2)^(-1/2) = sum_n binom(-1/2, n) b^(2n) g^(2n)
+        c = binom(-0.5, n) * b ** (2 * n)
+        ref[2 * n] += c
+        if 2 * n + 1 <= T:
+            ref[2 * n + 1] += 1j * b * c
+    np.testing.assert_allclose(v, ref, atol=1e-15)
