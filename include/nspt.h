@@ -63,7 +63,8 @@ enum { NSPT_PREC_FP64 = 0,  /* plain FP64 everywhere (the paper's ZGEMM form) */
                                FP32 partial sums, double-word recombination */ };
 
 /* which call a workspace is sized for */
-enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_MD = 3 };
+enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_MD = 3,
+       NSPT_OP_UNITARIZE = 4 };
 
 #define NSPT_RESCALE_AUTO (-1000)
 
@@ -146,6 +147,22 @@ NSPT_API int nspt_polymat_mul_backward(const void* A, const void* B, const void*
  */
 NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int batch, int flux,
                            double eps, const nspt_opts* opts, void* stream);
+
+/*
+ * Order-by-order unitarity projection of link series, in place (Sec. 2 names a
+ * unitarity projection among the NSPT steps and prints no algorithm; this is the
+ * polar factor in the truncated ring):
+ *   V = U * (U^+ * U)^(-1/2) = U * sum_{n=0}^{T} binom(-1/2, n) D^n,  D = U^+ * U - 1,
+ * with star products (Eq. 5) in the form of opts (naive or FFT, FP64 or split) and
+ * the series dagger (U^+)^(k) = (U^(k))^H.  Order 0 of every series must be unitary; it
+ * is left exactly unchanged (D^(0) is taken as 0).  Then V^+ * V = 1 through order T,
+ * and a unitary series is its own projection (up to rounding).
+ *   U : [batch][T+1][N][N] complex128, updated in place (a link tensor
+ *       [b][4][T+1][N][N] is batch = 4 b series)
+ * T + 2 products per call.  Workspace: NSPT_OP_UNITARIZE.  NSPT_RESCALE_AUTO is
+ * refused (NSPT_ERR_UNSUPPORTED); a fixed rescale applies to every product.
+ */
+NSPT_API int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, void* stream);
 
 /*
  * Grouped products: `count` (<= 64) independent products of uneven sizes,

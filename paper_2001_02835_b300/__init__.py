@@ -22,14 +22,15 @@ import torch
 
 __all__ = [
     "lib", "library_path", "Opts", "NsptError",
-    "polymat_mul", "polymat_mul_host", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops", "order_fft", "order_ifft",
+    "polymat_mul", "polymat_mul_host", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops",
+    "tek_unitarize", "order_fft", "order_ifft",
     "workspace_size", "star", "PolymatMul",
     "ALGO_NAIVE", "ALGO_FFT", "ALGO_AUTO", "PREC_FP64", "PREC_SPLIT", "RESCALE_AUTO",
 ]
 
 ALGO_NAIVE, ALGO_FFT, ALGO_AUTO = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0, 1
-OP_MUL, OP_MUL_BACKWARD, OP_LANGEVIN, OP_MD = 0, 1, 2, 3
+OP_MUL, OP_MUL_BACKWARD, OP_LANGEVIN, OP_MD, OP_UNITARIZE = 0, 1, 2, 3, 4
 RESCALE_AUTO = -1000
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -73,6 +74,7 @@ _SIGS = {
     "nspt_polymat_mul_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_langevin_step": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_md_trajectory": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, _i, ctypes.POINTER(Opts), _vp]),
+    "nspt_tek_unitarize": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_order_fft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_order_ifft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_status_string": (ctypes.c_char_p, [_i]),
@@ -286,6 +288,22 @@ def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, n
                                       _stream_ptr(U.device))
     _check(rc, "nspt_tek_md_trajectory")
     return U, P
+
+
+def tek_unitarize(U: torch.Tensor, **kw) -> torch.Tensor:
+    """Unitarity projection in place: every series of U ((..., T+1, N, N), e.g. links
+    (batch, 4, T+1, N, N)) becomes its polar factor U * (U^+ U)^(-1/2) in the truncated ring,
+    order 0 kept (see include/nspt.h).  kw: algo, prec, fft_len, slices, rescale_log2r."""
+    _check_tensor(U, "U")
+    if U.dim() < 3 or U.shape[-1] != U.shape[-2]:
+        raise ValueError("U must be (..., T+1, N, N)")
+    T, N = U.shape[-3] - 1, U.shape[-1]
+    nser = U.numel() // ((T + 1) * N * N)
+    opts = make_opts(**kw)
+    ws = _with_ws(OP_UNITARIZE, N, T, nser, opts, U.device)  # noqa: F841
+    rc = lib().nspt_tek_unitarize(U.data_ptr(), N, T, nser, ctypes.byref(opts), _stream_ptr(U.device))
+    _check(rc, "nspt_tek_unitarize")
+    return U
 
 
 def tek_wilson_loops(U: torch.Tensor, flux: int, amax: int, **kw) -> torch.Tensor:

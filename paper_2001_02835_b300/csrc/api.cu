@@ -570,6 +570,54 @@ int wilson_run(const Plan& p, const double2* U, int flux, int amax, double2* W, 
   return NSPT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Unitarity projection: V = U * (U^+ U)^(-1/2) in the truncated ring (the polar
+// factor), order 0 kept.  D = U^+ U - 1 with D^(0) := 0, the binomial series
+// S = sum_{n<=T} c_n D^n (c_n = binom(-1/2, n)) by Horner,
+// S_n = c_n 1 + D * S_{n+1}, then V = U * S; every product in the form of opts.
+// ---------------------------------------------------------------------------
+size_t ws_unitarize(const Plan& p) {
+  const size_t ser = (size_t)p.batch * (p.T + 1) * p.E * sizeof(double2);
+  return 3 * al256(ser) + al256(ws_mul(p));
+}
+
+double binom_minus_half(int n) {  // (-1)^n (2n)! / (4^n (n!)^2), by the ratio c_n / c_{n-1}
+  double c = 1.0;
+  for (int k = 1; k <= n; ++k) c *= -(2.0 * k - 1.0) / (2.0 * k);
+  return c;
+}
+
+int unitarize_run(const Plan& p, double2* U, void* ws, cudaStream_t st) {
+  const int N = p.N, T = p.T, nb = p.batch;
+  const long long E = p.E, T1 = T + 1, ser = (long long)nb * T1 * E;
+  char* base = (char*)ws;
+  double2* D = (double2*)base;
+  base += al256(ser * sizeof(double2));
+  double2* S[2] = {(double2*)base, (double2*)(base + al256(ser * sizeof(double2)))};
+  base += 2 * al256(ser * sizeof(double2));
+  void* mws = base;
+  int rc;
+  // D = U^+ * U - 1, with D^(0) = 0 (order 0 is unitary); U^+ goes through S[0]
+  TRY(nspt_series_dagger(U, S[0], N, (long long)nb * T1, st));
+  if ((rc = mul_plan(p, S[0], U, D, mws, st))) return rc;
+  TRY(nspt_series_order0_identity(D, T, N, nb, 0.0, 1, st));
+  // S_T = c_T 1, S_n = c_n 1 + D * S_{n+1} (order 0 of D * S is zero in exact arithmetic: set)
+  TRY(cudaMemsetAsync(S[0], 0, (size_t)ser * sizeof(double2), st));
+  TRY(nspt_series_order0_identity(S[0], T, N, nb, binom_minus_half(T), 1, st));
+  int cur = 0;
+  for (int n = T - 1; n >= 0; --n) {
+    if ((rc = mul_plan(p, D, S[cur], S[cur ^ 1], mws, st))) return rc;
+    TRY(nspt_series_order0_identity(S[cur ^ 1], T, N, nb, binom_minus_half(n), 1, st));
+    cur ^= 1;
+  }
+  // V = U * S into D (free again), orders 1..T copied back; order 0 of U is kept as it is
+  if ((rc = mul_plan(p, U, S[cur], D, mws, st))) return rc;
+  if (T >= 1)
+    TRY(cudaMemcpy2DAsync(U + E, (size_t)T1 * E * sizeof(double2), D + E, (size_t)T1 * E * sizeof(double2),
+                          (size_t)T * E * sizeof(double2), nb, cudaMemcpyDeviceToDevice, st));
+  return NSPT_OK;
+}
+
 std::mutex g_init_mu;
 int g_init_dev[64] = {0};
 
@@ -706,6 +754,7 @@ size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opt
     case NSPT_OP_MUL_BACKWARD: return ws_bwd(p);
     case NSPT_OP_LANGEVIN: return ws_langevin(p);
     case NSPT_OP_MD: return ws_md(p);
+    case NSPT_OP_UNITARIZE: return ws_unitarize(p);
     default: return 0;
   }
 }
@@ -762,6 +811,21 @@ int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void
                     opts ? opts->workspace : nullptr, st);
   return nspt_split_bwd(p.N, p.T, p.batch, p.M, p.slices, p.log2r, (const double2*)A, (const double2*)B,
                         (const double2*)gC, (double2*)gA, (double2*)gB, opts->workspace, st);
+}
+
+int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, void* stream) {
+  Plan p;
+  int rc = make_plan(N, T, batch, opts, &p);
+  if (rc) return rc;
+  if (!U) return NSPT_ERR_ARG;
+  if (p.rescale_auto) return NSPT_ERR_UNSUPPORTED;  // would synchronise once per product
+  if ((rc = check_ws(opts, ws_unitarize(p)))) return rc;
+  if ((rc = nspt_init())) return rc;
+  {
+    const void* ptrs[1] = {U};
+    if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 1))) return rc;
+  }
+  return unitarize_run(p, (double2*)U, opts ? opts->workspace : nullptr, (cudaStream_t)stream);
 }
 
 int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int batch, int flux, double eps,

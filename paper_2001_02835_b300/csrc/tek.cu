@@ -1,6 +1,7 @@
 // Elementwise kernels of the TEK Langevin step and MD integrator (Eqs. 2-3 in
 // rescaled time), of exp_star by Paterson-Stockmeyer (block combination), and
-// of the Wilson-loop measurement (trace of the last product as a correlation).
+// of the Wilson-loop measurement (trace of the last product as a correlation),
+// and of the unitarity projection (series dagger, order-0 identity terms).
 //
 // From the staple series S_mu (Eq. 3, plus sign on the second term) of every
 // link of every stream:
@@ -267,5 +268,70 @@ cudaError_t nspt_wilson_combine(const double2* tr, double2* W, int nplanes, int 
   ProfScope ps(NSPT_STAGE_TEK, st);
   const long long n = (long long)batch * amax * amax * (T + 1);
   wilson_combine_kernel<<<blocks_for(n), 256, 0, st>>>(tr, W, nplanes, amax, batch, T + 1, scale);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Unitarity projection helpers: the series dagger (U^+)^(k) = (U^(k))^H of every
+// coefficient, and order-0 identity terms.
+// ---------------------------------------------------------------------------
+namespace {
+
+// grid (ceil(N/32), ceil(N/32), min(nmat, 65535)), block (32, 8): one 32 x 32 tile of each
+// matrix (matrices z, z + gridDim.z, ...) through shared memory, rows read and written
+// coalesced
+__global__ void __launch_bounds__(256) dagger_kernel(const double2* __restrict__ X, double2* __restrict__ Y, int N,
+                                                     long long nmat) {
+  __shared__ double2 tile[32][33];
+  const long long E = (long long)N * N;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (long long m = blockIdx.z; m < nmat; m += gridDim.z) {
+    const double2* Xm = X + m * E;
+    double2* Ym = Y + m * E;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      const int i = by + r, j = bx + threadIdx.x;
+      if (i < N && j < N) tile[r][threadIdx.x] = Xm[(long long)i * N + j];
+    }
+    __syncthreads();
+    // Y[j][i] = conj(X[i][j]): row j = bx + r of Y, column i = by + threadIdx.x
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      const int j = bx + r, i = by + threadIdx.x;
+      if (i < N && j < N) {
+        const double2 v = tile[threadIdx.x][r];
+        Ym[(long long)j * N + i] = make_double2(v.x, -v.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// order 0 of every series: X[s][0] = c 1 (set) or X[s][0] += c 1 (add)
+__global__ void order0_identity_kernel(double2* X, int T1, int N, long long nseries, double c, int set) {
+  const long long E = (long long)N * N;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseries * E) return;
+  const long long s = i / E, e = i % E;
+  double2* x = X + s * T1 * E + e;
+  const bool diag = (e / N) == (e % N);
+  if (set) *x = make_double2(diag ? c : 0.0, 0.0);
+  else if (diag) x->x += c;
+}
+
+}  // namespace
+
+cudaError_t nspt_series_dagger(const double2* X, double2* Y, int N, long long nmat, cudaStream_t st) {
+  if (nmat <= 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  const unsigned nt = (unsigned)((N + 31) / 32);
+  dim3 grid(nt, nt, (unsigned)std::min<long long>(nmat, 65535));
+  dagger_kernel<<<grid, dim3(32, 8), 0, st>>>(X, Y, N, nmat);
+  return cudaGetLastError();
+}
+
+cudaError_t nspt_series_order0_identity(double2* X, int T, int N, long long nseries, double c, int set,
+                                        cudaStream_t st) {
+  if (nseries <= 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  order0_identity_kernel<<<blocks_for(nseries * (long long)N * N), 256, 0, st>>>(X, T + 1, N, nseries, c, set);
   return cudaGetLastError();
 }

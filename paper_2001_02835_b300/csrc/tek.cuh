@@ -76,3 +76,9 @@ cudaError_t nspt_trace_corr(const double2* L1, const double2* L2, double2* t, do
                             int batch, cudaStream_t st);
 cudaError_t nspt_wilson_combine(const double2* tr, double2* W, int nplanes, int amax, int batch, int T, double scale,
                                 cudaStream_t st);
+
+// unitarity projection: Y[m] = X[m]^H for nmat N x N matrices (Y must not overlap X);
+// order 0 of each of nseries series [T+1][N][N]: X^(0) = c 1 (set != 0) or X^(0) += c 1
+cudaError_t nspt_series_dagger(const double2* X, double2* Y, int N, long long nmat, cudaStream_t st);
+cudaError_t nspt_series_order0_identity(double2* X, int T, int N, long long nseries, double c, int set,
+                                        cudaStream_t st);

@@ -35,7 +35,7 @@ C_OBS = 64.0                  # max err / 2^-(8S-1) over the product cases, S <=
 F_OBS = 2.0 ** -45            # max err of the product cases at S = 7, 8
 SPLIT_C = 4 * C_OBS
 SPLIT_FLOOR = 4 * F_OBS
-CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 2.0, "wilson": 8.0}
+CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 2.0, "wilson": 8.0, "unitarize": 2.0}
 
 
 def dev(x: np.ndarray) -> torch.Tensor:
@@ -67,7 +67,7 @@ def max_order_rel(X, ref) -> float:
 def split_bound(S: int, kind: str = "product", T: int = 0) -> float:
     """Stated per-order bound of the split form with S slices (module docstring); T, the
     truncation order, matters for the chained kinds only."""
-    growth = 2.0 ** max(0.0, (T - 24) / 8.0) if kind in ("langevin", "md", "wilson") else 1.0
+    growth = 2.0 ** max(0.0, (T - 24) / 8.0) if kind in ("langevin", "md", "wilson", "unitarize") else 1.0
     return CHAIN[kind] * growth * (SPLIT_C * 2.0 ** -(8 * S - 1) + SPLIT_FLOOR)
 
 
