@@ -132,6 +132,21 @@ def time_oracle_naive(N, T, nprod, seed):
     return time.perf_counter() - t0
 
 
+def single_core_oracle_seconds(N, T):
+    """The oracle's FFT-CONV of one product in a child process whose BLAS runs one thread
+    (the thread count is fixed when numpy loads, so it cannot change in this process)."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = "1"
+    code = ("import sys; sys.path.insert(0, %r); import bench; "
+            "print(bench.time_oracle_products(%d, %d, 1, %d))" % (ROOT, N, T, syn.SEED_BASE + 2))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return float(r.stdout.strip().split()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
 def cpu_baseline(N, T, M):
     """The oracle as it stands on the host cores, bounded samples: the workload's FFT-CONV on
     all cores (whole batches until about 10 s, at most 30 s) and on one core (one product),
@@ -147,14 +162,10 @@ def cpu_baseline(N, T, M):
     out = {"value": done / tcpu, "unit": "products/s", "cores": cores, "kind": "oracle",
            "sample": "%d products (N=%d, T=%d, M=%d) by the numpy FP64 oracle's direct-DFT FFT-CONV on %s"
                      % (done, N, T, M, cpu_model())}
-    try:
-        from threadpoolctl import threadpool_limits
-        with threadpool_limits(limits=1):
-            t1 = time_oracle_products(N, T, 1, syn.SEED_BASE + 2)
-        out["single_core"] = {"value": 1.0 / t1, "unit": "products/s", "cores": 1,
-                              "sample": "1 product (N=%d, T=%d), direct-DFT FFT-CONV" % (N, T)}
-    except ImportError:  # pragma: no cover
-        out["single_core"] = None
+    t1 = single_core_oracle_seconds(N, T)
+    out["single_core"] = None if t1 is None else {
+        "value": 1.0 / t1, "unit": "products/s", "cores": 1,
+        "sample": "1 product (N=%d, T=%d), direct-DFT FFT-CONV, BLAS limited to one thread" % (N, T)}
     t0 = time_oracle_naive(9, 8, BATCH, syn.SEED_BASE)
     out["naive_su9_T8"] = {"value": BATCH / t0, "unit": "products/s", "cores": cores,
                            "sample": "batch of 4 products (N=9, T=8), Eq. 5 loops"}
