@@ -91,9 +91,11 @@ typedef struct nspt_opts {
                           is flattened), among those that lift no order of A or B above
                           max(1, its largest order) and, in the split form, keep the scale
                           factors 2^(k log2r) within 2^+-120; TEK step: A = B = U; MD link
-                          update: A = U, B = i eps P; refitted at every step or phase --
-                          this reads per-order maxima back and synchronises the stream, so
-                          never inside graph capture; default 0 */
+                          update: A = U, B = i eps P; refitted at every step or phase.
+                          The fit runs on the device (a per-order maxima kernel and a
+                          one-block fit kernel on `stream`), and the transforms read the
+                          fitted exponent from the workspace, so nothing is read back and
+                          the call can be captured in a CUDA graph; default 0 */
   void* workspace;     /* device scratch, >= nspt_workspace_size() bytes */
   size_t workspace_bytes;
 } nspt_opts;
@@ -159,8 +161,8 @@ NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, in
  * and a unitary series is its own projection (up to rounding).
  *   U : [batch][T+1][N][N] complex128, updated in place (a link tensor
  *       [b][4][T+1][N][N] is batch = 4 b series)
- * T + 2 products per call.  Workspace: NSPT_OP_UNITARIZE.  NSPT_RESCALE_AUTO is
- * refused (NSPT_ERR_UNSUPPORTED); a fixed rescale applies to every product.
+ * T + 2 products per call.  Workspace: NSPT_OP_UNITARIZE.  A fixed rescale applies to
+ * every product; NSPT_RESCALE_AUTO fits one per product.
  */
 NSPT_API int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, void* stream);
 
@@ -238,7 +240,7 @@ NSPT_API int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, i
  *   A, B : host [batch][T+1][N][N] complex128;  C : host, same shape, no overlap
  * Workspace: nspt_workspace_size_host() bytes of DEVICE memory (two slots of
  * three series plus the product workspace of one element).
- * NSPT_RESCALE_AUTO is refused (NSPT_ERR_UNSUPPORTED): it synchronises per element.
+ * NSPT_RESCALE_AUTO is not supported here (NSPT_ERR_UNSUPPORTED).
  */
 NSPT_API size_t nspt_workspace_size_host(int N, int T, int batch, const nspt_opts* opts);
 NSPT_API int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, int batch,

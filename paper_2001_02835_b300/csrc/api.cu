@@ -22,6 +22,7 @@
 
 namespace {
 thread_local cudaError_t g_last_cuda = cudaSuccess;
+thread_local const int* g_dev_log2r = nullptr;
 
 int next_pow2(int x) {
   int m = 1;
@@ -121,10 +122,14 @@ int mul_fp64(const Plan& p, const double2* A, const double2* B, double2* C, void
   int* fit = w.take<int>(2 * 513);
   // per-order rescale A_k, B_k -> r^k A_k, r^k B_k, undone on C (exact; as in the split form)
   int lr = p.log2r;
+  int* dlr = nullptr;  // fitted exponent in device memory (the last word of the fit scratch)
   if (p.rescale_auto) {
-    const int rc = nspt_split_fit_rescale(A, B, N, T, b, fit, &lr, st, false);
+    dlr = fit + 2 * 513 - 1;
+    const int rc = nspt_split_fit_rescale_dev(A, B, N, T, b, fit, dlr, st, false);
     if (rc) return rc;
+    lr = 1;
   }
+  NsptDevLog2r scope(dlr);
   TRY(nspt_fft_fwd64(A, T + 1, At, (int)p.E, T, b, M, 0, lr, st));
   TRY(nspt_fft_fwd64(B, T + 1, Bt, (int)p.E, T, b, M, 0, lr, st));
   ZgemmParams P = zg(ZG_MODE, At, M, Bt, M, Ct, M, N, M, T);
@@ -215,12 +220,22 @@ size_t ws_langevin(const Plan& p) { return ((ws_langevin_core(p) + 255) & ~(size
 void* fit_scratch(const Plan& p, void* ws) { return (char*)ws + ((ws_langevin_core(p) + 255) & ~(size_t)255); }
 
 // exponent of the per-order rescale of a TEK step's order transforms (FFT forms only): fixed, or
-// with NSPT_RESCALE_AUTO fitted to the per-order maxima of A and B (synchronises the stream)
-int tek_log2r(const Plan& p, const double2* A, const double2* B, void* ws, cudaStream_t st, int* lr) {
+// with NSPT_RESCALE_AUTO fitted on the device to the per-order maxima of A and B; then *lr = 1
+// and *dlr points at the fitted exponent, which the caller hands to the transforms through an
+// NsptDevLog2r scope
+int tek_log2r(const Plan& p, const double2* A, const double2* B, void* ws, cudaStream_t st, int* lr,
+              const int** dlr) {
   *lr = 0;
+  *dlr = nullptr;
   if (p.algo != NSPT_ALGO_FFT) return NSPT_OK;
   if (!p.rescale_auto) { *lr = p.log2r; return NSPT_OK; }
-  return nspt_split_fit_rescale(A, B, p.N, p.T, p.batch * 4, fit_scratch(p, ws), lr, st, p.prec == NSPT_PREC_SPLIT);
+  int* scratch = (int*)fit_scratch(p, ws);
+  int* out = scratch + 2 * 513 - 1;
+  const int rc = nspt_split_fit_rescale_dev(A, B, p.N, p.T, p.batch * 4, scratch, out, st, p.prec == NSPT_PREC_SPLIT);
+  if (rc) return rc;
+  *lr = 1;
+  *dlr = out;
+  return NSPT_OK;
 }
 
 // mode: NSPT_LMODE_STEP (drift, increment, update), NSPT_LMODE_DRIFT (drift F only),
@@ -467,9 +482,11 @@ size_t ws_md(const Plan& p) {
 
 int md_phase(const Plan& p, double2* U, double2* F, const double2* Y, int flux, void* lws, cudaStream_t st, int mode) {
   int lr = 0;
+  const int* dlr = nullptr;
   // the force phase multiplies links only; the link update also powers of the increment Y
-  const int rc = tek_log2r(p, U, mode == NSPT_LMODE_UPDATE ? Y : U, lws, st, &lr);
+  const int rc = tek_log2r(p, U, mode == NSPT_LMODE_UPDATE ? Y : U, lws, st, &lr, &dlr);
   if (rc) return rc;
+  NsptDevLog2r scope(dlr);
   if (p.prec == NSPT_PREC_SPLIT)
     return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, U, nullptr, F, flux, 0.0, lws, st, mode, Y, lr);
   return langevin_fp64(p, U, nullptr, F, flux, 0.0, lws, st, mode, Y, lr);
@@ -717,6 +734,9 @@ int host_run(const Plan& pc, int batch, const double2* A, const double2* B, doub
 }  // namespace
 
 void nspt_set_last_cuda_error(cudaError_t e) { g_last_cuda = e; }
+const int* nspt_dev_log2r() { return g_dev_log2r; }
+NsptDevLog2r::NsptDevLog2r(const int* p) : prev_(g_dev_log2r) { g_dev_log2r = p; }
+NsptDevLog2r::~NsptDevLog2r() { g_dev_log2r = prev_; }
 
 extern "C" {
 
@@ -818,7 +838,6 @@ int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, 
   int rc = make_plan(N, T, batch, opts, &p);
   if (rc) return rc;
   if (!U) return NSPT_ERR_ARG;
-  if (p.rescale_auto) return NSPT_ERR_UNSUPPORTED;  // would synchronise once per product
   if ((rc = check_ws(opts, ws_unitarize(p)))) return rc;
   if ((rc = nspt_init())) return rc;
   {
@@ -851,9 +870,11 @@ int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int 
     if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 3))) return rc;
   }
   int lr = 0;
+  const int* dlr = nullptr;
   if ((rc = tek_log2r(p, (const double2*)U, (const double2*)U, opts ? opts->workspace : nullptr, (cudaStream_t)stream,
-                      &lr)))
+                      &lr, &dlr)))
     return rc;
+  NsptDevLog2r scope(dlr);
   if (p.prec != NSPT_PREC_FP64) {
     return nspt_split_langevin(p.N, p.T, p.batch, p.M, p.slices, (double2*)U, (const double2*)eta, (double2*)F, flux,
                                eps, opts->workspace, (cudaStream_t)stream, NSPT_LMODE_STEP, nullptr, lr);

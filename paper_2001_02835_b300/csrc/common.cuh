@@ -14,6 +14,22 @@
 
 void nspt_set_last_cuda_error(cudaError_t e);
 
+// Per-order rescale fitted on the device: while an NsptDevLog2r scope is alive on this host
+// thread, every order transform launched multiplies its log2r argument by *p, read when the
+// kernel runs (the fit kernel writes *p earlier on the same stream), so the fitted mode needs
+// no read-back and can be captured in a CUDA graph.  A null p means a fixed rescale.
+const int* nspt_dev_log2r();
+class NsptDevLog2r {
+ public:
+  explicit NsptDevLog2r(const int* p);
+  ~NsptDevLog2r();
+  NsptDevLog2r(const NsptDevLog2r&) = delete;
+  NsptDevLog2r& operator=(const NsptDevLog2r&) = delete;
+
+ private:
+  const int* prev_;
+};
+
 // Pointer kinds of an entry point's buffers, checked on the host before any
 // launch, so that a host pointer where device memory is expected (or the
 // reverse) returns NSPT_ERR_ARG instead of faulting a kernel.  Skipped while

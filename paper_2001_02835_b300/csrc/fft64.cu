@@ -38,7 +38,8 @@ __device__ __forceinline__ int bitrev(int i) {
 template <int M, int EB>
 __global__ void __launch_bounds__(EB * 8)
 fft_fwd64_kernel(const double2* __restrict__ in, long long in_stride, double2* __restrict__ out, int E,
-                 int T, int log2s, int log2r) {
+                 int T, int log2s, int log2r, const int* __restrict__ dlr) {
+  if (dlr) log2r *= *dlr;  // rescale exponent fitted on the device
   extern __shared__ double2 sm[];  // [M][EB]
   const int e = threadIdx.x;       // entry within strip
   const int y = threadIdx.y;       // 0..7
@@ -90,7 +91,9 @@ __device__ __forceinline__ double2 load_spec(const float4* p) {
 template <int M, int EB, typename InT>
 __global__ void __launch_bounds__(EB * 8)
 fft_inv64_kernel(const InT* __restrict__ in, double2* __restrict__ out, long long out_stride, int E,
-                 int N, int T, int log2u, int log2r, double post, int add_identity, int kmin) {
+                 int N, int T, int log2u, int log2r, double post, int add_identity, int kmin,
+                 const int* __restrict__ dlr) {
+  if (dlr) log2r *= *dlr;  // rescale exponent fitted on the device
   extern __shared__ double2 sm[];
   const int e = threadIdx.x;
   const int y = threadIdx.y;
@@ -143,7 +146,7 @@ cudaError_t launch_fwd(const double2* in, long long ins, double2* out, int E, in
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr);
+  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr, nspt_dev_log2r());
   return cudaGetLastError();
 }
 
@@ -156,7 +159,7 @@ cudaError_t launch_inv(const InT* in, double2* out, long long outs, int E, int N
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, out, outs, E, N, T, lu, lr, post, addi, kmin);
+  kern<<<grid, block, smem, st>>>(in, out, outs, E, N, T, lu, lr, post, addi, kmin, nspt_dev_log2r());
   return cudaGetLastError();
 }
 

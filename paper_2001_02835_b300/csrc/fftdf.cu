@@ -38,7 +38,8 @@ using fftdf::st;
 template <int M, int EB, bool TOUT>
 __global__ void __launch_bounds__(EB * 8)
 fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* __restrict__ out, int E, int T,
-                  int log2s, int log2r, int N) {
+                  int log2s, int log2r, int N, const int* __restrict__ dlr) {
+  if (dlr) log2r *= *dlr;  // rescale exponent fitted on the device
   extern __shared__ float4 sm[];  // [M][EB]
   constexpr int CB = EB / 8;      // columns per block (TOUT)
   const int e = threadIdx.x, y = threadIdx.y, b = blockIdx.y;
@@ -83,7 +84,9 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
 template <int M, int EB>
 __global__ void __launch_bounds__(EB * 8)
 fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long long out_stride, int E, int T,
-                  int log2u, int log2r, float post_h, float post_l, int add_identity, int N, int kmin) {
+                  int log2u, int log2r, float post_h, float post_l, int add_identity, int N, int kmin,
+                  const int* __restrict__ dlr) {
+  if (dlr) log2r *= *dlr;  // rescale exponent fitted on the device
   extern __shared__ float4 sm[];
   const int e = threadIdx.x, y = threadIdx.y, b = blockIdx.y;
   const long long e0 = (long long)blockIdx.x * EB;
@@ -189,7 +192,7 @@ cudaError_t launch_fwd(const double2* in, long long ins, float4* out, int E, int
   const long long blocks = tout_n ? (long long)((tout_n + 7) / 8) * ((tout_n + EB / 8 - 1) / (EB / 8))
                                   : ((long long)E + EB - 1) / EB;
   dim3 grid((unsigned)blocks, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr, tout_n);
+  kern<<<grid, block, smem, st>>>(in, ins, out, E, T, ls, lr, tout_n, nspt_dev_log2r());
   return cudaGetLastError();
 }
 
@@ -202,7 +205,7 @@ cudaError_t launch_inv(const float4* in, double2* out, long long outs, int E, in
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   dim3 grid((E + EB - 1) / EB, batch), block(EB, 8);
-  kern<<<grid, block, smem, st>>>(in, out, outs, E, T, lu, lr, ph, pl, addi, N, kmin);
+  kern<<<grid, block, smem, st>>>(in, out, outs, E, T, lu, lr, ph, pl, addi, N, kmin, nspt_dev_log2r());
   return cudaGetLastError();
 }
 

@@ -417,63 +417,73 @@ __global__ void order_maxexp_kernel(const double2* __restrict__ A, const double2
 
 }  // namespace
 
-// Fits log2 r for the per-order rescale (a0): with m_k = log2 max|A_k| + log2 max|B_k|
-// over the orders where both are non-zero, the least-squares slope sigma of m_k
-// against k gives r = 2^round(-sigma / 2), one r for both operands so that
-// C_k = r^-k (A' * B')_k.  Reads a few integers back: synchronises the stream.
-int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int batch, void* scratch, int* log2r,
-                           cudaStream_t st, bool float_range) {
-  int* d = (int*)scratch;
-  TRYC(cudaMemsetAsync(d, 0, sizeof(int) * 2 * (T + 1), st));
-  const long long E = (long long)N * N;
-  dim3 grid((unsigned)std::min<long long>((E + 255) / 256, 64), T + 1);
-  order_maxexp_kernel<<<grid, 256, 0, st>>>(A, B, d, E, T, batch);
-  TRYC(cudaGetLastError());
-  std::vector<int> h(2 * (T + 1));
-  TRYC(cudaMemcpyAsync(h.data(), d, sizeof(int) * 2 * (T + 1), cudaMemcpyDeviceToHost, st));
-  TRYC(cudaStreamSynchronize(st));
-  // exponent fields: y_k = log2 max|A_k| + log2 max|B_k| ~ (eA - 1023) + (eB - 1023).  The
-  // relative error of order k grows with max_j(y_j + 2 j log2r) - (y_k + 2 k log2r): take the
-  // log2r that minimises the spread of y_k + 2 k log2r over the nonzero orders (for a geometric
-  // decay this flattens it; for a faster, factorial one it balances the first and last orders),
-  // the smallest |log2r| among equals
-  std::vector<std::pair<int, double>> y;
-  int maxA = -100000, maxB = -100000;  // log2 of the largest order of each operand
-  for (int k = 0; k <= T; ++k) {
-    if (h[k] != 0) maxA = std::max(maxA, h[k] - 1023);
-    if (h[T + 1 + k] != 0) maxB = std::max(maxB, h[T + 1 + k] - 1023);
-    if (h[k] != 0 && h[T + 1 + k] != 0) y.push_back({k, (double)(h[k] - 1023) + (double)(h[T + 1 + k] - 1023)});
+namespace {
+
+// One block of 128 threads: candidate c (c <= 120) is log2r = 0, 1, -1, 2, -2, ... (c odd:
+// (c + 1) / 2, c even: -c / 2).  Its spread max_k - min_k of y_k + 2 k log2r over the orders
+// where both operands are nonzero, or +inf when it is not allowed; the smallest spread wins,
+// the earliest candidate (smallest |log2r|) among equal spreads.  h: exponent fields of the
+// per-order maxima of A (h[k]) and B (h[T + 1 + k]), 0 for an all-zero order.
+__global__ void __launch_bounds__(128) fit_log2r_kernel(const int* __restrict__ h, int T, int float_range,
+                                                        int* __restrict__ out) {
+  __shared__ double spread[128];
+  __shared__ int maxes[2];
+  const int c = threadIdx.x;
+  if (c == 0) {
+    int ma = -100000, mb = -100000;
+    for (int k = 0; k <= T; ++k) {
+      if (h[k] != 0) ma = max(ma, h[k] - 1023);
+      if (h[T + 1 + k] != 0) mb = max(mb, h[T + 1 + k] - 1023);
+    }
+    maxes[0] = ma;
+    maxes[1] = mb;
   }
-  *log2r = 0;
-  if (y.size() >= 2) {
-    double best = 1e300;
-    for (int a = 0; a <= 120; ++a) {
-      const int lr = (a % 2) ? (a + 1) / 2 : -(a / 2);  // 0, 1, -1, 2, -2, ...
-      // the double-float transforms work in the FP32 exponent range: scale factors 2^(k lr)
-      // within 2^+-120
-      if (float_range && (long long)std::abs(lr) * T > 120) continue;
-      // no scaled order may exceed max(1, the largest unscaled order): the rescale lifts small
-      // orders but never makes a series larger than it was or than 1, so products and powers
-      // of the scaled series (staples, exp_star's powers) stay in range
-      const int capA = std::max(maxA, 0), capB = std::max(maxB, 0);
-      bool ok = true;
-      for (int k = 0; k <= T && ok; ++k) {
-        if (h[k] != 0 && h[k] - 1023 + k * lr > capA) ok = false;
-        if (h[T + 1 + k] != 0 && h[T + 1 + k] - 1023 + k * lr > capB) ok = false;
-      }
-      if (!ok) continue;
-      double lo = 1e300, hi = -1e300;
-      for (const auto& kv : y) {
-        const double v = kv.second + 2.0 * kv.first * lr;
-        lo = std::min(lo, v);
-        hi = std::max(hi, v);
-      }
-      if (hi - lo < best - 1e-9) {
-        best = hi - lo;
-        *log2r = lr;
-      }
+  __syncthreads();
+  const int lr = (c % 2) ? (c + 1) / 2 : -(c / 2);
+  const int capA = max(maxes[0], 0), capB = max(maxes[1], 0);
+  bool ok = c <= 120 && !(float_range && abs(lr) * T > 120);
+  double lo = 1e300, hi = -1e300;
+  int ny = 0;
+  for (int k = 0; k <= T; ++k) {
+    const int a = h[k], b = h[T + 1 + k];
+    if (a != 0 && a - 1023 + k * lr > capA) ok = false;
+    if (b != 0 && b - 1023 + k * lr > capB) ok = false;
+    if (a != 0 && b != 0) {
+      const double v = (double)(a - 1023) + (double)(b - 1023) + 2.0 * k * lr;
+      lo = fmin(lo, v);
+      hi = fmax(hi, v);
+      ++ny;
     }
   }
+  spread[c] = ok ? hi - lo : 1e300;
+  __syncthreads();
+  if (c == 0) {
+    int best_c = -1;
+    double best = 1e300;
+    if (ny >= 2)
+      for (int i = 0; i <= 120; ++i)
+        if (spread[i] < best - 1e-9) { best = spread[i]; best_c = i; }
+    *out = best_c < 0 ? 0 : ((best_c % 2) ? (best_c + 1) / 2 : -(best_c / 2));
+  }
+}
+
+}  // namespace
+
+int nspt_split_fit_rescale_dev(const double2* A, const double2* B, int N, int T, int batch, int* scratch, int* out,
+                               cudaStream_t st, bool float_range) {
+  TRYC(cudaMemsetAsync(scratch, 0, sizeof(int) * 2 * (T + 1), st));
+  const long long E = (long long)N * N;
+  dim3 grid((unsigned)std::min<long long>((E + 255) / 256, 64), T + 1);
+  {
+    ProfScope ps(NSPT_STAGE_OTHER, st);
+    order_maxexp_kernel<<<grid, 256, 0, st>>>(A, B, scratch, E, T, batch);
+  }
+  TRYC(cudaGetLastError());
+  {
+    ProfScope ps(NSPT_STAGE_OTHER, st);
+    fit_log2r_kernel<<<1, 128, 0, st>>>(scratch, T, float_range ? 1 : 0, out);
+  }
+  TRYC(cudaGetLastError());
   return NSPT_OK;
 }
 
@@ -481,7 +491,15 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
                    const double2* B, double2* C, void* ws, cudaStream_t st) {
   const int E = N * N, Q = batch * M;
   SplitWs w = carve(ws, N, batch, M, S, nullptr);
-  if (rescale_auto) TRYS(nspt_split_fit_rescale(A, B, N, T, batch, w.expA, &log2r, st));
+  // fitted rescale: on the device, into a spare word of the status block (the maxima go to expA,
+  // which the slicer overwrites later; the exponent must outlive it for the inverse transform)
+  int* dlr = nullptr;
+  if (rescale_auto) {
+    dlr = w.err + 16;
+    TRYS(nspt_split_fit_rescale_dev(A, B, N, T, batch, w.expA, dlr, st));
+    log2r = 1;
+  }
+  NsptDevLog2r scope(dlr);
   TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
   // a0 + a1: per-order rescale A_k -> 2^(k log2r) A_k fused into the forward transform
   // (B's spectra are written transposed, so that both operands are sliced by rows)

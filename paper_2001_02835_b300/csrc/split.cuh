@@ -26,12 +26,14 @@ int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int re
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st);
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st);
-// least-squares fit of the per-order rescale exponent: log2r = round(-sigma/2), sigma the slope over k
-// of log2 max|A_k| + log2 max|B_k| (A, B: `batch` series [T+1][N][N]); scratch: 2 (T+1) ints of device
-// memory; reads the maxima back and synchronises `st`.  float_range: only exponents whose scale
-// factors and scaled maxima fit the FP32 range of the double-float transforms (split form)
-int nspt_split_fit_rescale(const double2* A, const double2* B, int N, int T, int batch, void* scratch, int* log2r,
-                           cudaStream_t st, bool float_range = true);
+// fit of the per-order rescale exponent on the device: with y_k = log2 max|A_k| + log2 max|B_k|
+// over the orders where both are nonzero (A, B: `batch` series [T+1][N][N]), the integer log2r
+// minimising the spread of y_k + 2 k log2r (smallest |log2r| among equals), among those that lift
+// no order of A or B above max(1, its largest order) and, with float_range, keep the scale factors
+// within 2^+-120 (the FP32 range of the double-float transforms).  scratch: 2 (T+1) ints of device
+// memory; the exponent is written to *out (device memory) on `st`; nothing is read back.
+int nspt_split_fit_rescale_dev(const double2* A, const double2* B, int N, int T, int batch, int* scratch, int* out,
+                               cudaStream_t st, bool float_range = true);
 size_t nspt_split_ws_grouped(const nspt_polymat_desc* d, int count, int S);
 int nspt_split_mul_grouped(const nspt_polymat_desc* d, int count, int S, int log2r, void* ws, cudaStream_t st);
 int nspt_split_autotune_grouped(const nspt_polymat_desc* d, int count, int S, void* ws, const char* cache_path,

@@ -104,5 +104,8 @@ def test_unitarize_argument_checks(nspt):
     x = torch.zeros((1, 3, 4, 4), dtype=torch.complex128, device="cuda")
     assert L.nspt_tek_unitarize(None, 4, 2, 1, ctypes.byref(o), None) == -1
     assert L.nspt_tek_unitarize(x.data_ptr(), 4, 2, 1, ctypes.byref(o), None) == -4   # no workspace
-    o = nspt.make_opts(algo="fft", prec="fp64", rescale_log2r=nspt.RESCALE_AUTO)
-    assert L.nspt_tek_unitarize(x.data_ptr(), 4, 2, 1, ctypes.byref(o), None) == -3
+    # the fitted per-order rescale is allowed (one fit per product, on the device)
+    tU = dev(near_unitary_links(syn.rng(9500), 2, 1, 6, 1))
+    ref = tek.unitarize(host(tU))
+    nspt.tek_unitarize(tU, algo="fft", prec="fp64", rescale_log2r=nspt.RESCALE_AUTO)
+    assert max_order_rel(host(tU), ref) <= 1e-12
