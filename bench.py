@@ -429,6 +429,31 @@ def per_order_vs_oracle(torch, nspt, A, B, dA, dB, dC, T, barrier, extras):
     return out
 
 
+def md_graph_leg(torch, nspt, barrier, L=11, T=15, flux=1, eps=0.02, nsteps=40):
+    """One 40-step MD trajectory at SU(121), O(g^15) in the split form with the fitted rescale,
+    enqueued eagerly and replayed as one captured CUDA graph (the fit runs on the device, so
+    the whole trajectory captures): at this size the host's enqueue time of the ~300 launches
+    per step is not hidden behind the GPU."""
+    g = syn.rng(syn.SEED_BASE + 6)
+    N = L * L
+    U0 = torch.from_numpy(np.ascontiguousarray(syn.vacuum_links(L, flux, T, 1))).cuda()
+    eta = torch.from_numpy(np.ascontiguousarray(syn.md_momenta(g, N, 1))).cuda()
+    kw = dict(algo="fft", prec="split", rescale_log2r=nspt.RESCALE_AUTO)
+    U, P = U0.clone(), torch.zeros_like(U0)
+    nspt.tek_md_trajectory(U, P, flux, eps, nsteps, eta=eta, **kw)      # thermalisation
+    Ut = U.clone()
+    eager = time_steps(torch, lambda: nspt.tek_md_trajectory(U, P, flux, eps, nsteps, eta=eta, **kw), 2, 1, barrier) / 2
+    Ug, Pg = Ut.clone(), torch.zeros_like(Ut)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        nspt.tek_md_trajectory(Ug, Pg, flux, eps, nsteps, eta=eta, **kw)
+    replay = time_steps(torch, graph.replay, 2, 1, barrier) / 2
+    del graph, U, P, Ug, Pg, U0, Ut, eta
+    return {"ms_per_trajectory_eager": eager, "ms_per_trajectory_graph": replay, "md_steps": nsteps,
+            "workload": "SU(%d), O(g^%d), one configuration, split form, fitted rescale" % (N, T)}
+
+
 def time_steps(torch, fn, steps, warmup, barrier):
     for _ in range(warmup):
         fn()
@@ -575,6 +600,7 @@ def run_ours(args):
         del gC
         extras["langevin_su121_T31_8streams"] = langevin_leg(torch, nspt, barrier)
         extras["md_trajectory_su225_T31"] = md_leg(torch, nspt, barrier)
+        extras["md_trajectory_su121_T15_graph"] = md_graph_leg(torch, nspt, barrier)
         msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
         extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
