@@ -21,7 +21,8 @@ functions fix (each pinned by a test):
 * unitarity projection (the paper names a unitarity projection among the NSPT
   steps but prints no algorithm): the polar factor of the series in the
   truncated ring, V = U * (U^+ * U)^(-1/2), with order 0 (unitary) kept as it is;
-  see ``unitarize``;
+  optionally followed by the removal of the U(1) (trace, zero-mode) phase, so that
+  det V = det U^(0) through order T; see ``unitarize``;
 * Wilson loops: W(a, b) = 1/(12 N) sum over ordered planes of
   z_{mu nu}^(ab) Tr[U_mu^a U_nu^b (U_mu^a)^+ (U_nu^b)^+] (the paper measures Wilson
   loops but does not restate their definition; the z^(ab) factor makes the
@@ -201,7 +202,59 @@ def binom_minus_half(n: int) -> float:
     return (-1) ** n * math.comb(2 * n, n) / 4.0 ** n
 
 
-def unitarize(U) -> np.ndarray:
+def log_star_unit(D) -> np.ndarray:
+    """log_star(1 + D) = sum_{n=1}^{T} (-1)^(n+1) D^{star n} / n for a series with D^(0) = 0
+    (exact through order T)."""
+    D = np.asarray(D, np.complex128)
+    if np.any(D[..., 0, :, :] != 0):
+        raise ValueError("log_star_unit needs D^(0) = 0")
+    T = D.shape[-3] - 1
+    out = np.zeros_like(D)
+    P = D.copy()
+    for n in range(1, T + 1):
+        out = out + ((-1) ** (n + 1) / n) * P
+        P = pm.star(P, D)
+    return out
+
+
+def scalar_exp(b) -> np.ndarray:
+    """Coefficients of exp(b(g)) for a scalar series b with b_0 = 0, shape (..., T+1), by
+    k s_k = sum_{j=1}^{k} j b_j s_{k-j}, s_0 = 1 (the derivative of exp(b) is b' exp(b))."""
+    b = np.asarray(b, np.complex128)
+    T = b.shape[-1] - 1
+    s = np.zeros_like(b)
+    s[..., 0] = 1.0
+    for k in range(1, T + 1):
+        acc = np.zeros(b.shape[:-1], np.complex128)
+        for j in range(1, k + 1):
+            acc = acc + j * b[..., j] * s[..., k - j]
+        s[..., k] = acc / k
+    return s
+
+
+def remove_u1_phase(V) -> np.ndarray:
+    """For a unitary series V: the phase series a(g) = Im Tr log(V0^+ V(g)) (a_0 = 0) and
+    W = V * exp(-i a(g) / N), so that det W = det V^(0) through order T.  The trace part of the
+    algebra is the U(1) (zero) mode of the links; an SU(N) evolution keeps it zero, and
+    rounding can move it."""
+    V = np.asarray(V, np.complex128)
+    N = V.shape[-1]
+    V0h = np.zeros_like(V)
+    V0h[..., 0, :, :] = np.conj(np.swapaxes(V[..., 0, :, :], -1, -2))
+    D = pm.star(V0h, V)
+    D[..., 0, :, :] = 0.0
+    a = np.imag(np.trace(log_star_unit(D), axis1=-2, axis2=-1))     # (..., T+1), a_0 = 0
+    s = scalar_exp(-1j * a / N)
+    W = np.zeros_like(V)
+    T = V.shape[-3] - 1
+    for k in range(T + 1):
+        for j in range(k + 1):
+            W[..., k, :, :] += V[..., j, :, :] * s[..., k - j, None, None]
+    W[..., 0, :, :] = V[..., 0, :, :]
+    return W
+
+
+def unitarize(U, special: bool = False) -> np.ndarray:
     """Order-by-order projection of a series onto a unitary series: the polar factor
     V = U * H^(-1/2) with H = U^+ * U (star products), for a series whose order 0 is unitary.
 
@@ -209,7 +262,8 @@ def unitarize(U) -> np.ndarray:
     series (1 + D)^(-1/2) = sum_{n=0}^{T} c_n D^{star n}, c_n = binom(-1/2, n), exact through
     order T because D^{star n} starts at order n.  D^(0) is set to 0 (order 0 is taken as
     unitary and is left exactly unchanged).  V^+ * V = 1 through order T, and a unitary series
-    is its own projection.  Shape (..., T+1, N, N)."""
+    is its own projection.  With special=True the U(1) phase is removed as well
+    (remove_u1_phase): det V = det U^(0) through order T.  Shape (..., T+1, N, N)."""
     U = np.asarray(U, np.complex128)
     N = U.shape[-1]
     T = U.shape[-3] - 1
@@ -224,4 +278,4 @@ def unitarize(U) -> np.ndarray:
         P = pm.star(P, D)
     V = pm.star(U, S)
     V[..., 0, :, :] = U[..., 0, :, :]
-    return V
+    return remove_u1_phase(V) if special else V

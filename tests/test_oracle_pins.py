@@ -715,3 +715,74 @@ def test_unitarize_1x1_is_the_phase_of_a_scalar_series():
         if 2 * n + 1 <= T:
             ref[2 * n + 1] += 1j * b * c
     np.testing.assert_allclose(v, ref, atol=1e-15)
+
+
+def test_log_star_and_scalar_exp_special_cases():
+    # scalar series: log(1 + d) and exp(b) against numpy polynomial arithmetic
+    T = 7
+    rg = np.random.default_rng(73)
+    d = np.zeros(T + 1, np.complex128)
+    d[1:] = rg.normal(size=T) + 1j * rg.normal(size=T)
+    L = tek.log_star_unit(d.reshape(T + 1, 1, 1))[:, 0, 0]
+    # exp of the log series gives back 1 + d (truncated)
+    np.testing.assert_allclose(tek.scalar_exp(L), np.r_[1.0, d[1:]], atol=1e-12)
+    # exp(b) for b = c g: c^k / k!
+    b = np.zeros(T + 1, np.complex128)
+    b[1] = 0.3 - 0.2j
+    ref = np.array([b[1] ** k / math.factorial(k) for k in range(T + 1)])
+    np.testing.assert_allclose(tek.scalar_exp(b), ref, atol=1e-15)
+    # log of a commuting (diagonal) matrix series: entrywise scalar logs
+    D = np.zeros((T + 1, 2, 2), np.complex128)
+    D[1:, 0, 0] = d[1:]
+    D[1:, 1, 1] = np.conj(d[1:])
+    LD = tek.log_star_unit(D)
+    np.testing.assert_allclose(LD[:, 0, 0], L, atol=1e-13)
+    np.testing.assert_allclose(LD[:, 1, 1], tek.log_star_unit(np.conj(d).reshape(T + 1, 1, 1))[:, 0, 0], atol=1e-13)
+
+
+def test_u1_phase_removal_fixes_the_determinant_nonperturbatively():
+    # sum_k g^k W^(k) = polar(U(g)) * (det U0 / det polar(U(g)))^(1/N) + O(g^{T+1})
+    rg = syn.rng(74)
+    L, k, T = 3, 1, 3
+    N = L * L
+    U = syn.link_series(rg, L, k, T, 1)[0]
+    U[:, 0] = syn.haar_sun(rg, N, 4)
+    W = tek.unitarize(U, special=True)
+    errs, dets = [], []
+    for gc in (5e-3, 1e-2):
+        pw = gc ** np.arange(T + 1)
+        Ug = np.einsum("k,mkij->mij", pw, U)
+        ref = []
+        for m in range(4):
+            P = sla.polar(Ug[m])[0]
+            ratio = np.linalg.det(U[m, 0]) / np.linalg.det(P)
+            ref.append(P * ratio ** (1.0 / N))
+        got = np.einsum("k,mkij->mij", pw, W)
+        errs.append(np.abs(got - np.stack(ref)).max())
+        dets.append(max(abs(np.linalg.det(got[m]) - np.linalg.det(U[m, 0])) for m in range(4)))
+    assert errs[0] < 1e-8
+    assert 2 ** (T + 1) * 0.5 < errs[1] / errs[0] < 2 ** (T + 1) * 1.7
+    assert dets[0] < 1e-8 and 2 ** (T + 1) * 0.5 < dets[1] / dets[0] < 2 ** (T + 1) * 1.7
+
+
+def test_u1_phase_removal_keeps_special_unitary_series():
+    # an SU(N)-type series exp_star(i H) * Gamma with traceless H has no U(1) phase to remove
+    rg = syn.rng(75)
+    L, k, T = 3, 1, 5
+    N = L * L
+    H = syn.gaussian(rg, (4, T + 1, N, N), 1.0 / N)
+    H = 0.5 * (H + np.conj(np.swapaxes(H, -1, -2)))
+    H = H - (np.trace(H, axis1=-2, axis2=-1) / N)[..., None, None] * np.eye(N)
+    H[:, 0] = 0
+    G = np.zeros((4, T + 1, N, N), np.complex128)
+    G[:, 0] = syn.twist_eaters(L, k)
+    U = pm.star(tek.exp_star(1j * H), G)
+    np.testing.assert_allclose(tek.unitarize(U, special=True), U, atol=1e-13)
+    # a phase-rotated one gets its phase removed: U * exp(i c g) (scalar) -> U
+    c = 0.37
+    ph = tek.scalar_exp(np.r_[0.0, 1j * c, np.zeros(T - 1)])
+    Ur = np.zeros_like(U)
+    for kk in range(T + 1):
+        for j in range(kk + 1):
+            Ur[:, kk] += U[:, j] * ph[kk - j]
+    np.testing.assert_allclose(tek.unitarize(Ur, special=True), U, atol=1e-12)
