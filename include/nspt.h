@@ -152,19 +152,26 @@ NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, in
 
 /*
  * Order-by-order unitarity projection of link series, in place (Sec. 2 names a
- * unitarity projection among the NSPT steps and prints no algorithm; this is the
- * polar factor in the truncated ring):
+ * unitarity projection and zero-mode subtraction among the NSPT steps and prints no
+ * algorithm; this is the polar factor in the truncated ring, optionally followed by
+ * the removal of the U(1) (trace) mode):
  *   V = U * (U^+ * U)^(-1/2) = U * sum_{n=0}^{T} binom(-1/2, n) D^n,  D = U^+ * U - 1,
  * with star products (Eq. 5) in the form of opts (naive or FFT, FP64 or split) and
  * the series dagger (U^+)^(k) = (U^(k))^H.  Order 0 of every series must be unitary; it
  * is left exactly unchanged (D^(0) is taken as 0).  Then V^+ * V = 1 through order T,
  * and a unitary series is its own projection (up to rounding).
+ * special = 1 also removes the U(1) phase a(g) = Im Tr log(U0^+ V(g)) (a_0 = 0),
+ *   V <- V * exp(-i a / N)   (a scalar series times the matrix series),
+ * so that det V = det U^(0) through order T; a is taken from Jacobi's formula,
+ * a_k = Im Tr(V^+ * V')_(k-1) / k with V'_j = (j+1) V_(j+1) (one more product).
+ * special = 0 stops at the polar factor.  Other values: NSPT_ERR_ARG.
  *   U : [batch][T+1][N][N] complex128, updated in place (a link tensor
  *       [b][4][T+1][N][N] is batch = 4 b series)
- * T + 2 products per call.  Workspace: NSPT_OP_UNITARIZE.  A fixed rescale applies to
+ * T + 2 products (T + 3 with special = 1) per call.  Workspace: NSPT_OP_UNITARIZE.  A fixed rescale applies to
  * every product; NSPT_RESCALE_AUTO fits one per product.
  */
-NSPT_API int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, void* stream);
+NSPT_API int nspt_tek_unitarize(void* U, int N, int T, int batch, int special, const nspt_opts* opts,
+                                void* stream);
 
 /*
  * Grouped products: `count` (<= 64) independent products of uneven sizes,

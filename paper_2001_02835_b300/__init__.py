@@ -74,7 +74,7 @@ _SIGS = {
     "nspt_polymat_mul_backward": (_i, [_vp, _vp, _vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_langevin_step": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_md_trajectory": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, _i, ctypes.POINTER(Opts), _vp]),
-    "nspt_tek_unitarize": (_i, [_vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
+    "nspt_tek_unitarize": (_i, [_vp, _i, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_order_fft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_order_ifft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_status_string": (ctypes.c_char_p, [_i]),
@@ -290,10 +290,11 @@ def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, n
     return U, P
 
 
-def tek_unitarize(U: torch.Tensor, **kw) -> torch.Tensor:
+def tek_unitarize(U: torch.Tensor, special: bool = False, **kw) -> torch.Tensor:
     """Unitarity projection in place: every series of U ((..., T+1, N, N), e.g. links
     (batch, 4, T+1, N, N)) becomes its polar factor U * (U^+ U)^(-1/2) in the truncated ring,
-    order 0 kept (see include/nspt.h).  kw: algo, prec, fft_len, slices, rescale_log2r."""
+    order 0 kept; with special=True its U(1) phase is removed too (det U = det U^(0) through
+    order T; see include/nspt.h).  kw: algo, prec, fft_len, slices, rescale_log2r."""
     _check_tensor(U, "U")
     if U.dim() < 3 or U.shape[-1] != U.shape[-2]:
         raise ValueError("U must be (..., T+1, N, N)")
@@ -301,7 +302,8 @@ def tek_unitarize(U: torch.Tensor, **kw) -> torch.Tensor:
     nser = U.numel() // ((T + 1) * N * N)
     opts = make_opts(**kw)
     ws = _with_ws(OP_UNITARIZE, N, T, nser, opts, U.device)  # noqa: F841
-    rc = lib().nspt_tek_unitarize(U.data_ptr(), N, T, nser, ctypes.byref(opts), _stream_ptr(U.device))
+    rc = lib().nspt_tek_unitarize(U.data_ptr(), N, T, nser, int(bool(special)), ctypes.byref(opts),
+                                  _stream_ptr(U.device))
     _check(rc, "nspt_tek_unitarize")
     return U
 

@@ -595,7 +595,8 @@ int wilson_run(const Plan& p, const double2* U, int flux, int amax, double2* W, 
 // ---------------------------------------------------------------------------
 size_t ws_unitarize(const Plan& p) {
   const size_t ser = (size_t)p.batch * (p.T + 1) * p.E * sizeof(double2);
-  return 3 * al256(ser) + al256(ws_mul(p));
+  const size_t ph = (size_t)p.batch * (p.T + 1);  // phase a_k (double) and exp series (double2)
+  return 3 * al256(ser) + al256(ph * sizeof(double)) + al256(ph * sizeof(double2)) + al256(ws_mul(p));
 }
 
 double binom_minus_half(int n) {  // (-1)^n (2n)! / (4^n (n!)^2), by the ratio c_n / c_{n-1}
@@ -604,7 +605,7 @@ double binom_minus_half(int n) {  // (-1)^n (2n)! / (4^n (n!)^2), by the ratio c
   return c;
 }
 
-int unitarize_run(const Plan& p, double2* U, void* ws, cudaStream_t st) {
+int unitarize_run(const Plan& p, double2* U, int special, void* ws, cudaStream_t st) {
   const int N = p.N, T = p.T, nb = p.batch;
   const long long E = p.E, T1 = T + 1, ser = (long long)nb * T1 * E;
   char* base = (char*)ws;
@@ -612,6 +613,10 @@ int unitarize_run(const Plan& p, double2* U, void* ws, cudaStream_t st) {
   base += al256(ser * sizeof(double2));
   double2* S[2] = {(double2*)base, (double2*)(base + al256(ser * sizeof(double2)))};
   base += 2 * al256(ser * sizeof(double2));
+  double* phase = (double*)base;
+  base += al256((size_t)nb * T1 * sizeof(double));
+  double2* phs = (double2*)base;
+  base += al256((size_t)nb * T1 * sizeof(double2));
   void* mws = base;
   int rc;
   // D = U^+ * U - 1, with D^(0) = 0 (order 0 is unitary); U^+ goes through S[0]
@@ -632,6 +637,16 @@ int unitarize_run(const Plan& p, double2* U, void* ws, cudaStream_t st) {
   if (T >= 1)
     TRY(cudaMemcpy2DAsync(U + E, (size_t)T1 * E * sizeof(double2), D + E, (size_t)T1 * E * sizeof(double2),
                           (size_t)T * E * sizeof(double2), nb, cudaMemcpyDeviceToDevice, st));
+  if (!special || T < 1) return NSPT_OK;
+  // U(1) phase a(g) = Im Tr log(U0^+ U(g)) of the unitary series now in U, from Jacobi's
+  // formula: d/dg log det U = Tr(U^-1 U') = Tr(U^+ * U') (U unitary through order T), so
+  // a_k = Im Tr(U^+ * U')_(k-1) / k -- one product; then U <- U * exp(-i a / N) (scalar
+  // series), so that det U = det U0 through order T
+  TRY(nspt_series_dagger(U, S[0], N, (long long)nb * T1, st));
+  TRY(nspt_series_derivative(U, S[1], T, N, nb, st));
+  if ((rc = mul_plan(p, S[0], S[1], D, mws, st))) return rc;
+  TRY(nspt_series_imag_trace(D, phase, N, (long long)nb * T1, st));
+  TRY(nspt_series_remove_phase(U, phase, phs, T, N, nb, st));
   return NSPT_OK;
 }
 
@@ -833,7 +848,7 @@ int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void
                         (const double2*)gC, (double2*)gA, (double2*)gB, opts->workspace, st);
 }
 
-int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, void* stream) {
+int nspt_tek_unitarize(void* U, int N, int T, int batch, int special, const nspt_opts* opts, void* stream) {
   Plan p;
   int rc = make_plan(N, T, batch, opts, &p);
   if (rc) return rc;
@@ -844,7 +859,8 @@ int nspt_tek_unitarize(void* U, int N, int T, int batch, const nspt_opts* opts, 
     const void* ptrs[1] = {U};
     if ((rc = nspt_check_ptrs((cudaStream_t)stream, true, ptrs, 1))) return rc;
   }
-  return unitarize_run(p, (double2*)U, opts ? opts->workspace : nullptr, (cudaStream_t)stream);
+  if (special != 0 && special != 1) return NSPT_ERR_ARG;
+  return unitarize_run(p, (double2*)U, special, opts ? opts->workspace : nullptr, (cudaStream_t)stream);
 }
 
 int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, int T, int batch, int flux, double eps,

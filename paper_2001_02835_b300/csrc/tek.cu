@@ -335,3 +335,92 @@ cudaError_t nspt_series_order0_identity(double2* X, int T, int N, long long nser
   order0_identity_kernel<<<blocks_for(nseries * (long long)N * N), 256, 0, st>>>(X, T + 1, N, nseries, c, set);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// U(1) phase removal after the unitarity projection: the derivative series, Im Tr
+// per order, the phase series exp(-i a / N), and the scalar-series product
+// W_k = sum_j V_j s_(k-j).
+// ---------------------------------------------------------------------------
+namespace {
+
+// derivative series Y_j = (j + 1) V_(j+1), j < T, Y_T = 0, of every series
+__global__ void deriv_series_kernel(const double2* __restrict__ V, double2* __restrict__ Y, int T, int N,
+                                    long long nseries) {
+  const long long E = (long long)N * N;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseries * (T + 1) * E) return;
+  const long long e = i % E, j = (i / E) % (T + 1), q = i / ((T + 1) * E);
+  const double2* v = V + q * (T + 1) * E + e;
+  Y[i] = (j < T) ? make_double2((j + 1) * v[(j + 1) * E].x, (j + 1) * v[(j + 1) * E].y) : make_double2(0.0, 0.0);
+}
+
+// one thread per series: the phase a_k = t_(k-1) / k (t = Im Tr(V^+ * V') per order, so that
+// a' = t), and s_0 = 1, s_k = (1/k) sum_{j=1}^{k} j b_j s_(k-j) with b_j = -i a_j / N (the
+// coefficients of exp(b), from (exp b)' = b' exp b); j b_j = -i t_(j-1) / N
+__global__ void phase_series_kernel(const double* __restrict__ t, double2* __restrict__ sr, int T, int N,
+                                    long long nseries) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nseries) return;
+  const double* tq = t + q * (T + 1);
+  double2* s = sr + q * (T + 1);
+  s[0] = make_double2(1.0, 0.0);
+  for (int k = 1; k <= T; ++k) {
+    double re = 0.0, im = 0.0;
+    for (int j = 1; j <= k; ++j) {
+      // j b_j s_(k-j) = (-i x)(u + i v) = x v - i x u, x = j a_j / N = t_(j-1) / N
+      const double x = tq[j - 1] / N;
+      const double2 u = s[k - j];
+      re += x * u.y;
+      im -= x * u.x;
+    }
+    s[k] = make_double2(re / k, im / k);
+  }
+}
+
+// in place, one thread per entry of every series: V_k <- sum_{j<=k} V_j s_(k-j), k = T..1
+// (descending, so every V_j read is still the input); order 0 is unchanged since s_0 = 1
+__global__ void scalar_series_mul_kernel(double2* __restrict__ V, const double2* __restrict__ sr, int T, int N,
+                                         long long nseries) {
+  const long long E = (long long)N * N;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nseries * E) return;
+  const long long q = i / E, e = i % E;
+  double2* v = V + q * (T + 1) * E + e;
+  const double2* s = sr + q * (T + 1);
+  for (int k = T; k >= 1; --k) {
+    double re = 0.0, im = 0.0;
+    for (int j = 0; j <= k; ++j) {
+      const double2 x = v[(long long)j * E], y = s[k - j];
+      re += x.x * y.x - x.y * y.y;
+      im += x.x * y.y + x.y * y.x;
+    }
+    v[(long long)k * E] = make_double2(re, im);
+  }
+}
+
+}  // namespace
+
+cudaError_t nspt_series_derivative(const double2* V, double2* Y, int T, int N, long long nseries, cudaStream_t st) {
+  if (nseries <= 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  deriv_series_kernel<<<blocks_for(nseries * (T + 1) * (long long)N * N), 256, 0, st>>>(V, Y, T, N, nseries);
+  return cudaGetLastError();
+}
+
+cudaError_t nspt_series_imag_trace(const double2* X, double* out, int N, long long nmat, cudaStream_t st) {
+  if (nmat <= 0) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  imag_trace_kernel<<<(unsigned)((nmat + 7) / 8), 256, 0, st>>>(X, out, N, nmat);
+  return cudaGetLastError();
+}
+
+cudaError_t nspt_series_remove_phase(double2* V, const double* t, double2* sr, int T, int N, long long nseries,
+                                     cudaStream_t st) {
+  if (nseries <= 0 || T < 1) return cudaSuccess;
+  ProfScope ps(NSPT_STAGE_TEK, st);
+  phase_series_kernel<<<(unsigned)((nseries + 127) / 128), 128, 0, st>>>(t, sr, T, N, nseries);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  scalar_series_mul_kernel<<<blocks_for(nseries * (long long)N * N), 256, 0, st>>>(V, sr, T, N, nseries);
+  return cudaGetLastError();
+}

@@ -82,3 +82,10 @@ cudaError_t nspt_wilson_combine(const double2* tr, double2* W, int nplanes, int 
 cudaError_t nspt_series_dagger(const double2* X, double2* Y, int N, long long nmat, cudaStream_t st);
 cudaError_t nspt_series_order0_identity(double2* X, int T, int N, long long nseries, double c, int set,
                                         cudaStream_t st);
+// U(1) phase removal: Y_j = (j + 1) V_(j+1) (Y_T = 0); out[m] = sum_i Im X[m]_ii for nmat
+// matrices; V_k <- sum_j V_j s_(k-j) in place with s = exp(-i a / N), a_k = t_(k-1) / k for
+// t [nseries][T+1] (t_k = Im Tr(V^+ * V')_k), sr [nseries][T+1] scratch
+cudaError_t nspt_series_derivative(const double2* V, double2* Y, int T, int N, long long nseries, cudaStream_t st);
+cudaError_t nspt_series_imag_trace(const double2* X, double* out, int N, long long nmat, cudaStream_t st);
+cudaError_t nspt_series_remove_phase(double2* V, const double* a, double2* sr, int T, int N, long long nseries,
+                                     cudaStream_t st);

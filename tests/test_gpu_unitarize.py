@@ -102,10 +102,44 @@ def test_unitarize_argument_checks(nspt):
     L = nspt.lib()
     o = nspt.make_opts(algo="fft", prec="fp64")
     x = torch.zeros((1, 3, 4, 4), dtype=torch.complex128, device="cuda")
-    assert L.nspt_tek_unitarize(None, 4, 2, 1, ctypes.byref(o), None) == -1
-    assert L.nspt_tek_unitarize(x.data_ptr(), 4, 2, 1, ctypes.byref(o), None) == -4   # no workspace
+    assert L.nspt_tek_unitarize(None, 4, 2, 1, 0, ctypes.byref(o), None) == -1
+    assert L.nspt_tek_unitarize(x.data_ptr(), 4, 2, 1, 0, ctypes.byref(o), None) == -4   # no workspace
+    ws = nspt._with_ws(nspt.OP_UNITARIZE, 4, 2, 1, o, x.device)  # noqa: F841
+    assert L.nspt_tek_unitarize(x.data_ptr(), 4, 2, 1, 2, ctypes.byref(o), None) == -1   # special: 0 or 1
     # the fitted per-order rescale is allowed (one fit per product, on the device)
     tU = dev(near_unitary_links(syn.rng(9500), 2, 1, 6, 1))
     ref = tek.unitarize(host(tU))
     nspt.tek_unitarize(tU, algo="fft", prec="fp64", rescale_log2r=nspt.RESCALE_AUTO)
     assert max_order_rel(host(tU), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("algo,prec", FORMS)
+@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 6, 2), (2, 1, 1, 1), (5, 2, 15, 1), (11, 3, 31, 1)])
+def test_unitarize_special_matches_oracle(nspt, algo, prec, L, flux, T, streams):
+    """The projection with the U(1) phase removed: every order against the oracle, and
+    det V^(k) conditions through the oracle's det-preserving result (checked on the CPU)."""
+    if L == 11 and algo == "naive":
+        pytest.skip("the naive form at SU(121), O(g^31) adds nothing over the FFT forms here")
+    g = syn.rng(9800 + 10 * L + T)
+    N = L * L
+    U = near_unitary_links(g, L, flux, T, streams)
+    # a U(1) drift on top: every series times exp(i c g) with a seeded c per series
+    c = g.normal(size=(streams, 4)) * 0.3
+    ph = tek.scalar_exp(np.concatenate([np.zeros((streams, 4, 1)), 1j * c[..., None],
+                                        np.zeros((streams, 4, T - 1))], axis=-1)) if T >= 1 else None
+    if ph is not None:
+        Ur = np.zeros_like(U)
+        for k in range(T + 1):
+            for j in range(k + 1):
+                Ur[:, :, k] += U[:, :, j] * ph[:, :, k - j, None, None]
+        U = Ur
+    ref = tek.unitarize(U, special=True)
+    res = {}
+    for r in ([0, nspt.RESCALE_AUTO] if algo == "fft" else [0]):
+        tU = dev(U)
+        nspt.tek_unitarize(tU, special=True, algo=algo, prec=prec, rescale_log2r=r)
+        got = host(tU)
+        np.testing.assert_array_equal(got[:, :, 0], U[:, :, 0])
+        res[r] = max_order_rel(got, ref)
+    record("unitarize_special", algo=algo, prec=prec, N=N, T=T, err=res[0], err_auto=res.get(nspt.RESCALE_AUTO))
+    assert res[0] <= _tol(prec, T), res

@@ -786,3 +786,22 @@ def test_u1_phase_removal_keeps_special_unitary_series():
         for j in range(kk + 1):
             Ur[:, kk] += U[:, j] * ph[kk - j]
     np.testing.assert_allclose(tek.unitarize(Ur, special=True), U, atol=1e-12)
+
+
+def test_u1_phase_from_jacobis_formula_equals_the_log_definition():
+    # for a unitary series V: Im Tr log(V0^+ V)_k = Im Tr(V^+ * V')_(k-1) / k, V'_j = (j+1) V_(j+1)
+    rg = syn.rng(76)
+    L, k, T = 3, 1, 8
+    U = tek.unitarize(syn.link_series(rg, L, k, T, 1)[0])
+    V0h = np.zeros_like(U)
+    V0h[:, 0] = np.conj(np.swapaxes(U[:, 0], -1, -2))
+    D = pm.star(V0h, U)
+    D[:, 0] = 0
+    a_log = np.imag(np.trace(tek.log_star_unit(D), axis1=-2, axis2=-1))
+    Vp = np.zeros_like(U)
+    Vp[:, :T] = U[:, 1:] * np.arange(1, T + 1)[None, :, None, None]
+    t = np.imag(np.trace(pm.star(pm.dagger(U), Vp), axis1=-2, axis2=-1))
+    a_jac = np.zeros_like(a_log)
+    a_jac[:, 1:] = t[:, :T] / np.arange(1, T + 1)[None, :]
+    np.testing.assert_allclose(a_jac, a_log, atol=1e-11 * np.abs(a_log).max())
+    assert np.abs(a_log[:, 1:]).max() > 1e-3
