@@ -376,9 +376,9 @@ def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     """One MD trajectory of the paper's length (40 leapfrog steps, momentum refreshed at its
     start) of one SU(225) configuration at O(g^31) in the split form, with the time split
     into the force phase (drift plus momentum kicks) and the link-update phase, and the
-    measurement of its Wilson loops up to 2 x 2.  The configuration starts at the twisted
-    vacuum and is thermalised by one untimed trajectory; the timed trajectory follows it
-    with fresh momenta."""
+    measurement of its Wilson loops up to 2 x 2 and the unitarity projection of its links.
+    The configuration starts at the twisted vacuum and is thermalised by one untimed
+    trajectory; the timed trajectory follows it with fresh momenta."""
     g = syn.rng(syn.SEED_BASE + 5)
     N = L * L
     tU = torch.from_numpy(np.ascontiguousarray(syn.vacuum_links(L, flux, T, 1))).cuda()
@@ -393,8 +393,12 @@ def md_leg(torch, nspt, barrier, L=15, T=31, flux=1, eps=0.02, nsteps=40):
     finite = bool(torch.isfinite(torch.view_as_real(tU)).all().item())
     umax = [float(x) for x in tU.abs()[0].amax(dim=(0, 2, 3)).cpu()]
     msw = time_steps(torch, lambda: nspt.tek_wilson_loops(tU, flux, 2, algo="fft", prec="split"), 2, 1, barrier) / 2
+    # the unitarity projection of the evolved links (polar factor and U(1) phase), on a copy
+    tW = tU.clone()
+    msu = time_steps(torch, lambda: nspt.tek_unitarize(tW, special=True, algo="fft", prec="split"), 2, 1, barrier) / 2
+    del tW
     out = {"ms_per_trajectory": ms, "md_steps": nsteps, "ms_per_md_step": ms / nsteps,
-           "wilson_loops_amax2_ms": msw,
+           "wilson_loops_amax2_ms": msw, "unitarity_projection_ms": msu,
            "force_ms": ph.get("md_force", (0.0, 0))[0], "link_update_ms": ph.get("md_link", (0.0, 0))[0],
            "kernel_stages_ms": {k: v[0] for k, v in ph.items() if k not in ("md_force", "md_link")},
            "links_finite": finite, "max_abs_link_order_0_8_16_24_31": [umax[k] for k in (0, 8, 16, 24, T)],
