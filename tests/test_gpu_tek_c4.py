@@ -140,6 +140,51 @@ def test_action_gradient_central_differences(nspt, c4):
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (mu, j, a, b, d, fd, an)
 
 
+def _oracle_action_fftconv(U, z):
+    """The truncated action (Eq. 1, beta stripped) of one stream by the oracle, with its
+    FFT-CONV product (direct DFTs, pinned against Eq. 5 on the CPU) for speed."""
+    from oracle import polymat as pm
+    N = U.shape[-1]
+    S = np.zeros(U.shape[-3], np.complex128)
+    for mu in range(4):
+        for nu in range(4):
+            if mu == nu:
+                continue
+            Um, Un = U[mu], U[nu]
+            P = pm.star_dftconv(pm.star_dftconv(pm.star_dftconv(Um, Un), pm.dagger(Um)), pm.dagger(Un))
+            S -= z[mu, nu] * np.trace(P, axis1=-2, axis2=-1)
+    S[0] += 12 * N
+    return S
+
+
+def test_weighted_action_gradient_vs_oracle_central_differences(nspt, c4):
+    """Loss = sum_k w_k Re S~^(k) with seeded w_k ~ N(0, 1) on stream 0 (every order of the
+    action, so every order of the backward's correlations): the autograd gradient through the
+    library's forward and backward kernels against central differences (h = 1e-6, FP64) of the
+    oracle's action at sampled link entries."""
+    z = c4["z"]
+    w = np.random.default_rng(41).normal(size=T + 1)
+    U0 = c4["tU"][:1].clone().requires_grad_(True)
+    S = action_series(nspt, U0, z)[0]
+    (S.real * torch.from_numpy(w).to(S.device)).sum().backward()
+    G = U0.grad[0]
+    Uh = c4["U"][0]
+    h = 1e-6
+    rs = np.random.default_rng(42)
+    for _ in range(2):
+        mu, j, a, b = int(rs.integers(4)), int(rs.integers(T + 1)), int(rs.integers(N)), int(rs.integers(N))
+        for d in (1.0, 1j):
+            Up, Um = Uh.copy(), Uh.copy()
+            Up[mu, j, a, b] += h * d
+            Um[mu, j, a, b] -= h * d
+            lp = float(np.dot(w, _oracle_action_fftconv(Up, z).real))
+            lm = float(np.dot(w, _oracle_action_fftconv(Um, z).real))
+            fd = (lp - lm) / (2 * h)
+            an = G[mu, j, a, b].real.item() if d == 1.0 else G[mu, j, a, b].imag.item()
+            record("c4_weighted_grad_fd", fd=fd, an=an)
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (mu, j, a, b, d, fd, an)
+
+
 def test_langevin_step_with_backward_drift(nspt, c4):
     """U' = exp_star(i X) * U with X from the backward-derived drift, composed from
     library products (Horner with shrinking truncation), equals the library's step."""
