@@ -72,3 +72,22 @@ def test_md_trajectory_with_fitted_rescale_replays_in_a_graph(nspt, prec):
         torch.cuda.synchronize()
         np.testing.assert_array_equal(host(Ug), host(Ue))
         np.testing.assert_array_equal(host(Pg), host(Pe))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_fitted_rescale_degenerate_inputs(nspt, prec):
+    """All-zero series, a single order (T = 0) and one nonzero order: the device fit has fewer
+    than two orders to fit and keeps r = 1; the products stay exact zeros or match the
+    fixed-rescale result bit for bit."""
+    z = torch.zeros((2, 8, 5, 5), dtype=torch.complex128, device="cuda")
+    C = nspt.polymat_mul(z, z, algo="fft", prec=prec, rescale_log2r=nspt.RESCALE_AUTO)
+    assert torch.count_nonzero(C).item() == 0
+    g = syn.rng(9900)
+    for T in (0, 5):
+        A = dev(syn.series_batch(g, 6, T, 2))
+        B = dev(syn.series_batch(g, 6, T, 2))
+        if T > 0:
+            A[:, 1:] = 0          # only order 0 nonzero in A: one usable order
+        ca = nspt.polymat_mul(A, B, algo="fft", prec=prec, rescale_log2r=nspt.RESCALE_AUTO)
+        c0 = nspt.polymat_mul(A, B, algo="fft", prec=prec, rescale_log2r=0)
+        np.testing.assert_array_equal(host(ca), host(c0))

@@ -114,7 +114,7 @@ def test_unitarize_argument_checks(nspt):
 
 
 @pytest.mark.parametrize("algo,prec", FORMS)
-@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 6, 2), (2, 1, 1, 1), (5, 2, 15, 1), (11, 3, 31, 1)])
+@pytest.mark.parametrize("L,flux,T,streams", [(3, 1, 6, 2), (2, 1, 0, 1), (2, 1, 1, 1), (5, 2, 15, 1), (11, 3, 31, 1)])
 def test_unitarize_special_matches_oracle(nspt, algo, prec, L, flux, T, streams):
     """The projection with the U(1) phase removed: every order against the oracle, and
     det V^(k) conditions through the oracle's det-preserving result (checked on the CPU)."""
