@@ -25,7 +25,7 @@ import paper_2001_02835_b300 as nspt  # noqa: E402
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["mul", "backward", "langevin", "md", "wilson"], default="mul")
+    ap.add_argument("--op", choices=["mul", "backward", "langevin", "md", "wilson", "unitarize"], default="mul")
     ap.add_argument("--algo", default="fft")
     ap.add_argument("--prec", default="split")
     ap.add_argument("--N", type=int, default=225)
@@ -47,6 +47,18 @@ def main(argv=None):
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
         eta = torch.from_numpy(np.ascontiguousarray(syn.hermitian_noise(g, a.N, 4 * a.batch).reshape(a.batch, 4, a.N, a.N))).cuda()
         fn = lambda: nspt.tek_langevin_step(U, eta, 1, 0.01, **kw)  # noqa: E731
+    elif a.op == "unitarize":
+        # the projection with the U(1) phase removed, on links with Gaussian higher orders scaled
+        # down to a small drift from unitarity, on a copy per call
+        L = int(round(a.N ** 0.5))
+        U0 = syn.link_series(g, L, 1, a.T, a.batch)
+        U0[:, :, 1:] *= 1e-2
+        U0 = torch.from_numpy(np.ascontiguousarray(U0)).cuda()
+        U = torch.empty_like(U0)
+
+        def fn():
+            U.copy_(U0)
+            nspt.tek_unitarize(U, special=True, **kw)
     elif a.op == "wilson":
         L = int(round(a.N ** 0.5))
         U = torch.from_numpy(np.ascontiguousarray(syn.link_series(g, L, 1, a.T, a.batch))).cuda()
