@@ -20,9 +20,10 @@ Chained computations (the Langevin step, MD, the Wilson loops) mix the orders in
 product of the chain, and their error grows with the truncation order beyond T ~ 24 in
 the FP64 FFT form as much as in the split form (the split/FP64 error ratio stays near
 100 at every T); the bound for them is CHAIN[kind] * 2^max(0, (T - 24)/8) times the
-product bound, with CHAIN calibrated the same way (largest observed ratio to the product
-bound 0.42 for the Langevin step and 0.38 for MD at SU(121), O(g^31), 2.4 for the Wilson
-loops there).
+product bound, with CHAIN calibrated the same way: four times the largest observed ratio to
+the product bound times the growth, rounded (0.42 for the Langevin step at SU(121), O(g^31);
+1.48 for one MD step at SU(225), O(g^31) with the fitted rescale; 2.4 for the Wilson loops at
+SU(121), O(g^31)).
 """
 import json
 import os
@@ -35,7 +36,7 @@ C_OBS = 64.0                  # max err / 2^-(8S-1) over the product cases, S <=
 F_OBS = 2.0 ** -45            # max err of the product cases at S = 7, 8
 SPLIT_C = 4 * C_OBS
 SPLIT_FLOOR = 4 * F_OBS
-CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 2.0, "wilson": 8.0, "unitarize": 2.0}
+CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 6.0, "wilson": 8.0, "unitarize": 2.0}
 
 
 def dev(x: np.ndarray) -> torch.Tensor:
