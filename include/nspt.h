@@ -167,8 +167,11 @@ NSPT_API int nspt_tek_langevin_step(void* U, const void* eta, void* F, int N, in
  * special = 0 stops at the polar factor.  Other values: NSPT_ERR_ARG.
  *   U : [batch][T+1][N][N] complex128, updated in place (a link tensor
  *       [b][4][T+1][N][N] is batch = 4 b series)
- * T + 2 products (T + 3 with special = 1) per call.  Workspace: NSPT_OP_UNITARIZE.  A fixed rescale applies to
- * every product; NSPT_RESCALE_AUTO fits one per product.
+ * T + 2 products (T + 3 with special = 1) per call.  Workspace: NSPT_OP_UNITARIZE.
+ * A fixed rescale applies to every product; NSPT_RESCALE_AUTO fits one per product.
+ * The projection is well conditioned for the series it is for (unitary ones with a small
+ * drift); far from unitary, its high orders come out of the cancellation of much larger
+ * terms and lose accuracy.
  */
 NSPT_API int nspt_tek_unitarize(void* U, int N, int T, int batch, int special, const nspt_opts* opts,
                                 void* stream);
