@@ -91,3 +91,27 @@ def test_fitted_rescale_degenerate_inputs(nspt, prec):
         ca = nspt.polymat_mul(A, B, algo="fft", prec=prec, rescale_log2r=nspt.RESCALE_AUTO)
         c0 = nspt.polymat_mul(A, B, algo="fft", prec=prec, rescale_log2r=0)
         np.testing.assert_array_equal(host(ca), host(c0))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "split"])
+def test_wilson_loops_and_projection_with_fitted_rescale_replay_in_a_graph(nspt, prec):
+    """Every product of the Wilson-loop measurement and of the unitarity projection (U(1) phase
+    included) fits its rescale on the device, so both calls capture and replay bit for bit."""
+    L, flux, T = 3, 1, 12
+    U0 = dev(decaying_links(L, flux, T, 1, 9800))
+    kw = dict(algo="fft", prec=prec, rescale_log2r=nspt.RESCALE_AUTO)
+    We = nspt.tek_wilson_loops(U0, flux, 2, **kw)
+    Ve = U0.clone()
+    nspt.tek_unitarize(Ve, special=True, **kw)
+    Ug = U0.clone()
+    Vg = U0.clone()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        Wg = nspt.tek_wilson_loops(Ug, flux, 2, **kw)
+        nspt.tek_unitarize(Vg, special=True, **kw)
+    Vg.copy_(U0)
+    graph.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(Wg), host(We))
+    np.testing.assert_array_equal(host(Vg), host(Ve))

@@ -78,6 +78,21 @@ def test_grouped_split_cuda_graph_replay(nspt):
         np.testing.assert_array_equal(host(Cs[i]), eager[i])
 
 
+def test_grouped_fp64_cuda_graph_replay(nspt):
+    """The FP64 form of the grouped call (products one after another) captures too."""
+    As, Bs = make_group(6250, SIZES[:4])
+    dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
+    eager = [host(c) for c in nspt.polymat_mul_grouped(dA, dB, prec="fp64")]
+    Cs = [torch.zeros_like(a) for a in dA]
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        nspt.polymat_mul_grouped(dA, dB, Cs, prec="fp64")
+    graph.replay()
+    for i in range(len(Cs)):
+        np.testing.assert_array_equal(host(Cs[i]), eager[i])
+
+
 def test_autotuner_picks_a_width_and_caches_it(nspt):
     As, Bs = make_group(6300, [(121, 15, 1), (49, 31, 1), (169, 15, 1)])
     dA, dB = [dev(a) for a in As], [dev(b) for b in Bs]
