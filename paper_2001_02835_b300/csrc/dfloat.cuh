@@ -90,6 +90,45 @@ __device__ __forceinline__ cdf cdf_mul(cdf a, dfl c, dfl s) {
   return cdf{df_fast(r.re.h, r.re.l), df_fast(r.im.h, r.im.l)};
 }
 
+// ---- sums on a common grid (inside one radix-4 butterfly of the transforms) ----
+// The high parts of a butterfly's inputs are first rounded to one grid u, a power
+// of two, and the remainders join the low parts (exact: h = g + (h - g)).  With
+// every input below 2^(E+1) in magnitude and u = 2^(E-21), any sum of up to four
+// high parts is a multiple of u of at most 2^(E+3) = 2^24 u, so a single FP32
+// addition forms it exactly; only the low parts round.  A sum then costs two
+// additions instead of the eight to eleven of TwoSum-based double-float.  The
+// price is that a value's error is bounded relative to the butterfly's largest
+// input (about 2^-45 of it per step) rather than to the value itself.
+//
+// K = 1.5 * 2^(E+2) is the rounding constant: for |h| < 2^(E+1) = K/3, h + K
+// lies in [2^(E+2), 2^(E+3)], whose spacing is u, so fl(h + K) - K is h rounded
+// to the grid (the subtraction is exact by Sterbenz's lemma).  amax is the
+// largest |hi| of the butterfly's inputs; its exponent field gives E.  Zero or
+// subnormal amax gives a grid at the bottom of the FP32 range.
+__device__ __forceinline__ float grid_magic(float amax) {
+  unsigned ex = (__float_as_uint(amax) & 0x7F800000u) + (2u << 23);
+  ex = min(ex, 254u << 23);
+  return __uint_as_float(ex | 0x00400000u);
+}
+__device__ __forceinline__ dfl df_regrid(dfl a, float K) {
+  const float g = __fsub_rn(__fadd_rn(a.h, K), K);
+  return dfl{g, __fadd_rn(__fsub_rn(a.h, g), a.l)};
+}
+__device__ __forceinline__ cdf cdf_regrid(cdf a, float K) { return cdf{df_regrid(a.re, K), df_regrid(a.im, K)}; }
+__device__ __forceinline__ float cdf_amax(cdf a) { return fmaxf(fabsf(a.re.h), fabsf(a.im.h)); }
+// sums of two values on the same grid: the high part is exact, the low part rounds
+__device__ __forceinline__ cdf cg_add(cdf a, cdf b) {
+  return cdf{dfl{__fadd_rn(a.re.h, b.re.h), __fadd_rn(a.re.l, b.re.l)},
+             dfl{__fadd_rn(a.im.h, b.im.h), __fadd_rn(a.im.l, b.im.l)}};
+}
+__device__ __forceinline__ cdf cg_sub(cdf a, cdf b) {
+  return cdf{dfl{__fsub_rn(a.re.h, b.re.h), __fsub_rn(a.re.l, b.re.l)},
+             dfl{__fsub_rn(a.im.h, b.im.h), __fsub_rn(a.im.l, b.im.l)}};
+}
+// multiplication by i and by -i (exact)
+__device__ __forceinline__ cdf cdf_mul_i(cdf a) { return cdf{df_neg(a.im), a.re}; }
+__device__ __forceinline__ cdf cdf_mul_mi(cdf a) { return cdf{a.im, df_neg(a.re)}; }
+
 // 2^k as a float for -252 <= k <= 254 (two factors keep it exact)
 __device__ __forceinline__ void pow2_pair(int k, float& f1, float& f2) {
   const int k1 = k / 2, k2 = k - k1;

@@ -55,7 +55,32 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
     valid = j < N && l < N;
     src = in + (long long)b * in_stride * E + (long long)j * N + l;
   }
-  fftdf::fwd_to_smem<M, EB>(sm, src, E, valid, T, log2s, log2r);
+  if constexpr (M == 64 || M == 128) {
+    constexpr int GPT = fftdf::RegFft<M>::GPT;
+    cdf z[GPT][8];
+    fftdf::fwd_regs<M, EB>(sm, src, E, valid, T, log2s, log2r, z);
+    if (!TOUT) {
+      if (!valid) return;
+      float4* dst = out + (long long)b * M * E + e0 + e;
+#pragma unroll
+      for (int t = 0; t < GPT; ++t)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int i = 8 * (y * GPT + t) + j;
+          st(&dst[(long long)bitrev<M>(i) * E], z[t][j]);
+        }
+      return;
+    }
+    // transposed output: back to shared memory (rows this thread read in the exchange), then
+    // the block store below
+#pragma unroll
+    for (int t = 0; t < GPT; ++t)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) st(&sm[(8 * (y * GPT + t) + j) * EB + e], z[t][j]);
+    __syncthreads();
+  } else {
+    fftdf::fwd_to_smem<M, EB>(sm, src, E, valid, T, log2s, log2r);
+  }
   if (TOUT) {
     // this thread stores smem column c = entry (j0 + e % 8, l0 + e / 8) at (l, j)
     const int jj = e % 8, ll = e / 8, c = jj * CB + ll;
@@ -79,6 +104,80 @@ __device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
   return df_fast(p, e);
 }
 
+// DIT radix-2^2 butterfly (after the step's twiddles), sums on a common grid:
+// a <- (a + b) + (c + d), b <- (a - b) - i (c - d), c <- (a + b) - (c + d), d <- (a - b) + i (c - d).
+__device__ __forceinline__ void dit4_grid(cdf& a, cdf& b, cdf& c, cdf& d) {
+  const float K = grid_magic(fftdf::cdf_amax4(a, b, c, d));
+  a = cdf_regrid(a, K); b = cdf_regrid(b, K); c = cdf_regrid(c, K); d = cdf_regrid(d, K);
+  const cdf apb = cg_add(a, b), amb = cg_sub(a, b), cpd = cg_add(c, d);
+  const cdf mi = cdf_mul_mi(cg_sub(c, d));  // (-i)(c - d)
+  a = cg_add(apb, cpd); b = cg_add(amb, mi); c = cg_sub(apb, cpd); d = cg_sub(amb, mi);
+}
+
+// One DIT radix-2^2 step over spans (H, 2H), sums on a common grid: for the
+// group of size 4H at g * 4H and n < H, with x_m = row g*4H + n + m*H and
+// j = n * M / (4H), the inputs x1, x2, x3 are first multiplied by w^-2j, w^-j,
+// w^-3j, then
+//   o0 = (x0 + x1) + (x2 + x3),   o1 = (x0 - x1) - i (x2 - x3),
+//   o2 = (x0 + x1) - (x2 + x3),   o3 = (x0 - x1) + i (x2 - x3).
+template <int M, int EB, int H>
+__device__ __forceinline__ void dit4_stage(float4* sm) {
+  constexpr int LH = fftdf::ilog2<H>(), TS = M / (4 * H);
+  const int e = threadIdx.x, y = threadIdx.y;
+  // with H <= 8 every butterfly of this thread has n = y mod H: one twiddle set
+  fftdf::Tw3<M, true> t;
+  if (H <= 8) t.load((y & (H - 1)) * TS);
+#pragma unroll
+  for (int u = y; u < M / 4; u += 8) {
+    const int g = u >> LH, n = u & (H - 1);
+    const int base = g * 4 * H + n;
+    cdf a = ld(&sm[base * EB + e]), bq = ld(&sm[(base + H) * EB + e]);
+    cdf c = ld(&sm[(base + 2 * H) * EB + e]), d = ld(&sm[(base + 3 * H) * EB + e]);
+    if (H > 8) t.load(n * TS);
+    t.apply(bq, c, d);
+    dit4_grid(a, bq, c, d);
+    st(&sm[base * EB + e], a);
+    st(&sm[(base + H) * EB + e], bq);
+    st(&sm[(base + 2 * H) * EB + e], c);
+    st(&sm[(base + 3 * H) * EB + e], d);
+  }
+}
+
+// One DIT radix-2 step of span H (normalised double-float sums).
+template <int M, int EB, int H>
+__device__ __forceinline__ void dit2_stage(float4* sm) {
+  constexpr int LH = fftdf::ilog2<H>(), TS = M / (2 * H);
+  const int e = threadIdx.x, y = threadIdx.y;
+#pragma unroll
+  for (int bf = y; bf < M / 2; bf += 8) {
+    const int g = bf >> LH, j = bf & (H - 1);
+    const int i0 = g * 2 * H + j, i1 = i0 + H;
+    const cdf u = ld(&sm[i0 * EB + e]);
+    cdf v = ld(&sm[i1 * EB + e]);
+    if (j != 0) {
+      dfl c, s;
+      tw(j * TS, M, true, c, s);
+      v = cdf_mul_lazy(v, c, s);
+    }
+    st(&sm[i0 * EB + e], cdf_add(u, v));
+    st(&sm[i1 * EB + e], cdf_sub(u, v));
+  }
+}
+
+// DIT steps of spans H, 4H, ... while two are left below M/2, then one radix-2
+// step if one is; the last stage (span M/2) is fused into the output.
+template <int M, int EB, int H>
+__device__ __forceinline__ void dit_stages(float4* sm) {
+  if constexpr (2 * H <= M / 4) {
+    dit4_stage<M, EB, H>(sm);
+    __syncthreads();
+    dit_stages<M, EB, 4 * H>(sm);
+  } else if constexpr (H <= M / 4) {
+    dit2_stage<M, EB, H>(sm);
+    __syncthreads();
+  }
+}
+
 // post: extra real double-float factor on the result; add_identity: + 1 on the
 // diagonal of order 0 (entry e is (e / N, e % N)); orders below kmin are not stored
 template <int M, int EB>
@@ -92,6 +191,20 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
   const long long e0 = (long long)blockIdx.x * EB;
   const bool valid = (e0 + e) < E;
   const float4* src = in + (long long)b * M * E + e0 + e;
+  constexpr int LOGM = 31 - __builtin_clz(M);
+  const long long ent = e0 + e;
+  const bool diag = add_identity && (ent / N) == (ent % N);
+  const bool scaled = !(post_h == 1.f && post_l == 0.f);
+  double2* dst = out + (long long)b * out_stride * E + e0 + e;
+  // order k: scaled by 2^(log2u - k log2r) / M and by post, + 1 on the diagonal of order 0
+  auto put = [&](int k, cdf r) {
+    float f1, f2;
+    pow2_pair(log2u - k * log2r - LOGM, f1, f2);
+    r = cdf{df_scale(df_scale(r.re, f1), f2), df_scale(df_scale(r.im, f1), f2)};
+    if (scaled) r = cdf{df_mul(r.re, dfl{post_h, post_l}), df_mul(r.im, dfl{post_h, post_l})};
+    if (diag && k == 0) r.re = df_add(r.re, dfl{1.f, 0.f});
+    dst[(long long)k * E] = make_double2(df_to_double(r.re), df_to_double(r.im));  // hi + lo in FP64
+  };
   // loads in groups of up to 16 per thread, all in flight before their stores
   constexpr int NL = (M + 7) / 8, G = NL < 16 ? NL : 16;
 #pragma unroll 1
@@ -109,56 +222,8 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
     }
   }
   __syncthreads();
-  // DIT stages of spans 1 .. M/4: radix 2^2 steps over spans (h, 2h) while two are left
-  int h = 1;
-#pragma unroll 1
-  for (; 2 * h <= M / 4; h <<= 2) {
-    const int tstep = M / (4 * h);  // w_L^-m = conj(w_M^(m M / L)), L = 4h
-    for (int u = y; u < M / 4; u += 8) {
-      const int g = u >> (__ffs(h) - 1), n = u & (h - 1);  // h is a power of two
-      const int base = g * 4 * h + n;
-      cdf a = ld(&sm[base * EB + e]), bq = ld(&sm[(base + h) * EB + e]);
-      cdf c = ld(&sm[(base + 2 * h) * EB + e]), d = ld(&sm[(base + 3 * h) * EB + e]);
-      if (n != 0) {
-        dfl cw, sw;
-        tw(2 * n * tstep, M, true, cw, sw); bq = cdf_mul_lazy(bq, cw, sw);
-        tw(n * tstep, M, true, cw, sw);     c = cdf_mul_lazy(c, cw, sw);
-        tw(3 * n * tstep, M, true, cw, sw); d = cdf_mul_lazy(d, cw, sw);
-      }
-      // first-layer sums feed only the second layer, which renormalises
-      const cdf apb = cdf_add_lazy(a, bq), amb = cdf_sub_lazy(a, bq);
-      const cdf cpd = cdf_add_lazy(c, d), cmd = cdf_sub_lazy(c, d);
-      const cdf mi = cdf{cmd.im, df_neg(cmd.re)};  // (-i)(c - d)
-      st(&sm[base * EB + e], cdf_add(apb, cpd));
-      st(&sm[(base + h) * EB + e], cdf_add(amb, mi));
-      st(&sm[(base + 2 * h) * EB + e], cdf_sub(apb, cpd));
-      st(&sm[(base + 3 * h) * EB + e], cdf_sub(amb, mi));
-    }
-    __syncthreads();
-  }
-  if (h <= M / 4) {  // one radix-2 DIT stage of span h left
-    const int tstep = M / (2 * h);
-    for (int bf = y; bf < M / 2; bf += 8) {
-      const int g = bf >> (__ffs(h) - 1), j = bf & (h - 1);
-      const int i0 = g * 2 * h + j, i1 = i0 + h;
-      const cdf u = ld(&sm[i0 * EB + e]);
-      cdf v = ld(&sm[i1 * EB + e]);
-      if (j != 0) {
-        dfl c, s;
-        tw(j * tstep, M, true, c, s);
-        v = cdf_mul_lazy(v, c, s);
-      }
-      st(&sm[i0 * EB + e], cdf_add(u, v));
-      st(&sm[i1 * EB + e], cdf_sub(u, v));
-    }
-    __syncthreads();
-  }
+  dit_stages<M, EB, 1>(sm);
   if (!valid) return;
-  double2* dst = out + (long long)b * out_stride * E + e0 + e;
-  constexpr int LOGM = 31 - __builtin_clz(M);
-  const long long ent = e0 + e;
-  const bool diag = add_identity && (ent / N) == (ent % N);
-  const bool scaled = !(post_h == 1.f && post_l == 0.f);
   for (int k = y; k <= T; k += 8) {
     if (k < kmin) continue;
     const cdf u = ld(&sm[k * EB + e]);
@@ -168,13 +233,7 @@ fft_inv_df_kernel(const float4* __restrict__ in, double2* __restrict__ out, long
       tw(k, M, true, c, s);
       v = cdf_mul_lazy(v, c, s);
     }
-    cdf r = cdf_add_lazy(u, v);  // converted to FP64 as hi + lo, exact either way
-    float f1, f2;
-    pow2_pair(log2u - k * log2r - LOGM, f1, f2);
-    r = cdf{df_scale(df_scale(r.re, f1), f2), df_scale(df_scale(r.im, f1), f2)};
-    if (scaled) r = cdf{df_mul(r.re, dfl{post_h, post_l}), df_mul(r.im, dfl{post_h, post_l})};
-    if (diag && k == 0) r.re = df_add(r.re, dfl{1.f, 0.f});
-    dst[(long long)k * E] = make_double2(df_to_double(r.re), df_to_double(r.im));
+    put(k, cdf_add_lazy(u, v));
   }
 }
 

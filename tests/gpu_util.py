@@ -6,24 +6,25 @@ against the largest order's norm instead.
 
 Split-form bound.  With S digit slices every spectrum row (column) is carried to 8S - 1
 bits below its largest entry, so a product's per-order relative error is
-c * 2^-(8S-1), plus a floor f from the double-float transforms (about 48 bits).  c and f
-were calibrated once on B300 from the parity cases themselves (every product case of
-the tests, the benchmarked SU(225), O(g^63) batch and the 64-product group, S = 2..8):
-the largest observed err / 2^-(8S-1) at S <= 6 was 62 (order 0 of the SU(225), O(g^63)
-product), so C_OBS = 64, and the S = 7, 8 results, which the floor dominates, stayed below
-F_OBS = 2^-45.  The stated bound takes four times both:
-    split_bound(S) = 256 * 2^-(8S-1) + 2^-43      (2^-39 + 2^-43 = 1.9e-12 at S = 6),
-which is the unit of the last digit with S - 1 slices: the result with one slice fewer
-(observed 40..60 times that unit) fails it.
+c * 2^-(8S-1), plus a floor f from the double-float transforms (about 45 bits: their sums
+are formed on a common grid per butterfly, so each step's error is bounded relative to
+the butterfly's largest input).  c and f were calibrated on B300 from the parity cases
+themselves (every product case of the tests, the benchmarked SU(225), O(g^63) batch and the
+64-product group, S = 2..8): the largest observed err / 2^-(8S-1) at S <= 6 was 84 (an
+SU(6), O(g^200) product, M = 512), so C_OBS = 84, and the S = 7, 8 results, which the floor
+dominates, stayed below F_OBS = 2^-44.  The stated bound takes four times both:
+    split_bound(S) = 336 * 2^-(8S-1) + 2^-42      (2.4e-12 + 2.3e-13 = 2.6e-12 at S = 6),
+1.3 units of the last digit with S - 1 slices: the result with one slice fewer (observed 6
+to 60 such units at N >= 9) fails it.
 
 Chained computations (the Langevin step, MD, the Wilson loops) mix the orders in every
 product of the chain, and their error grows with the truncation order beyond T ~ 24 in
 the FP64 FFT form as much as in the split form (the split/FP64 error ratio stays near
 100 at every T); the bound for them is CHAIN[kind] * 2^max(0, (T - 24)/8) times the
-product bound, with CHAIN calibrated the same way: four times the largest observed ratio to
-the product bound times the growth, rounded (0.42 for the Langevin step at SU(121), O(g^31);
-1.48 for one MD step at SU(225), O(g^31) with the fitted rescale; 2.4 for the Wilson loops at
-SU(121), O(g^31)).
+product bound, with CHAIN at least four times the largest observed ratio to the product
+bound times the growth (0.34 for the Langevin step at SU(121), O(g^31); 1.09 for one MD step
+at SU(225), O(g^31) with the fitted rescale; 1.72 for the Wilson loops at SU(121), O(g^31);
+0.21 for the backward; 0.14 for the unitarity projection).
 """
 import json
 import os
@@ -32,8 +33,8 @@ import numpy as np
 import torch
 
 # calibration constants (see the module docstring)
-C_OBS = 64.0                  # max err / 2^-(8S-1) over the product cases, S <= 6
-F_OBS = 2.0 ** -45            # max err of the product cases at S = 7, 8
+C_OBS = 84.0                  # max err / 2^-(8S-1) over the product cases, S <= 6
+F_OBS = 2.0 ** -44            # max err of the product cases at S = 7, 8
 SPLIT_C = 4 * C_OBS
 SPLIT_FLOOR = 4 * F_OBS
 CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 6.0, "wilson": 8.0, "unitarize": 2.0}
