@@ -157,14 +157,25 @@ __device__ __forceinline__ dfl df_from_double(double x) {
   return dfl{h, l};
 }
 
-// float -> FP64 by bit assembly (normal floats; zero and denormals exactly)
+// float -> FP64 by bit assembly, subnormal floats normalised with a leading-zero
+// count; integer operations only (no FP64-pipe conversion).
 __device__ __forceinline__ double f2d(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ef = (u >> 23) & 0xFF;
-  if (ef == 0 || ef == 255) return (double)f;
-  const unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
-                                  ((unsigned long long)(ef - 127 + 1023) << 52) |
-                                  ((unsigned long long)(u & 0x7FFFFF) << 29);
+  const unsigned m = u & 0x7FFFFF;
+  const unsigned long long sign = (unsigned long long)(u >> 31) << 63;
+  unsigned long long bits;
+  if (ef == 0) {
+    // m 2^-149 with the leading one at bit p: exponent p - 149, fraction m << (52 - p)
+    const int p = 31 - __clz(m | 1u);
+    bits = m ? (sign | ((unsigned long long)(p - 149 + 1023) << 52) |
+                (((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull))
+             : sign;
+  } else if (ef == 255) {
+    bits = sign | 0x7FF0000000000000ull | ((unsigned long long)m << 29);
+  } else {
+    bits = sign | ((unsigned long long)(ef - 127 + 1023) << 52) | ((unsigned long long)m << 29);
+  }
   return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return f2d(a.h) + f2d(a.l); }
