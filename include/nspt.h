@@ -75,7 +75,11 @@ typedef struct nspt_opts {
   int fft_len;         /* M; 0 = smallest power of two >= 2(T+1); else a power of two
                           >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
-  int complex_mode;    /* split form: 4 (four real products per complex product); 0 = 4 */
+  int complex_mode;    /* split form: real products per complex product of the mode GEMMs: 4 (the
+                          complex product embedded in real MMAs; every entry point), or 3 (3M:
+                          A_re B_re, A_im B_im, (A_re + A_im)(B_re + B_im); nspt_polymat_mul and
+                          its workspace query only, with slices <= 6 and N <= 512, else
+                          NSPT_ERR_UNSUPPORTED); 0 = 4 */
   int rescale_log2r;   /* per-order rescale A_k, B_k -> r^k A_k, r^k B_k with r = 2^rescale_log2r,
                           undone exactly on C (not part of the paper): FFT-CONV products (split
                           and FP64 forms, the FP64 backward excepted); split and FP64 FFT forms

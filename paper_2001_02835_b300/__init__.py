@@ -125,7 +125,7 @@ def _prec(p) -> int:
     return {"fp64": PREC_FP64, "split": PREC_SPLIT}.get(p, p)
 
 
-def make_opts(algo="auto", prec="fp64", fft_len=0, slices=0, rescale_log2r=0) -> Opts:
+def make_opts(algo="auto", prec="fp64", fft_len=0, slices=0, rescale_log2r=0, complex_mode=0) -> Opts:
     o = Opts()
     lib().nspt_opts_default(ctypes.byref(o))
     o.algo = _algo(algo)
@@ -133,6 +133,7 @@ def make_opts(algo="auto", prec="fp64", fft_len=0, slices=0, rescale_log2r=0) ->
     o.fft_len = int(fft_len)
     o.slices = int(slices)
     o.rescale_log2r = int(rescale_log2r)
+    o.complex_mode = int(complex_mode)
     return o
 
 
@@ -185,7 +186,8 @@ def _with_ws(op, N, T, batch, opts, device):
 
 
 def polymat_mul(A: torch.Tensor, B: torch.Tensor, C: Optional[torch.Tensor] = None, **kw) -> torch.Tensor:
-    """C = A star B (Eq. 5) through nspt_polymat_mul; kw: algo, prec, fft_len, slices, rescale_log2r."""
+    """C = A star B (Eq. 5) through nspt_polymat_mul; kw: algo, prec, fft_len, slices, rescale_log2r,
+    complex_mode (split form: 4, or 3 for three real products per complex product)."""
     _check_tensor(A, "A")
     _check_tensor(B, "B")
     if A.shape != B.shape:

@@ -35,9 +35,11 @@ struct Plan {
   long long E;
   int algo, prec, M, slices, log2r;
   bool rescale_auto;
+  int cm;  // split form: real products per complex product (4, or 3 for 3M)
 };
 
-int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p) {
+// allow_3m: the entry point takes complex_mode = 3 (the plain product)
+int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool allow_3m = false) {
   nspt_opts d;
   nspt_opts_default(&d);
   if (!o) o = &d;
@@ -52,7 +54,14 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p) {
   if (ilog2_exact(p->M) < 0 || p->M < 2 * (T + 1) || p->M > 512) return NSPT_ERR_ARG;
   p->slices = o->slices ? o->slices : 6;
   if (p->slices < 2 || p->slices > 8) return NSPT_ERR_ARG;
-  if (o->complex_mode != 0 && o->complex_mode != 4) return NSPT_ERR_UNSUPPORTED;
+  p->cm = 4;
+  if (o->complex_mode == 3) {
+    // 3M: split-form FFT-CONV products with S <= 6 and row-form slicing (N <= 512)
+    if (!allow_3m || p->prec != NSPT_PREC_SPLIT || p->slices > 6 || N > 512) return NSPT_ERR_UNSUPPORTED;
+    p->cm = 3;
+  } else if (o->complex_mode != 0 && o->complex_mode != 4) {
+    return NSPT_ERR_UNSUPPORTED;
+  }
   p->rescale_auto = (o->rescale_log2r == NSPT_RESCALE_AUTO);
   p->log2r = p->rescale_auto ? 0 : o->rescale_log2r;
   if (!p->rescale_auto && (p->log2r < -60 || p->log2r > 60)) return NSPT_ERR_ARG;
@@ -105,7 +114,7 @@ size_t ws_mul(const Plan& p) {
   if (p.algo == NSPT_ALGO_NAIVE) return 0;
   const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
   if (p.prec == NSPT_PREC_FP64) return 3 * ((spec + 255) & ~(size_t)255) + 2 * 513 * sizeof(int);  // + fit scratch
-  return nspt_split_ws_mul(p.N, p.T, p.batch, p.M, p.slices);
+  return nspt_split_ws_mul(p.N, p.T, p.batch, p.M, p.slices, p.cm);
 }
 
 int mul_fp64(const Plan& p, const double2* A, const double2* B, double2* C, void* ws, cudaStream_t st) {
@@ -543,7 +552,7 @@ size_t ws_wilson(const Plan& p, int amax) {
 
 int mul_plan(const Plan& p, const double2* A, const double2* B, double2* C, void* ws, cudaStream_t st) {
   if (p.prec == NSPT_PREC_FP64) return mul_fp64(p, A, B, C, ws, st);
-  return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, A, B, C, ws, st);
+  return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, A, B, C, ws, st, p.cm);
 }
 
 int wilson_run(const Plan& p, const double2* U, int flux, int amax, double2* W, void* ws, cudaStream_t st) {
@@ -783,7 +792,7 @@ int nspt_init(void) {
 
 size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opts) {
   Plan p;
-  if (make_plan(N, T, batch, opts, &p) != NSPT_OK) return 0;
+  if (make_plan(N, T, batch, opts, &p, op == NSPT_OP_MUL) != NSPT_OK) return 0;
   switch (op) {
     case NSPT_OP_MUL: return ws_mul(p);
     case NSPT_OP_MUL_BACKWARD: return ws_bwd(p);
@@ -804,7 +813,7 @@ static int check_ws(const nspt_opts* o, size_t need) {
 int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int batch, const nspt_opts* opts,
                      void* stream) {
   Plan p;
-  int rc = make_plan(N, T, batch, opts, &p);
+  int rc = make_plan(N, T, batch, opts, &p, true);
   if (rc) return rc;
   if (!A || !B || !C) return NSPT_ERR_ARG;
   const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
@@ -819,7 +828,7 @@ int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int ba
   if (p.prec == NSPT_PREC_FP64)
     return mul_fp64(p, (const double2*)A, (const double2*)B, (double2*)C, opts ? opts->workspace : nullptr, st);
   return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, (const double2*)A,
-                        (const double2*)B, (double2*)C, opts->workspace, st);
+                        (const double2*)B, (double2*)C, opts->workspace, st, p.cm);
 }
 
 int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB, int N, int T,

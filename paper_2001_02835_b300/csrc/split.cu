@@ -127,7 +127,9 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
 // front (all loads in flight at once), the row exponent is a warp max over the
 // registers, and the digits are produced one digit index at a time for the
 // four entries, each leaving as one 8-byte bf16x4 store per plane (256
-// contiguous bytes per warp store).  Same output as slice_kernel.
+// contiguous bytes per warp store).  Same output as slice_kernel.  With sum3
+// (P = 3) the third plane holds the digits of re + im (the 3M product's
+// operand) at the row exponent e + 1 instead of -re: |re + im| < 2^(e+1).
 __device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
   const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
   return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
@@ -136,7 +138,7 @@ __device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d)
 template <int S, int NQ>
 __global__ void __launch_bounds__(256, NQ <= 2 ? 4 : 2)
 slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int rev, int conj, int N, int Kp, int P,
-                  __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+                  int sum3, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   const int q = blockIdx.y;
   const int b = q / M, p = q % M;
   const int sp = rev ? (M - p) % M : p;
@@ -162,14 +164,16 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   if (lane == 0) exps[(long long)q * N + r] = e;
   const long long plane = (long long)N * Kp;
   __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
-  float f1, f2;
+  float f1, f2, g1, g2;
   pow2_pair(-e, f1, f2);
+  pow2_pair(-e - 1, g1, g2);
 #pragma unroll
   for (int t = 0; t < NQ; ++t) {
     const int k = 4 * lane + 128 * t;
     if (k >= N) break;
-    // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the four entries
-    float vr[4], vi[4], lr[4], li[4];
+    // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the four entries,
+    // and (3M) of (re + im) 2^-(e+1)
+    float vr[4], vi[4], lr[4], li[4], vs[4], ls[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const float4 x = v[t][c];
@@ -178,35 +182,48 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
       lr[c] = (x.y * f1) * f2;
       vi[c] = sg * ((x.z * f1) * f2);
       li[c] = sg * ((x.w * f1) * f2);
+      if (sum3) {
+        const dfl su = df_add(dfl{x.x, x.y}, dfl{sg * x.z, sg * x.w});
+        vs[c] = (su.h * g1) * g2;
+        ls[c] = (su.l * g1) * g2;
+      } else {
+        vs[c] = 0.f;
+        ls[c] = 0.f;
+      }
     }
 #pragma unroll
     for (int i = 0; i < S; ++i) {
       // digit i: t = v rounded to a multiple of 2^(-7-8i); lo joins before digit 3 (see to_digits)
       const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
-      float dr[4], di[4];
+      float dr[4], di[4], ds[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (i == 3) { vr[c] = vr[c] + lr[c]; vi[c] = vi[c] + li[c]; }
-        const float tr = (vr[c] + sig) - sig, ti = (vi[c] + sig) - sig;
+        if (i == 3) { vr[c] = vr[c] + lr[c]; vi[c] = vi[c] + li[c]; vs[c] = vs[c] + ls[c]; }
+        const float tr = (vr[c] + sig) - sig, ti = (vi[c] + sig) - sig, ts = (vs[c] + sig) - sig;
         vr[c] = vr[c] - tr;
         vi[c] = vi[c] - ti;
+        vs[c] = vs[c] - ts;
         dr[c] = tr * 128.f;
         di[c] = ti * 128.f;
+        ds[c] = ts * 128.f;
       }
       __nv_bfloat16* o = orow + (long long)P * i * plane + k;
       *reinterpret_cast<uint2*>(o) = pack_bf16x4(dr[0], dr[1], dr[2], dr[3]);
       *reinterpret_cast<uint2*>(o + plane) = pack_bf16x4(di[0], di[1], di[2], di[3]);
-      if (P == 3) *reinterpret_cast<uint2*>(o + 2 * plane) = pack_bf16x4(-dr[0], -dr[1], -dr[2], -dr[3]);
+      if (P == 3) {
+        *reinterpret_cast<uint2*>(o + 2 * plane) =
+            sum3 ? pack_bf16x4(ds[0], ds[1], ds[2], ds[3]) : pack_bf16x4(-dr[0], -dr[1], -dr[2], -dr[3]);
+      }
     }
   }
 }
 
 template <int S, int NQ>
 int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int conj, int N, int Kp, int Q, int P,
-                      __nv_bfloat16* out, int* exps, cudaStream_t st) {
+                      int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_rows_kernel<S, NQ><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+  slice_rows_kernel<S, NQ><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, sum3, out, exps);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
@@ -214,14 +231,15 @@ int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int co
 
 template <int S, typename InT>
 int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q, int P,
-                 __nv_bfloat16* out, int* exps, cudaStream_t st) {
+                 int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
   if constexpr (std::is_same<InT, float4>::value) {
     if (!trans && N <= 512) {
-      if (N <= 128) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
-      if (N <= 256) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
-      return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, out, exps, st);
+      if (N <= 128) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      if (N <= 256) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
     }
   }
+  if (sum3) return NSPT_ERR_UNSUPPORTED;  // the (re + im) plane: row form only
   const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
   cudaError_t e = cudaFuncSetAttribute(slice_kernel<S, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
@@ -242,14 +260,15 @@ struct SplitWs {
   float4* Ct;
 };
 
-SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total) {
+// cm = 3: the left operand's slices carry a third plane (re + im) as well
+SplitWs carve(void* ws, int N, int batch, int M, int S, size_t* total, int cm = 4) {
   WsCarver w(ws, SIZE_MAX);
   SplitWs s;
   const long long E = (long long)N * N, Q = (long long)batch * M;
   s.err = w.take<int>(64);
   s.At = w.take<float4>((size_t)Q * E);
   s.Bt = w.take<float4>((size_t)Q * E);
-  s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+  s.slA = w.take<__nv_bfloat16>((size_t)Q * S * (cm == 3 ? 3 : 2) * N * kpad(N));
   s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 3 * N * kpad(N));
   s.expA = w.take<int>((size_t)Q * N);
   s.expB = w.take<int>((size_t)Q * N);
@@ -295,10 +314,10 @@ int gemm(const SplitWs& w, int N, int Q, int S, cudaStream_t st) {
 
 template <typename InT>
 int slice_any(int S, const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q, int P,
-              void* out, int* exps, cudaStream_t st) {
+              void* out, int* exps, cudaStream_t st, int sum3 = 0) {
   __nv_bfloat16* o = (__nv_bfloat16*)out;
   switch (S) {
-#define NSPT_CASE(s) case s: return launch_slice<s, InT>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, P, o, exps, st);
+#define NSPT_CASE(s) case s: return launch_slice<s, InT>(X, bstride, M, rev, trans, conj, N, kpad(N), Q, P, sum3, o, exps, st);
     NSPT_CASE(2) NSPT_CASE(3) NSPT_CASE(4) NSPT_CASE(5) NSPT_CASE(6) NSPT_CASE(7) NSPT_CASE(8)
 #undef NSPT_CASE
     default: return NSPT_ERR_ARG;
@@ -311,8 +330,8 @@ int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev,
 }
 
 int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                        int P, void* out, int* exps, cudaStream_t st) {
-  return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, P, out, exps, st);
+                        int P, void* out, int* exps, cudaStream_t st, int sum3) {
+  return slice_any<float4>(S, X, bstride, M, rev, trans, conj, N, Q, P, out, exps, st, sum3);
 }
 
 // Library-owned side streams of a device: the independent per-product chains of a grouped call
@@ -376,9 +395,9 @@ int nspt_split_init() {
   return nspt_split_gemm_init();
 }
 
-size_t nspt_split_ws_mul(int N, int T, int batch, int M, int S) {
+size_t nspt_split_ws_mul(int N, int T, int batch, int M, int S, int cm) {
   size_t total = 0;
-  carve(nullptr, N, batch, M, S, &total);
+  carve(nullptr, N, batch, M, S, &total, cm);
   return total;
 }
 
@@ -488,9 +507,10 @@ int nspt_split_fit_rescale_dev(const double2* A, const double2* B, int N, int T,
 }
 
 int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescale_auto, const double2* A,
-                   const double2* B, double2* C, void* ws, cudaStream_t st) {
+                   const double2* B, double2* C, void* ws, cudaStream_t st, int cm) {
   const int E = N * N, Q = batch * M;
-  SplitWs w = carve(ws, N, batch, M, S, nullptr);
+  if (cm == 3 && (S > 6 || N > 512)) return NSPT_ERR_UNSUPPORTED;
+  SplitWs w = carve(ws, N, batch, M, S, nullptr, cm);
   // fitted rescale: on the device, into a spare word of the status block (the maxima go to expA,
   // which the slicer overwrites later; the exponent must outlive it for the inverse transform)
   int* dlr = nullptr;
@@ -505,18 +525,23 @@ int nspt_split_mul(int N, int T, int batch, int M, int S, int log2r, bool rescal
   // (B's spectra are written transposed, so that both operands are sliced by rows)
   // a2: slices of A~_q (rows) and of B~_q^T (rows of the transposed spectra); the two operands'
   // chains run on side streams, so that one operand's transform overlaps the other's slicing
+  // (3M: both operands' slices carry planes (re, im, re + im))
   TRYS(fork_join(2, st, [&](int i, cudaStream_t s) -> int {
     if (i == 0) {
       TRYC(nspt_fft_fwd_df(A, T + 1, w.At, E, T, batch, M, 0, log2r, s));
-      TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, 2, w.slA, w.expA, s));
+      TRYS(nspt_split_slice_df(S, w.At, M, M, 0, 0, 0, N, Q, cm == 3 ? 3 : 2, w.slA, w.expA, s, cm == 3));
     } else {
       TRYC(nspt_fft_fwd_df(B, T + 1, w.Bt, E, T, batch, M, 0, log2r, s, N));
-      TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, s));
+      TRYS(nspt_split_slice_df(S, w.Bt, M, M, 0, 0, 0, N, Q, 3, w.slB, w.expB, s, cm == 3));
     }
     return NSPT_OK;
   }));
   // a3: mode GEMMs on the tensor cores
-  TRYS(gemm(w, N, Q, S, st));
+  if (cm == 3) {
+    TRYS(nspt_split_gemm3m(gemm_args(w, N, Q, S), st));
+  } else {
+    TRYS(gemm(w, N, Q, S, st));
+  }
   // a4: inverse transform, truncation, unscale 2^(-k log2r)
   TRYC(nspt_fft_inv_df(w.Ct, C, T + 1, E, T, batch, M, 0, log2r, st));
   return NSPT_OK;

@@ -6,10 +6,11 @@
 #include "../../include/nspt.h"
 
 int nspt_split_init();
-size_t nspt_split_ws_mul(int N, int T, int batch, int M, int slices);
+// cm: complex products as 4 real products (the embedding, every entry point) or 3 (3M: products only)
+size_t nspt_split_ws_mul(int N, int T, int batch, int M, int slices, int cm = 4);
 size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int slices);
 int nspt_split_mul(int N, int T, int batch, int M, int slices, int log2r, bool rescale_auto, const double2* A,
-                   const double2* B, double2* C, void* ws, cudaStream_t st);
+                   const double2* B, double2* C, void* ws, cudaStream_t st, int cm = 4);
 int nspt_split_bwd(int N, int T, int batch, int M, int slices, int log2r, const double2* A, const double2* B,
                    const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
 // mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE; log2r: every order transform of the
@@ -21,8 +22,10 @@ int nspt_split_langevin(int N, int T, int batch, int M, int slices, double2* U, 
 // slices of Q planes of X (see slice_kernel): out bf16 [Q][S][2][N][Kp], exps [Q][N]
 int nspt_split_slice(int S, const double2* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
                      int P, void* out, int* exps, cudaStream_t st);
+// sum3 (with P = 3): the third plane holds re + im at the row exponent + 1 (3M operands; row form,
+// N <= 512, trans = 0 only, else NSPT_ERR_UNSUPPORTED)
 int nspt_split_slice_df(int S, const float4* X, long long bstride, int M, int rev, int trans, int conj, int N, int Q,
-                        int P, void* out, int* exps, cudaStream_t st);
+                        int P, void* out, int* exps, cudaStream_t st, int sum3 = 0);
 int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, const int* expB, void* C, int N, int Q,
                           int S, int* err, cudaStream_t st);
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st);

@@ -558,6 +558,7 @@ int nspt_split_gemm_init() {
   if (!rc) rc = set_attrs<7>();
   if (!rc) rc = set_attrs<8>();
   if (!rc) rc = nspt_split_gemm_ta_init();
+  if (!rc) rc = nspt_split_gemm3m_init();
   if (rc) return rc;
   return NSPT_OK;
 }

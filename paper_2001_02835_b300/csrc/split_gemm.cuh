@@ -22,6 +22,10 @@ int nspt_split_gemm_init();
 int nspt_split_gemm(const SplitGemmArgs& a, cudaStream_t st);
 // one persistent launch over the tiles of `count` problems (same S); err of a[0] is used
 int nspt_split_gemm_batch(const SplitGemmArgs* a, int count, int S, int bn, int num_sms, cudaStream_t st);
+// 3M variant (three real products per complex product; plain products, S <= 6): both operands'
+// slices with planes (re, im, re + im), tile 128 x 32 (split_gemm3m.cu)
+int nspt_split_gemm3m_init();
+int nspt_split_gemm3m(const SplitGemmArgs& a, cudaStream_t st);
 // variant with the left operand in tensor memory (tile 128 x 40), selected by bn = 40
 int nspt_split_gemm_ta_init();
 int nspt_split_gemm_ta_batch(const SplitGemmArgs* a, int count, int S, int num_sms, cudaStream_t st);

@@ -25,6 +25,12 @@ product bound, with CHAIN at least four times the largest observed ratio to the 
 bound times the growth (0.34 for the Langevin step at SU(121), O(g^31); 1.09 for one MD step
 at SU(225), O(g^31) with the fitted rescale; 1.72 for the Wilson loops at SU(121), O(g^31);
 0.21 for the backward; 0.14 for the unitarity projection).
+
+The 3M products (three real products per complex product, `complex_mode=3`) take the
+product bound times CHAIN["product3m"]: their imaginary part P3 - P1 - P2 comes from the
+digits of re + im, sliced at twice the row bound, and cancels; the largest observed ratio to
+the product bound was 0.38 (the SU(225), O(g^63) batch), 1.3-2.2 times the 4M error of the
+same product.
 """
 import json
 import os
@@ -37,7 +43,8 @@ C_OBS = 84.0                  # max err / 2^-(8S-1) over the product cases, S <=
 F_OBS = 2.0 ** -44            # max err of the product cases at S = 7, 8
 SPLIT_C = 4 * C_OBS
 SPLIT_FLOOR = 4 * F_OBS
-CHAIN = {"product": 1.0, "backward": 2.0, "langevin": 2.0, "md": 6.0, "wilson": 8.0, "unitarize": 2.0}
+CHAIN = {"product": 1.0, "product3m": 2.0, "backward": 2.0, "langevin": 2.0, "md": 6.0, "wilson": 8.0,
+         "unitarize": 2.0}
 
 
 def dev(x: np.ndarray) -> torch.Tensor:

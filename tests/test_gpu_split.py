@@ -62,6 +62,50 @@ def test_split_mul_matches_oracle(nspt, N, T, batch):
         assert errs[5] > bound(6), errs       # one slice fewer fails the bound
 
 
+# 3M (three real products per complex product): the plain product, S <= 6, N <= 512
+PRODUCT_CASES_3M = [c for c in PRODUCT_CASES if c[0] <= 512]
+
+
+@pytest.mark.parametrize("N,T,batch", PRODUCT_CASES_3M)
+def test_split_3m_matches_oracle(nspt, N, T, batch):
+    g = syn.rng(5000 + N + 100 * T)
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    tA, tB = dev(A), dev(B)
+    ref = pm.star(A, B)
+    errs = {}
+    for S in (6, 5):
+        C = host(nspt.polymat_mul(tA, tB, algo="fft", prec="split", slices=S, complex_mode=3))
+        errs[S] = max_order_rel(C, ref)
+    C4 = host(nspt.polymat_mul(tA, tB, algo="fft", prec="split", complex_mode=4))
+    e4 = max_order_rel(C4, ref)
+    record("split_mul_3m", N=N, T=T, batch=batch, err_S6=errs[6], err_S5=errs[5], err_4m=e4)
+    assert errs[6] <= split_bound(6, "product3m"), errs
+    assert errs[5] <= split_bound(5, "product3m"), errs
+    if N >= 9:
+        assert errs[5] > split_bound(6, "product3m"), errs    # one slice fewer fails the bound
+        # the 3M imaginary part cancels: larger error than the 4M form, within a small factor
+        assert e4 < errs[6] < 8 * e4, (e4, errs)
+
+
+def test_split_3m_unsupported_combinations(nspt):
+    """complex_mode = 3 is the split-form plain product only: the FP64 form, S > 6, N > 512
+    and the other entry points return NSPT_ERR_UNSUPPORTED (-3); other values are refused too."""
+    unsupported = r"\[-3\]"
+    g = syn.rng(5450)
+    A = dev(syn.series_batch(g, 9, 3, 1))
+    for kw in (dict(prec="fp64"), dict(prec="split", slices=7)):
+        with pytest.raises(nspt.NsptError, match=unsupported):
+            nspt.polymat_mul(A, A, algo="fft", complex_mode=3, **kw)
+    with pytest.raises(nspt.NsptError, match=unsupported):
+        nspt.polymat_mul(A, A, algo="fft", prec="split", complex_mode=2)
+    big = dev(syn.series_batch(g, 520, 1, 1))
+    with pytest.raises(nspt.NsptError, match=unsupported):
+        nspt.polymat_mul(big, big, algo="fft", prec="split", complex_mode=3)
+    with pytest.raises(nspt.NsptError, match=unsupported):
+        nspt.polymat_mul_backward(A, A, A, algo="fft", prec="split", complex_mode=3)
+
+
 @pytest.mark.parametrize("S", [2, 3, 4, 5, 6, 7, 8])
 def test_split_error_shrinks_with_slices(nspt, S):
     """Each S meets its stated bound; for S <= 6 the result with S - 1 slices fails
@@ -245,11 +289,14 @@ def test_split_su225_t63_full_oracle(nspt):
     e6 = order_errors(host(nspt.polymat_mul(tA, tB, algo="fft", prec="split")), ref)
     e5 = order_errors(host(nspt.polymat_mul(tA, tB, algo="fft", prec="split", slices=5)), ref)
     e64 = order_errors(host(nspt.polymat_mul(tA, tB, algo="fft", prec="fp64")), ref)
-    record("su225_t63", per_order_S6=e6.max(0), per_order_S5=e5.max(0), per_order_fp64=e64.max(0))
+    e3m = order_errors(host(nspt.polymat_mul(tA, tB, algo="fft", prec="split", complex_mode=3)), ref)
+    record("su225_t63", per_order_S6=e6.max(0), per_order_S5=e5.max(0), per_order_fp64=e64.max(0),
+           per_order_3m=e3m.max(0))
     assert e6.max() <= bound(6), e6.max()
     assert e5.max() > bound(6), e5.max()
     assert e5.max() <= bound(5), e5.max()
     assert e64.max() <= 1e-12, e64.max()
+    assert e3m.max() <= split_bound(6, "product3m"), e3m.max()
 
 
 def test_split_device_status_ok(nspt):
