@@ -74,6 +74,28 @@ def test_workspace_sizes(L):
     assert n.workspace_size(0, 225, 31, 4, n.make_opts(algo="fft", fft_len=128)) >= 6 * spec
 
 
+def test_complex_mode_plans_need_no_gpu(L):
+    """complex_mode = 3 (3M) is planned for the split-form product only: its workspace holds a
+    third slice plane of the left operand; every other combination is refused on the host."""
+    import paper_2001_02835_b300 as n
+    N, T, b = 225, 31, 4
+    m4 = n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="fft", prec="split"))
+    m3 = n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="fft", prec="split", complex_mode=3))
+    kp = (N + 7) & ~7
+    assert m3 - m4 >= b * 64 * 6 * N * kp * 2          # one more BF16 plane per slice and mode
+    for kw in (dict(prec="fp64"), dict(prec="split", slices=7), dict(prec="split", complex_mode=2)):
+        kw.setdefault("complex_mode", 3)
+        assert n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="fft", **kw)) == 0
+    assert n.workspace_size(n.OP_MUL, 513, 3, 1, n.make_opts(algo="fft", prec="split", complex_mode=3)) == 0
+    o3 = n.make_opts(algo="fft", prec="split", complex_mode=3)
+    assert n.workspace_size(n.OP_MUL_BACKWARD, N, T, b, o3) == 0
+    assert L.nspt_polymat_mul_backward(1 << 20, 2 << 20, 3 << 20, 4 << 20, 5 << 20, N, T, b, ctypes.byref(o3),
+                                       None) == -3
+    assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, 513, 3, 1, ctypes.byref(o3), None) == -3
+    # a valid 3M request without its workspace: the workspace check, not the plan, refuses it
+    assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, N, T, b, ctypes.byref(o3), None) == -4
+
+
 def test_argument_checks_of_md_wilson_and_host_product(L):
     import paper_2001_02835_b300 as n
     o = n.make_opts()

@@ -106,6 +106,23 @@ def test_split_3m_unsupported_combinations(nspt):
         nspt.polymat_mul_backward(A, A, A, algo="fft", prec="split", complex_mode=3)
 
 
+def test_split_3m_deterministic_and_graph_replay(nspt):
+    """The 3M product is bit-reproducible and replays bit for bit in a captured CUDA graph."""
+    g = syn.rng(5470)
+    N, T, batch = 64, 15, 2
+    tA, tB = dev(syn.series_batch(g, N, T, batch)), dev(syn.series_batch(g, N, T, batch))
+    kw = dict(algo="fft", prec="split", complex_mode=3)
+    C1 = host(nspt.polymat_mul(tA, tB, **kw))
+    np.testing.assert_array_equal(host(nspt.polymat_mul(tA, tB, **kw)), C1)
+    Cg = torch.zeros_like(tA)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        nspt.polymat_mul(tA, tB, Cg, **kw)
+    graph.replay()
+    np.testing.assert_array_equal(host(Cg), C1)
+
+
 @pytest.mark.parametrize("S", [2, 3, 4, 5, 6, 7, 8])
 def test_split_error_shrinks_with_slices(nspt, S):
     """Each S meets its stated bound; for S <= 6 the result with S - 1 slices fails
