@@ -1,5 +1,6 @@
 """Invariants of the GPU path that hold at any size: associativity of the truncated
-product, 1 x 1 series as scalar polynomials, and unitarity of the link series through
+product, exp(gX) * exp(-gX) = 1 through order T, 1 x 1 series as scalar polynomials, and
+unitarity of the link series through
 the Langevin step and MD trajectories (exp_star(i X) is unitary for Hermitian X, i.e.
 exp_star(iX) * exp_star(-iX) = 1 through order T), in every form."""
 import numpy as np
@@ -36,6 +37,66 @@ def test_product_is_associative(nspt, algo, prec):
     record("associativity", algo=algo, prec=prec, err=err)
     # four products, each within the per-product bound
     assert err <= (1e-12 if prec == "fp64" else 4 * split_bound(6)), err
+
+
+def _exp_series(X, T, sign):
+    """the truncated series of exp(sign g X): coefficients (sign X)^k / k!, k = 0..T"""
+    N = X.shape[0]
+    out = np.empty((T + 1, N, N), dtype=np.complex128)
+    out[0] = np.eye(N)
+    for k in range(1, T + 1):
+        out[k] = (sign * X) @ out[k - 1] / k
+    return out
+
+
+@pytest.mark.parametrize("algo,prec,cm", [("naive", "fp64", 4), ("fft", "fp64", 4), ("fft", "split", 4),
+                                          ("fft", "split", 3)])
+def test_exp_gx_times_exp_minus_gx_is_one(nspt, algo, prec, cm):
+    """exp(gX) * exp(-gX) = 1 through order T: order 0 is the identity and every higher order
+    vanishes.  The coefficients fall off factorially (1/31! ~ 1e-34 at ||X|| ~ 1), which no
+    geometric rescale r^k flattens, so each order's error is measured on the scale FFT-CONV
+    resolves it at: the naive form against sum_j ||A_j|| ||B_{k-j}|| (the size of order k's
+    terms), the FFT forms (rescale r = 2^2) against r^-k (sum_j ||r^j A_j||)(sum_j ||r^j B_j||)
+    / sqrt(M), the size of the rescaled spectra mapped back to order k.  The bound is
+    log2(M) u, u = 2^-53 (FP64) or 2^-(8S-1) (S slices); the split forms with one slice fewer fail
+    it."""
+    g = syn.rng(7520)
+    N, T, batch, log2r = 64, 31, 2, 2
+    M = 64
+    Xs = [syn.gaussian(g, (N, N), 1.0 / (4 * N)) for _ in range(batch)]     # ||X||_2 ~ 1
+    A = np.stack([_exp_series(X, T, +1) for X in Xs])
+    B = np.stack([_exp_series(X, T, -1) for X in Xs])
+    kw = dict(algo=algo, prec=prec)
+    if algo == "fft":
+        kw["rescale_log2r"] = log2r
+    if cm == 3:
+        kw["complex_mode"] = 3
+    dA, dB = dev(A), dev(B)
+
+    def zero_order_errors(C):
+        C = C.copy()
+        C[:, 0] -= np.eye(N)
+        return np.sqrt(np.sum(np.abs(C) ** 2, axis=(-1, -2)))
+
+    e = zero_order_errors(host(nspt.polymat_mul(dA, dB, **kw)))
+    na = np.sqrt(np.sum(np.abs(A) ** 2, axis=(-1, -2)))          # (batch, T+1)
+    nb = np.sqrt(np.sum(np.abs(B) ** 2, axis=(-1, -2)))
+    k = np.arange(T + 1)
+    if algo == "naive":
+        scale = np.stack([np.convolve(na[b], nb[b])[:T + 1] for b in range(batch)])
+    else:
+        r = 2.0 ** log2r
+        sa = (na * r ** k).sum(axis=1, keepdims=True)
+        sb = (nb * r ** k).sum(axis=1, keepdims=True)
+        scale = sa * sb * r ** (-k) / np.sqrt(M)
+    err = (e / scale).max()
+    record("exp_identity", algo=algo, prec=prec, cm=cm, err=err)
+    if prec == "fp64":
+        assert err <= np.log2(M) * 2.0 ** -53, err
+    else:
+        assert err <= np.log2(M) * 2.0 ** -47, err
+        e5 = zero_order_errors(host(nspt.polymat_mul(dA, dB, slices=5, **kw)))
+        assert (e5 / scale).max() > np.log2(M) * 2.0 ** -47, (e5 / scale).max()
 
 
 @pytest.mark.parametrize("algo,prec", FORMS)
