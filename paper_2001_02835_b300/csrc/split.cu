@@ -135,10 +135,25 @@ __device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d)
   return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
 }
 
-template <int S, int NQ>
-__global__ void __launch_bounds__(256, NQ <= 2 ? 4 : 2)
+// W consecutive bf16 values as one 8-byte (W = 4) or 16-byte (W = 8) store
+template <int W>
+__device__ __forceinline__ void store_bf16(__nv_bfloat16* o, const float (&d)[W]) {
+  if constexpr (W == 4) {
+    *reinterpret_cast<uint2*>(o) = pack_bf16x4(d[0], d[1], d[2], d[3]);
+  } else {
+    static_assert(W == 8, "4 or 8 entries per store");
+    const uint2 a = pack_bf16x4(d[0], d[1], d[2], d[3]), b = pack_bf16x4(d[4], d[5], d[6], d[7]);
+    *reinterpret_cast<uint4*>(o) = make_uint4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// W adjacent entries per lane and chunk (4: 8-byte stores, 8: 16-byte stores); NQ chunks of
+// 32 W entries per row
+template <int S, int NQ, int W, bool SUM3>
+__global__ void __launch_bounds__(256, NQ * W <= 8 ? 4 : 2)
 slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int rev, int conj, int N, int Kp, int P,
-                  int sum3, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+                  __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
+  constexpr bool sum3 = SUM3;
   const int q = blockIdx.y;
   const int b = q / M, p = q % M;
   const int sp = rev ? (M - p) % M : p;
@@ -146,18 +161,18 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   const int r = blockIdx.x * RB + warp;
   if (r >= N) return;
   const float4* src = X + ((long long)b * bstride + sp) * N * N + (long long)r * N;
-  float4 v[NQ][4];
+  float4 v[NQ][W];
 #pragma unroll
   for (int t = 0; t < NQ; ++t) {
-    const int k = 4 * lane + 128 * t;
+    const int k = W * lane + 32 * W * t;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[t][c] = (k + c < N) ? src[k + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < W; ++c) v[t][c] = (k + c < N) ? src[k + c] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   int mx = -100000;
 #pragma unroll
   for (int t = 0; t < NQ; ++t)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) mx = max(mx, exp_bound(v[t][c]));
+    for (int c = 0; c < W; ++c) mx = max(mx, exp_bound(v[t][c]));
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
@@ -169,13 +184,13 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   pow2_pair(-e - 1, g1, g2);
 #pragma unroll
   for (int t = 0; t < NQ; ++t) {
-    const int k = 4 * lane + 128 * t;
+    const int k = W * lane + 32 * W * t;
     if (k >= N) break;
-    // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the four entries,
+    // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the W entries,
     // and (3M) of (re + im) 2^-(e+1)
-    float vr[4], vi[4], lr[4], li[4], vs[4], ls[4];
+    float vr[W], vi[W], lr[W], li[W], vs[W], ls[W];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < W; ++c) {
       const float4 x = v[t][c];
       const float sg = conj ? -1.f : 1.f;
       vr[c] = (x.x * f1) * f2;
@@ -195,9 +210,9 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
     for (int i = 0; i < S; ++i) {
       // digit i: t = v rounded to a multiple of 2^(-7-8i); lo joins before digit 3 (see to_digits)
       const float sig = __int_as_float(((143 - 8 * i) << 23) | 0x400000);
-      float dr[4], di[4], ds[4];
+      float dr[W], di[W], ds[W];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < W; ++c) {
         if (i == 3) { vr[c] = vr[c] + lr[c]; vi[c] = vi[c] + li[c]; vs[c] = vs[c] + ls[c]; }
         const float tr = (vr[c] + sig) - sig, ti = (vi[c] + sig) - sig, ts = (vs[c] + sig) - sig;
         vr[c] = vr[c] - tr;
@@ -208,22 +223,31 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
         ds[c] = ts * 128.f;
       }
       __nv_bfloat16* o = orow + (long long)P * i * plane + k;
-      *reinterpret_cast<uint2*>(o) = pack_bf16x4(dr[0], dr[1], dr[2], dr[3]);
-      *reinterpret_cast<uint2*>(o + plane) = pack_bf16x4(di[0], di[1], di[2], di[3]);
-      if (P == 3) {
-        *reinterpret_cast<uint2*>(o + 2 * plane) =
-            sum3 ? pack_bf16x4(ds[0], ds[1], ds[2], ds[3]) : pack_bf16x4(-dr[0], -dr[1], -dr[2], -dr[3]);
+      if (P == 3 && !sum3) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) ds[c] = -dr[c];
       }
+      store_bf16<W>(o, dr);
+      store_bf16<W>(o + plane, di);
+      if (P == 3) store_bf16<W>(o + 2 * plane, ds);
     }
   }
 }
 
-template <int S, int NQ>
+template <int S, int NQ, int W>
 int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int conj, int N, int Kp, int Q, int P,
                       int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
   dim3 grid((N + RB - 1) / RB, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_rows_kernel<S, NQ><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, sum3, out, exps);
+  if (sum3) {
+    if constexpr (S <= 6) {
+      slice_rows_kernel<S, NQ, W, true><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+    } else {
+      return NSPT_ERR_UNSUPPORTED;
+    }
+  } else {
+    slice_rows_kernel<S, NQ, W, false><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+  }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
@@ -234,9 +258,9 @@ int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int
                  int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
   if constexpr (std::is_same<InT, float4>::value) {
     if (!trans && N <= 512) {
-      if (N <= 128) return launch_slice_rows<S, 1>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
-      if (N <= 256) return launch_slice_rows<S, 2>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
-      return launch_slice_rows<S, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      if (N <= 128) return launch_slice_rows<S, 1, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      if (N <= 256) return launch_slice_rows<S, 1, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      return launch_slice_rows<S, 2, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
     }
   }
   if (sum3) return NSPT_ERR_UNSUPPORTED;  // the (re + im) plane: row form only
