@@ -47,7 +47,23 @@ using namespace digits;
 // of batch element b.
 constexpr int RB = 8;  // output rows per CTA
 
-template <int S, typename InT>
+// four floats as four round-to-nearest bf16 values in one 8-byte word
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
+}
+
+// Shared-memory layout of slice_kernel: the rows of the output block, row rr at rr * ldr (ldr
+// odd and >= N rounded up to 4), entry k of a row at slice_swz(k) = k ^ ((k >> 3) & 3).  Both
+// staging patterns (a warp writing 32 consecutive entries of one row; a quarter warp writing one
+// entry of each of 8 rows) and the digit stage (a lane reading 4 adjacent entries) then touch 8
+// distinct 16-byte bank groups per quarter warp.
+__host__ __device__ constexpr int slice_ldr(int N) { return ((N + 3) & ~3) + 1; }
+__device__ __forceinline__ int slice_swz(int k) { return k ^ ((k >> 3) & 3); }
+
+// RBK output rows per CTA: 8 for row sources, 16 for column sources (trans), whose staging then
+// reads 256-byte runs of 16 consecutive entries
+template <int S, typename InT, int RBK>
 __global__ void __launch_bounds__(256)
 slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
              int P, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
@@ -57,43 +73,45 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   const int b = q / M, p = q % M;
   const int sp = rev ? (M - p) % M : p;
   const InT* Xm = X + ((long long)b * bstride + sp) * N * N;
-  const int r0 = blockIdx.x * RB;
-  const int nr = min(RB, N - r0);
-  const int ld = RB + 1;
+  const int r0 = blockIdx.x * RBK;
+  const int nr = min(RBK, N - r0);
+  const int ldr = slice_ldr(N);
   if (!trans) {
     // one warp per source row: coalesced row reads, four loads in flight per thread
     for (int rr = threadIdx.x >> 5; rr < nr; rr += blockDim.x >> 5) {
       const InT* src = Xm + (long long)(r0 + rr) * N;
-      InT* dst = tile + rr * N;
+      InT* dst = tile + rr * ldr;
       int k = threadIdx.x & 31;
       for (; k + 96 < N; k += 128) {
         const InT x0 = src[k], x1 = src[k + 32], x2 = src[k + 64], x3 = src[k + 96];
-        dst[k] = x0; dst[k + 32] = x1; dst[k + 64] = x2; dst[k + 96] = x3;
+        dst[slice_swz(k)] = x0; dst[slice_swz(k + 32)] = x1; dst[slice_swz(k + 64)] = x2; dst[slice_swz(k + 96)] = x3;
       }
-      for (; k < N; k += 32) dst[k] = src[k];
+      for (; k < N; k += 32) dst[slice_swz(k)] = src[k];
     }
   } else {
-    // RB consecutive entries of every source row: one 128- or 256-byte run per row
-    const int rr = threadIdx.x % RB;
-    constexpr int STEP = 256 / RB;
+    // RBK consecutive entries of every source row: one 128- or 256-byte run per row
+    const int rr = threadIdx.x % RBK;
+    constexpr int STEP = 256 / RBK;
     if (rr < nr) {
       const InT* src = Xm + r0 + rr;
-      int k = threadIdx.x / RB;
+      InT* dst = tile + rr * ldr;
+      int k = threadIdx.x / RBK;
       for (; k + 3 * STEP < N; k += 4 * STEP) {
         const InT x0 = src[(long long)k * N], x1 = src[(long long)(k + STEP) * N];
         const InT x2 = src[(long long)(k + 2 * STEP) * N], x3 = src[(long long)(k + 3 * STEP) * N];
-        tile[k * ld + rr] = x0; tile[(k + STEP) * ld + rr] = x1;
-        tile[(k + 2 * STEP) * ld + rr] = x2; tile[(k + 3 * STEP) * ld + rr] = x3;
+        dst[slice_swz(k)] = x0; dst[slice_swz(k + STEP)] = x1;
+        dst[slice_swz(k + 2 * STEP)] = x2; dst[slice_swz(k + 3 * STEP)] = x3;
       }
-      for (; k < N; k += STEP) tile[k * ld + rr] = src[(long long)k * N];
+      for (; k < N; k += STEP) dst[slice_swz(k)] = src[(long long)k * N];
     }
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long plane = (long long)N * Kp;
   for (int rr = warp; rr < nr; rr += blockDim.x / 32) {
+    const InT* row = tile + rr * ldr;
     auto elem = [&](int k) -> InT {
-      const InT v = trans ? tile[k * ld + rr] : tile[rr * N + k];
+      const InT v = row[slice_swz(k)];
       return conj ? conj_of(v) : v;
     };
     int mx = -100000;
@@ -104,19 +122,21 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
     const int r = r0 + rr;
     if (lane == 0) exps[(long long)q * N + r] = e;
     __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
-    for (int k = 2 * lane; k < N; k += 64) {
-      const InT v0 = elem(k);
-      const InT v1 = (k + 1 < N) ? elem(k + 1) : zero_of(v0);
-      float re0[S], im0[S], re1[S], im1[S];
-      digits_re_im<S>(v0, e, re0, im0);
-      digits_re_im<S>(v1, e, re1, im1);
+    // four adjacent entries per lane, one 8-byte store per digit plane
+    for (int k = 4 * lane; k < N; k += 128) {
+      float re[4][S], im[4][S];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const InT v = (k + c < N) ? elem(k + c) : zero_of(row[0]);
+        digits_re_im<S>(v, e, re[c], im[c]);
+      }
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 0) * plane + k) = __floats2bfloat162_rn(re0[i], re1[i]);
-        *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 1) * plane + k) = __floats2bfloat162_rn(im0[i], im1[i]);
+        __nv_bfloat16* o = orow + (long long)P * i * plane + k;
+        *reinterpret_cast<uint2*>(o) = pack_bf16x4(re[0][i], re[1][i], re[2][i], re[3][i]);
+        *reinterpret_cast<uint2*>(o + plane) = pack_bf16x4(im[0][i], im[1][i], im[2][i], im[3][i]);
         if (P == 3)
-          *reinterpret_cast<__nv_bfloat162*>(orow + ((long long)P * i + 2) * plane + k) =
-              __floats2bfloat162_rn(-re0[i], -re1[i]);
+          *reinterpret_cast<uint2*>(o + 2 * plane) = pack_bf16x4(-re[0][i], -re[1][i], -re[2][i], -re[3][i]);
       }
     }
   }
@@ -130,10 +150,6 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
 // contiguous bytes per warp store).  Same output as slice_kernel.  With sum3
 // (P = 3) the third plane holds the digits of re + im (the 3M product's
 // operand) at the row exponent e + 1 instead of -re: |re + im| < 2^(e+1).
-__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
-  const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
-  return make_uint2(*reinterpret_cast<const uint32_t*>(&lo), *reinterpret_cast<const uint32_t*>(&hi));
-}
 
 // W consecutive bf16 values as one 8-byte (W = 4) or 16-byte (W = 8) store
 template <int W>
@@ -264,12 +280,17 @@ int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int
     }
   }
   if (sum3) return NSPT_ERR_UNSUPPORTED;  // the (re + im) plane: row form only
-  const size_t smem = (size_t)(trans ? N * (RB + 1) : RB * N) * sizeof(InT);
-  cudaError_t e = cudaFuncSetAttribute(slice_kernel<S, InT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // column sources: 16 rows per CTA while the tile stays within 200 KB of shared memory (32 rows,
+  // one CTA per SM at N = 225, measured slower)
+  const bool wide = trans && (size_t)16 * slice_ldr(N) * sizeof(InT) <= (size_t)200 * 1024;
+  const int rbk = wide ? 16 : RB;
+  auto kern = wide ? slice_kernel<S, InT, 16> : slice_kernel<S, InT, RB>;
+  const size_t smem = (size_t)rbk * slice_ldr(N) * sizeof(InT);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
-  dim3 grid((N + RB - 1) / RB, Q);
+  dim3 grid((N + rbk - 1) / rbk, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
-  slice_kernel<S, InT><<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, P, out, exps);
+  kern<<<grid, 256, smem, st>>>(X, bstride, M, rev, trans, conj, N, Kp, P, out, exps);
   e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   return NSPT_OK;
