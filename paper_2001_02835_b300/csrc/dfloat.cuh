@@ -178,7 +178,23 @@ __device__ __forceinline__ double f2d(float f) {
   }
   return __longlong_as_double((long long)bits);
 }
-__device__ __forceinline__ double df_to_double(dfl a) { return f2d(a.h) + f2d(a.l); }
+// normal floats and zeros, the common case: the FP64 word is the float's sign, its exponent
+// rebiased (+896 in the 11-bit field) and its fraction shifted up by 29 bits
+__device__ __forceinline__ bool f2d_fast_ok(float f) {
+  const unsigned a = __float_as_uint(f) & 0x7FFFFFFFu;
+  return a == 0u || (a >> 23) - 1u < 254u;
+}
+__device__ __forceinline__ double f2d_fast(float f) {
+  const unsigned u = __float_as_uint(f), a = u & 0x7FFFFFFFu;
+  const unsigned hi = (u & 0x80000000u) | (a ? (a >> 3) + (896u << 20) : 0u);
+  return __hiloint2double((int)hi, (int)(a << 29));
+}
+__device__ __forceinline__ double df_to_double(dfl a) {
+  // one uniform branch: the whole warp takes the short path unless a subnormal, infinite or
+  // NaN part is present
+  if (__all_sync(__activemask(), f2d_fast_ok(a.h) && f2d_fast_ok(a.l))) return f2d_fast(a.h) + f2d_fast(a.l);
+  return f2d(a.h) + f2d(a.l);
+}
 
 // round(x * 2^sh) for x = hi + lo as a signed 64-bit integer (|result| < 2^63)
 __device__ __forceinline__ long long f_scaled_int(float f, int sh_base) {
