@@ -45,7 +45,7 @@ typedef enum nspt_status {
                                  or the reverse; checked with cudaPointerGetAttributes unless the
                                  stream is being captured into a graph) */
   NSPT_ERR_ALIAS = -2,        /* an output overlaps an input */
-  NSPT_ERR_UNSUPPORTED = -3,  /* valid request this build does not implement */
+  NSPT_ERR_UNSUPPORTED = -3,  /* valid request the library does not implement */
   NSPT_ERR_WORKSPACE = -4,    /* opts->workspace missing or too small */
   NSPT_ERR_CUDA = -5,         /* CUDA runtime error (see nspt_last_error) */
   NSPT_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */
