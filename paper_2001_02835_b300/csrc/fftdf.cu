@@ -71,21 +71,18 @@ fft_fwd_df_kernel(const double2* __restrict__ in, long long in_stride, float4* _
         }
       return;
     }
-    // transposed output: back to shared memory (rows this thread read in the exchange) with
-    // column c stored at c ^ ((c >> 3) & 3), which keeps both this write and the block store's
-    // reads (columns 4 jj + ll, jj = 0..7, in a quarter warp) free of bank conflicts
-    static_assert(EB == 32, "column swizzle of the transposed store");
-    auto swz = [](int c) { return c ^ ((c >> 3) & 3); };
+    // transposed output straight from the registers: this thread's entry (j, l) =
+    // (j0 + e / CB, l0 + e % CB) goes to (l, j), so for one mode a warp writes CB runs of 8
+    // consecutive j (128 bytes each)
+    if (!valid) return;
+    float4* dst = out + (long long)b * M * E + (long long)(l0 + e % CB) * N + j0 + e / CB;
 #pragma unroll
     for (int t = 0; t < GPT; ++t)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) st(&sm[(8 * (y * GPT + t) + j) * EB + swz(e)], z[t][j]);
-    __syncthreads();
-    const int jj = e % 8, ll = e / 8, c = jj * CB + ll;
-    if (j0 + jj >= N || l0 + ll >= N) return;
-    float4* dst = out + (long long)b * M * E + (long long)(l0 + ll) * N + j0 + jj;
-#pragma unroll
-    for (int i = y; i < M; i += 8) dst[(long long)bitrev<M>(i) * E] = sm[i * EB + swz(c)];
+      for (int j = 0; j < 8; ++j) {
+        const int i = 8 * (y * GPT + t) + j;
+        st(&dst[(long long)bitrev<M>(i) * E], z[t][j]);
+      }
     return;
   } else {
     fftdf::fwd_to_smem<M, EB>(sm, src, E, valid, T, log2s, log2r);
