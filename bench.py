@@ -437,6 +437,14 @@ def per_order_vs_oracle(torch, nspt, A, B, dA, dB, dC, T, barrier, extras):
     extras["split_S6_3m_T%d" % T] = {"products_per_s": BATCH / (ms3 * 1e-3), "ms_per_step": ms3,
                                      "max_per_order_rel_err_vs_oracle": float(e.max()),
                                      "note": "three real products per complex product (3M); 4M above"}
+    kwn = dict(algo="naive", prec="split")
+    msn = time_steps(torch, lambda: nspt.polymat_mul(dA, dB, dC, **kwn), 2, 1, barrier) / 2
+    e = errs(dC.cpu().numpy())
+    out["split_S6_naive"] = [float("%.3g" % x) for x in e]
+    extras["split_S6_naive_T%d" % T] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
+                                        "eff_tflops": naive_flops(A.shape[-1], T) * BATCH / (msn * 1e-3) / 1e12,
+                                        "max_per_order_rel_err_vs_oracle": float(e.max()),
+                                        "note": "naive form (Eq. 5): one tensor-core GEMM per pair of orders"}
     return out
 
 
@@ -615,6 +623,10 @@ def run_ours(args):
         msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive"), 1, 1, barrier)
         extras["fp64_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
+        msn = time_steps(torch, lambda: nspt.polymat_mul(a31, b31, c31, algo="naive", prec="split"), 3, 1,
+                         barrier) / 3
+        extras["split_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
+                                     "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
         del a31, b31, c31
 
     cpu = None

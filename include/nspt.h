@@ -55,7 +55,8 @@ typedef enum nspt_status {
 /* algorithm of the star product */
 enum { NSPT_ALGO_NAIVE = 0, /* Eq. 5: C_k = sum_l A_l B_{k-l}, (T+1)(T+2)/2 GEMMs */
        NSPT_ALGO_FFT = 1,   /* Sec. 2 Steps 1-5: M-point order FFT, M mode GEMMs, inverse FFT */
-       NSPT_ALGO_AUTO = 2 };/* FFT when T >= 3, else naive */
+       NSPT_ALGO_AUTO = 2 };/* FFT when T >= 3, else naive (split form: FFT in every entry
+                               point but nspt_polymat_mul) */
 
 /* arithmetic of the mode GEMMs */
 enum { NSPT_PREC_FP64 = 0,  /* plain FP64 everywhere (the paper's ZGEMM form) */
@@ -70,8 +71,9 @@ enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_
 
 typedef struct nspt_opts {
   int algo;            /* NSPT_ALGO_*; default NSPT_ALGO_AUTO */
-  int prec;            /* NSPT_PREC_*; default NSPT_PREC_FP64; NSPT_PREC_SPLIT needs the FFT
-                          form and N <= 1024 (else NSPT_ERR_UNSUPPORTED) */
+  int prec;            /* NSPT_PREC_*; default NSPT_PREC_FP64; NSPT_PREC_SPLIT needs N <= 1024,
+                          and the FFT form except in nspt_polymat_mul (and its workspace
+                          query), which also takes the naive form (else NSPT_ERR_UNSUPPORTED) */
   int fft_len;         /* M; 0 = smallest power of two >= 2(T+1); else a power of two
                           >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
@@ -82,7 +84,10 @@ typedef struct nspt_opts {
                           NSPT_ERR_UNSUPPORTED); 0 = 4 */
   int rescale_log2r;   /* per-order rescale A_k, B_k -> r^k A_k, r^k B_k with r = 2^rescale_log2r,
                           undone exactly on C (not part of the paper): FFT-CONV products (split
-                          and FP64 forms, the FP64 backward excepted); split and FP64 FFT forms
+                          and FP64 forms, the FP64 backward excepted); naive split products
+                          (an exponent shift of the slices of order k: no rounding, it only
+                          keeps the double-float accumulator within the FP32 range); split
+                          and FP64 FFT forms
                           of nspt_tek_langevin_step and
                           nspt_tek_md_trajectory, where it applies to every order transform
                           of the step (the map X_k -> r^k X_k commutes with every product and
@@ -123,6 +128,10 @@ NSPT_API size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_
  * M, forward transform with w = exp(+2 pi i/M) (Step 2), M mode-wise complex
  * GEMMs (Step 3), inverse transform with 1/M (Step 4), keep orders 0..T
  * (Step 5).  N >= 1, T >= 0, batch >= 1.
+ * Split form, NAIVE: every order of A and B is sliced once from FP64 and each
+ * of the (T+1)(T+2)/2 products A_l B_{k-l} is one tensor-core GEMM with its own
+ * row and column exponents, summed over l in double-float (no transforms, so
+ * no order's precision depends on the others' size).
  */
 NSPT_API int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int batch,
                      const nspt_opts* opts, void* stream);

@@ -187,7 +187,8 @@ def _with_ws(op, N, T, batch, opts, device):
 
 def polymat_mul(A: torch.Tensor, B: torch.Tensor, C: Optional[torch.Tensor] = None, **kw) -> torch.Tensor:
     """C = A star B (Eq. 5) through nspt_polymat_mul; kw: algo, prec, fft_len, slices, rescale_log2r,
-    complex_mode (split form: 4, or 3 for three real products per complex product)."""
+    complex_mode (split form: 4, or 3 for three real products per complex product).  Both forms
+    (algo "naive" or "fft") take prec "split"."""
     _check_tensor(A, "A")
     _check_tensor(B, "B")
     if A.shape != B.shape:

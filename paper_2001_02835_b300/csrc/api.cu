@@ -39,17 +39,22 @@ struct Plan {
 };
 
 // allow_3m: the entry point takes complex_mode = 3 (the plain product)
-int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool allow_3m = false) {
+// product: the plan is for nspt_polymat_mul, which alone takes the 3M variant and the naive form
+// of the split products
+int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool product = false) {
   nspt_opts d;
   nspt_opts_default(&d);
   if (!o) o = &d;
   if (N < 1 || T < 0 || batch < 1 || N > 4096 || T > 255) return NSPT_ERR_ARG;
   p->N = N; p->T = T; p->batch = batch; p->E = (long long)N * N;
   p->algo = o->algo;
-  if (p->algo == NSPT_ALGO_AUTO) p->algo = (T >= 3) ? NSPT_ALGO_FFT : NSPT_ALGO_NAIVE;
-  if (p->algo != NSPT_ALGO_NAIVE && p->algo != NSPT_ALGO_FFT) return NSPT_ERR_ARG;
   p->prec = o->prec;
   if (p->prec != NSPT_PREC_FP64 && p->prec != NSPT_PREC_SPLIT) return NSPT_ERR_ARG;
+  // auto: naive below T = 3, where the transforms cost more than the few pair products save;
+  // the split form's naive products exist for nspt_polymat_mul only
+  if (p->algo == NSPT_ALGO_AUTO)
+    p->algo = (T >= 3 || (p->prec == NSPT_PREC_SPLIT && !product)) ? NSPT_ALGO_FFT : NSPT_ALGO_NAIVE;
+  if (p->algo != NSPT_ALGO_NAIVE && p->algo != NSPT_ALGO_FFT) return NSPT_ERR_ARG;
   p->M = o->fft_len ? o->fft_len : next_pow2(2 * (T + 1));
   if (ilog2_exact(p->M) < 0 || p->M < 2 * (T + 1) || p->M > 512) return NSPT_ERR_ARG;
   p->slices = o->slices ? o->slices : 6;
@@ -57,7 +62,8 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool allow_3
   p->cm = 4;
   if (o->complex_mode == 3) {
     // 3M: split-form FFT-CONV products with S <= 6 and row-form slicing (N <= 512)
-    if (!allow_3m || p->prec != NSPT_PREC_SPLIT || p->slices > 6 || N > 512) return NSPT_ERR_UNSUPPORTED;
+    if (!product || p->prec != NSPT_PREC_SPLIT || p->algo != NSPT_ALGO_FFT || p->slices > 6 || N > 512)
+      return NSPT_ERR_UNSUPPORTED;
     p->cm = 3;
   } else if (o->complex_mode != 0 && o->complex_mode != 4) {
     return NSPT_ERR_UNSUPPORTED;
@@ -65,7 +71,7 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool allow_3
   p->rescale_auto = (o->rescale_log2r == NSPT_RESCALE_AUTO);
   p->log2r = p->rescale_auto ? 0 : o->rescale_log2r;
   if (!p->rescale_auto && (p->log2r < -60 || p->log2r > 60)) return NSPT_ERR_ARG;
-  if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE) return NSPT_ERR_UNSUPPORTED;
+  if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE && !product) return NSPT_ERR_UNSUPPORTED;
   // the split form's slicers hold up to 8 spectrum rows of N entries in shared memory
   if (p->prec == NSPT_PREC_SPLIT && N > 1024) return NSPT_ERR_UNSUPPORTED;
   return NSPT_OK;
@@ -111,7 +117,8 @@ cudaError_t add_identity(double2* X, long long stride_mats, int N, long long cou
 
 // --- forward product, FP64 ---
 size_t ws_mul(const Plan& p) {
-  if (p.algo == NSPT_ALGO_NAIVE) return 0;
+  if (p.algo == NSPT_ALGO_NAIVE)
+    return p.prec == NSPT_PREC_SPLIT ? nspt_split_ws_naive(p.N, p.T, p.batch, p.slices) : 0;
   const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
   if (p.prec == NSPT_PREC_FP64) return 3 * ((spec + 255) & ~(size_t)255) + 2 * 513 * sizeof(int);  // + fit scratch
   return nspt_split_ws_mul(p.N, p.T, p.batch, p.M, p.slices, p.cm);
@@ -552,6 +559,8 @@ size_t ws_wilson(const Plan& p, int amax) {
 
 int mul_plan(const Plan& p, const double2* A, const double2* B, double2* C, void* ws, cudaStream_t st) {
   if (p.prec == NSPT_PREC_FP64) return mul_fp64(p, A, B, C, ws, st);
+  if (p.algo == NSPT_ALGO_NAIVE)
+    return nspt_split_mul_naive(p.N, p.T, p.batch, p.slices, p.log2r, p.rescale_auto, A, B, C, ws, st);
   return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, A, B, C, ws, st, p.cm);
 }
 
@@ -825,10 +834,7 @@ int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int ba
     const void* ptrs[3] = {A, B, C};
     if ((rc = nspt_check_ptrs(st, true, ptrs, 3))) return rc;
   }
-  if (p.prec == NSPT_PREC_FP64)
-    return mul_fp64(p, (const double2*)A, (const double2*)B, (double2*)C, opts ? opts->workspace : nullptr, st);
-  return nspt_split_mul(p.N, p.T, p.batch, p.M, p.slices, p.log2r, p.rescale_auto, (const double2*)A,
-                        (const double2*)B, (double2*)C, opts->workspace, st, p.cm);
+  return mul_plan(p, (const double2*)A, (const double2*)B, (double2*)C, opts ? opts->workspace : nullptr, st);
 }
 
 int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB, int N, int T,

@@ -629,6 +629,166 @@ int nspt_split_gemm_stage(const void* slA, const void* slB, const int* expA, con
   return nspt_split_gemm(a, st);
 }
 
+// ---------------------------------------------------------------------------
+// Naive form (Eq. 5) on the tensor cores: C_k = sum_{l=0}^{k} A_l B_{k-l} as
+// (T+1)(T+2)/2 split-precision GEMMs per batch element, one for each pair
+// (l, j = k - l), accumulated in double-float.  Every order is sliced once,
+// straight from FP64 (A_l by rows, B_j by columns); each GEMM carries its
+// own operands' row and column exponents, so an order is not limited by the
+// size of the others as in a mode product, and no order transform is run.
+//
+// Schedule.  The pairs with l - j = d form one batched GEMM over j with
+// consecutive slices of A and of B and an output every second order
+// (k = 2j + d).  Set i holds the differences d = -i and d = i + 1 (d = 0 and 1
+// for i = 0) of every batch element: they write orders of opposite parity, so
+// no output is written twice within a set.  Set i has about T + 1 - i GEMMs
+// per batch element, so sets i and T - i are launched together, into two
+// accumulators (sets 0 .. T/2 into the first, whose set 0 writes every order
+// once; the others into a zeroed second one), summed on the way out: about
+// T/2 + 1 launches of T + 2 GEMMs per batch element each, instead of T + 1
+// launches whose last ones fill a fraction of the SMs.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct NaiveWs {
+  int* err;
+  __nv_bfloat16 *slA, *slB;
+  int *expA, *expB;
+  float4 *Ct, *Ct2;   // the two accumulators (Ct2 unused at T = 0)
+};
+
+NaiveWs carve_naive(void* ws, int N, int T, int batch, int S, size_t* total) {
+  WsCarver w(ws, SIZE_MAX);
+  NaiveWs s;
+  const long long Q = (long long)batch * (T + 1);
+  s.err = w.take<int>(64);
+  s.slA = w.take<__nv_bfloat16>((size_t)Q * S * 2 * N * kpad(N));
+  s.slB = w.take<__nv_bfloat16>((size_t)Q * S * 3 * N * kpad(N));
+  s.expA = w.take<int>((size_t)Q * N);
+  s.expB = w.take<int>((size_t)Q * N);
+  s.Ct = w.take<float4>((size_t)Q * N * N);
+  s.Ct2 = T > 0 ? w.take<float4>((size_t)Q * N * N) : nullptr;
+  if (total) *total = w.off;
+  return s;
+}
+
+// e_r += k log2r on the rows of order k of both operands (count = batch (T+1) N rows each): the
+// slices then stand for 2^(k log2r) A_k and 2^(k log2r) B_k exactly, and every product
+// A_l B_{k-l} comes out scaled by 2^(k log2r).  A zero row keeps zero digits whatever its exponent.
+__global__ void naive_shift_exps_kernel(int* expA, int* expB, int N, int T1, long long count, int log2r,
+                                        const int* dlr) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int k = (int)((i / N) % T1);
+  const int lr = dlr ? *dlr : log2r;
+  expA[i] += k * lr;
+  expB[i] += k * lr;
+}
+
+// C_k = 2^(-k log2r) (hi + lo) in FP64 of the sum of the two accumulators (Ct2 may be null), for
+// count = batch (T+1) E entries
+__global__ void naive_out_kernel(const float4* __restrict__ Ct, const float4* __restrict__ Ct2,
+                                 double2* __restrict__ C, long long E, int T1, long long count, int log2r,
+                                 const int* dlr) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const int k = (int)((i / E) % T1);
+  const int sh = -k * (dlr ? *dlr : log2r);
+  const float4 a = Ct[i];
+  cdf v{dfl{a.x, a.y}, dfl{a.z, a.w}};
+  if (Ct2) {
+    const float4 b = Ct2[i];
+    v = cdf_add(v, cdf{dfl{b.x, b.y}, dfl{b.z, b.w}});
+  }
+  double re = df_to_double(v.re), im = df_to_double(v.im);
+  if (sh != 0) { re = scalbn(re, sh); im = scalbn(im, sh); }
+  C[i] = make_double2(re, im);
+}
+
+// the launches of the schedule above
+int naive_gemms(const NaiveWs& w, int N, int T, int batch, int S, cudaStream_t st) {
+  const int T1 = T + 1, Kp = kpad(N);
+  const long long sa = (long long)S * 2 * N * Kp, sb = (long long)S * 3 * N * Kp, E = (long long)N * N;
+  std::vector<SplitGemmArgs> probs;
+  // the GEMMs of set i into accumulator C (plain: the first write of every order it touches)
+  auto add_set = [&](int i, float4* Cacc, bool plain) {
+    const int ds[2] = {i == 0 ? 0 : -i, i + 1};
+    for (int b = 0; b < batch; ++b) {
+      for (int d : ds) {
+        if (d > T) continue;
+        const int j0 = std::max(0, -d);
+        const int cnt = (T - d) / 2 - j0 + 1;  // j = j0 .. floor((T - d) / 2)
+        if (cnt < 1) continue;
+        const long long l0 = j0 + d, k0 = 2LL * j0 + d, base = (long long)b * T1;
+        SplitGemmArgs a;
+        a.slicesA = w.slA + (base + l0) * sa;
+        a.slicesB = w.slB + (base + j0) * sb;
+        a.expA = w.expA + (base + l0) * N;
+        a.expB = w.expB + (base + j0) * N;
+        a.C = Cacc + (base + k0) * E;
+        a.ldc_q = 2 * E;
+        a.N = N; a.Kp = Kp; a.Q = cnt; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = 48;
+        a.alpha = make_double2(1.0, 0.0); a.use_alpha = 0; a.accumulate = !plain;
+        probs.push_back(a);
+      }
+    }
+  };
+  if (T > 0) TRYC(cudaMemsetAsync(w.Ct2, 0, (size_t)batch * T1 * E * sizeof(float4), st));
+  for (int i = 0; 2 * i <= T; ++i) {
+    probs.clear();
+    add_set(i, w.Ct, i == 0);
+    if (T - i > i) add_set(T - i, w.Ct2, false);
+    for (size_t o = 0; o < probs.size(); o += NSPT_SPLIT_MAX_PROBLEMS) {
+      const int n = (int)std::min<size_t>(NSPT_SPLIT_MAX_PROBLEMS, probs.size() - o);
+      TRYS(nspt_split_gemm_batch(probs.data() + o, n, S, 48, g_num_sms, st));
+    }
+  }
+  return NSPT_OK;
+}
+
+}  // namespace
+
+size_t nspt_split_ws_naive(int N, int T, int batch, int S) {
+  size_t total = 0;
+  carve_naive(nullptr, N, T, batch, S, &total);
+  return total;
+}
+
+int nspt_split_mul_naive(int N, int T, int batch, int S, int log2r, bool rescale_auto, const double2* A,
+                         const double2* B, double2* C, void* ws, cudaStream_t st) {
+  NaiveWs w = carve_naive(ws, N, T, batch, S, nullptr);
+  const int T1 = T + 1, Q = batch * T1;
+  // fitted rescale into a spare word of the status block (the per-order maxima go to the
+  // accumulator, which the first GEMM launch overwrites)
+  int* dlr = nullptr;
+  if (rescale_auto) {
+    dlr = w.err + 16;
+    TRYS(nspt_split_fit_rescale_dev(A, B, N, T, batch, reinterpret_cast<int*>(w.Ct), dlr, st));
+  }
+  TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  // a2: slices of every order, the two operands on side streams
+  TRYS(fork_join(2, st, [&](int i, cudaStream_t s) -> int {
+    if (i == 0) return slice_any<double2>(S, A, T1, T1, 0, 0, 0, N, Q, 2, w.slA, w.expA, s);
+    return slice_any<double2>(S, B, T1, T1, 0, 1, 0, N, Q, 3, w.slB, w.expB, s);
+  }));
+  const long long rows = (long long)Q * N, E = (long long)N * N;
+  if (rescale_auto || log2r != 0) {
+    ProfScope ps(NSPT_STAGE_OTHER, st);
+    naive_shift_exps_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(w.expA, w.expB, N, T1, rows, log2r,
+                                                                           dlr);
+    TRYC(cudaGetLastError());
+  }
+  // a3 (Eq. 5): the pair GEMMs, accumulated in double-float
+  TRYS(naive_gemms(w, N, T, batch, S, st));
+  {
+    ProfScope ps(NSPT_STAGE_OTHER, st);
+    const long long cnt = (long long)Q * E;
+    naive_out_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.Ct, w.Ct2, C, E, T1, cnt, log2r, dlr);
+    TRYC(cudaGetLastError());
+  }
+  return NSPT_OK;
+}
+
 int nspt_split_read_error(void* ws, int* host_err, cudaStream_t st) {
   if (!ws) return NSPT_ERR_ARG;
   cudaError_t e = cudaMemcpyAsync(host_err, ws, sizeof(int), cudaMemcpyDeviceToHost, st);

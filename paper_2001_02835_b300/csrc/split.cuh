@@ -11,6 +11,12 @@ size_t nspt_split_ws_mul(int N, int T, int batch, int M, int slices, int cm = 4)
 size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int slices);
 int nspt_split_mul(int N, int T, int batch, int M, int slices, int log2r, bool rescale_auto, const double2* A,
                    const double2* B, double2* C, void* ws, cudaStream_t st, int cm = 4);
+// naive form (Eq. 5) with split-precision pair GEMMs (every order sliced from FP64; no transforms);
+// log2r / rescale_auto: the slices of order k stand for 2^(k log2r) times the order (exponent shift),
+// undone on the FP64 output, so that the double-float accumulator stays in the FP32 range
+size_t nspt_split_ws_naive(int N, int T, int batch, int slices);
+int nspt_split_mul_naive(int N, int T, int batch, int slices, int log2r, bool rescale_auto, const double2* A,
+                         const double2* B, double2* C, void* ws, cudaStream_t st);
 int nspt_split_bwd(int N, int T, int batch, int M, int slices, int log2r, const double2* A, const double2* B,
                    const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
 // mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE; log2r: every order transform of the

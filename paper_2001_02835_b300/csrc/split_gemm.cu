@@ -354,7 +354,7 @@ split_gemm_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
         const int k = ea + eb - 14, k1 = k / 2;
         return pow2f(k1) * pow2f(k - k1);
       };
-      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
+      float4* crow = P.C + (long long)q * P.ldcq + (long long)(mvalid ? m : 0) * N;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();

@@ -13,6 +13,7 @@ struct SplitGemmArgs {
   int bn;               // output tile width (32 or 48; 0 = default 48)
   double2 alpha;        // C = alpha * A B (+ C) when use_alpha / accumulate
   int use_alpha, accumulate;
+  long long ldc_q = 0;  // float4 entries from C_q to C_{q+1} (0: N * N, consecutive matrices)
 };
 
 // problems per grouped launch (their tensor maps travel in the kernel parameters)

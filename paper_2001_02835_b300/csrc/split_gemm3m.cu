@@ -278,7 +278,7 @@ split_gemm3m_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
         const int k = ea + eb - 14, k1 = k / 2;
         return pow2f(k1) * pow2f(k - k1);
       };
-      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
+      float4* crow = P.C + (long long)q * P.ldcq + (long long)(mvalid ? m : 0) * N;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();
@@ -357,6 +357,7 @@ int launch3(const SplitGemmArgs* a, int count, cudaStream_t st, int num_sms) {
     if (nspt_make_slice_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, 3, (long long)a[i].Q * S, BN3, S))
       return NSPT_ERR_CUDA;
     P.expA = a[i].expA; P.expB = a[i].expB; P.C = a[i].C;
+    P.ldcq = a[i].ldc_q ? a[i].ldc_q : (long long)a[i].N * a[i].N;
     P.N = a[i].N; P.Q = a[i].Q;
     P.tilesM = (a[i].N + BM - 1) / BM;
     P.tilesN = (a[i].N + BN3 - 1) / BN3;

@@ -26,6 +26,7 @@ struct GemmProblem {  // aligned like its CUtensorMap members
   const int* expA;
   const int* expB;
   float4* C;
+  long long ldcq;        // float4 entries from C_q to C_{q+1}
   int N, Q, tilesM, tilesN;
   long long tile_begin;  // first global tile index of this problem
   float4 alpha;          // C = alpha * A B (+ C): (re_hi, re_lo, im_hi, im_lo)
@@ -112,6 +113,7 @@ int build_batch(GemmBatch<MAXP>* gb, const SplitGemmArgs* a, int count, int S, i
     if (nspt_make_slice_map(&P.mA, a[i].slicesA, a[i].N, a[i].Kp, 2, (long long)a[i].Q * S, BM, 1)) return -5;
     if (nspt_make_slice_map(&P.mB, a[i].slicesB, a[i].N, a[i].Kp, 3, (long long)a[i].Q * S, bn, S)) return -5;
     P.expA = a[i].expA; P.expB = a[i].expB; P.C = a[i].C;
+    P.ldcq = a[i].ldc_q ? a[i].ldc_q : (long long)a[i].N * a[i].N;
     P.N = a[i].N; P.Q = a[i].Q;
     P.tilesM = (a[i].N + BM - 1) / BM;
     P.tilesN = (a[i].N + bn - 1) / bn;

@@ -233,7 +233,7 @@ split_gemm_ta_kernel(const __grid_constant__ GemmBatch<MAXP> gb, int* err) {
       const int m = m0 + row;
       const bool mvalid = m < N;
       const int ea = mvalid ? __ldg(P.expA + (long long)q * N + m) : 0;
-      float4* crow = P.C + ((long long)q * N + (mvalid ? m : 0)) * N;
+      float4* crow = P.C + (long long)q * P.ldcq + (long long)(mvalid ? m : 0) * N;
       if (!wait_bar(&sm.acc_full, pacc, &sm.abort_flag, err, 6, gb.wait_ns)) break;
       pacc ^= 1;
       tc::fence_after_sync();
