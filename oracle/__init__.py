@@ -13,9 +13,14 @@ polymat : the star product (Eq. 5) naive and by direct DFT (Sec. 2, Steps 1-5),
           its backward (the truncated correlation), helpers on series.
 tek     : twist phases (Eq. 1), the order-truncated TEK action, the staple and
           drift of Eqs. 2-3, exp-star and one Langevin step.
+noise   : the Langevin step's traceless Hermitian noise drawn from the
+          counter-based generator Philox4x32-10 (its published definition), for
+          the library's seeded noise call.
 
-Every function is pinned by ``tests/test_oracle_pins.py`` against closed forms,
+Every function is pinned by ``tests/test_oracle_pins.py`` (``noise``: by
+``tests/test_oracle_noise.py``, with the generator's published known-answer
+vectors) against closed forms,
 library routines on special cases, brute force or exact arithmetic; none of the
 functions is "parity unpinned".
 """
-from . import polymat, tek  # noqa: F401
+from . import noise, polymat, tek  # noqa: F401
