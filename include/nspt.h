@@ -247,6 +247,29 @@ NSPT_API int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, i
                                     double eps, int nsteps, const nspt_opts* opts, void* stream);
 
 /*
+ * Seeded noise for nspt_tek_langevin_step (and the momentum refresh of
+ * nspt_tek_md_trajectory): `count` traceless Hermitian N x N matrices with
+ * the step's normalisation (eta = sum_a xi_a T^a, xi_a ~ N(0,1) on generators
+ * with Tr(T^a T^b) = delta^ab: E|eta_ij|^2 = 1 off the diagonal), drawn from the
+ * counter-based generator Philox4x32-10 (Salmon et al., SC 2011).  Every value
+ * depends only on (seed, t, matrix, position), t = counter + *d_counter:
+ *   key = (seed mod 2^32, seed div 2^32); block b of matrix c uses the counter
+ *   (b, c, t mod 2^32, t div 2^32) and gives Gaussians 2b, 2b+1 of the matrix
+ *   (row-major) by Box-Muller on two 53-bit uniforms,
+ *   u1 = ((w0 >> 5) 2^26 + (w1 >> 6) + 1) 2^-53, u2 = ((w2 >> 5) 2^26 + (w3 >> 6)) 2^-53,
+ *   z_2b = r cos(2 pi u2), z_2b+1 = r sin(2 pi u2), r = sqrt(-2 ln u1);
+ *   eta_ij = (z_{iN+j} + i z_{jN+i})/sqrt(2) for i < j, eta_ji = conj(eta_ij),
+ *   eta_ii = z_{iN+i} - mean_k z_{kN+k}.
+ *   eta       : [count][N][N] complex128 (output, device)
+ *   d_counter : device word or NULL; when given, t = counter + *d_counter and the
+ *               call adds 1 to *d_counter after drawing, so a captured CUDA graph
+ *               draws fresh noise at every replay.
+ * Two launches on `stream`; no workspace.  1 <= N <= 4096, count >= 1.
+ */
+NSPT_API int nspt_tek_noise(void* eta, int N, int count, unsigned long long seed, unsigned long long counter,
+                            unsigned long long* d_counter, void* stream);
+
+/*
  * C = A star B (as nspt_polymat_mul, same opts) for series in HOST memory --
  * pinned (page-locked) for the copies to overlap; no counterpart in the paper.
  * The batch goes through the GPU one element at a time in two device slots:

@@ -23,7 +23,7 @@ import torch
 __all__ = [
     "lib", "library_path", "Opts", "NsptError",
     "polymat_mul", "polymat_mul_host", "polymat_mul_backward", "tek_langevin_step", "tek_md_trajectory", "tek_wilson_loops",
-    "tek_unitarize", "order_fft", "order_ifft",
+    "tek_unitarize", "tek_noise", "order_fft", "order_ifft",
     "workspace_size", "star", "PolymatMul",
     "ALGO_NAIVE", "ALGO_FFT", "ALGO_AUTO", "PREC_FP64", "PREC_SPLIT", "RESCALE_AUTO",
 ]
@@ -75,6 +75,7 @@ _SIGS = {
     "nspt_tek_langevin_step": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_md_trajectory": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _d, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_unitarize": (_i, [_vp, _i, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
+    "nspt_tek_noise": (_i, [_vp, _i, _i, ctypes.c_ulonglong, ctypes.c_ulonglong, _vp, _vp]),
     "nspt_order_fft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_order_ifft": (_i, [_vp, _vp, _i, _i, _i, _i, _vp]),
     "nspt_status_string": (ctypes.c_char_p, [_i]),
@@ -267,6 +268,27 @@ def tek_langevin_step(U: torch.Tensor, eta: torch.Tensor, flux: int, eps: float,
                                       N, T, batch, int(flux), float(eps), ctypes.byref(opts), _stream_ptr(U.device))
     _check(rc, "nspt_tek_langevin_step")
     return U, F
+
+
+def tek_noise(N: int, count: int, seed: int, counter: int = 0, d_counter: Optional[torch.Tensor] = None,
+              out: Optional[torch.Tensor] = None, device="cuda") -> torch.Tensor:
+    """`count` traceless Hermitian N x N noise matrices (complex128, (count, N, N)) from the
+    counter-based generator of nspt_tek_noise, keyed by seed and counter; with d_counter (a
+    one-element int64 tensor on the device) the counter is counter + d_counter, advanced by one
+    per call on the device, so that a captured graph draws fresh noise at every replay."""
+    if out is None:
+        out = torch.empty((count, N, N), dtype=torch.complex128, device=device)
+    _check_tensor(out, "out")
+    if tuple(out.shape[-3:]) != (count, N, N) or out.numel() != count * N * N:
+        raise ValueError("out must hold (count, N, N) complex128")
+    if d_counter is not None and (d_counter.dtype != torch.int64 or d_counter.numel() != 1
+                                  or d_counter.device != out.device):
+        raise ValueError("d_counter must be a one-element int64 tensor on the output's device")
+    rc = lib().nspt_tek_noise(out.data_ptr(), int(N), int(count), int(seed) & (2 ** 64 - 1),
+                              int(counter) & (2 ** 64 - 1), d_counter.data_ptr() if d_counter is not None else None,
+                              _stream_ptr(out.device))
+    _check(rc, "nspt_tek_noise")
+    return out
 
 
 def tek_md_trajectory(U: torch.Tensor, P: torch.Tensor, flux: int, eps: float, nsteps: int,

@@ -120,6 +120,14 @@ def test_naive_split_plans_need_no_gpu(L):
     assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, N, T, b, ctypes.byref(on), None) == -4
 
 
+def test_noise_argument_checks_need_no_gpu(L):
+    """nspt_tek_noise refuses a NULL output and empty or oversized shapes on the host."""
+    assert L.nspt_tek_noise(None, 9, 4, 1, 0, None, None) == -1
+    assert L.nspt_tek_noise(1 << 20, 0, 4, 1, 0, None, None) == -1
+    assert L.nspt_tek_noise(1 << 20, 4097, 4, 1, 0, None, None) == -1
+    assert L.nspt_tek_noise(1 << 20, 9, 0, 1, 0, None, None) == -1
+
+
 def test_argument_checks_of_md_wilson_and_host_product(L):
     import paper_2001_02835_b300 as n
     o = n.make_opts()
