@@ -364,6 +364,17 @@ def langevin_leg(torch, nspt, barrier, L=11, T=31, streams=8, flux=3, eps=0.01):
                         barrier) / reps
         out["%s_ms_per_step" % p] = ms
         out["%s_link_updates_per_s" % p] = streams * 4 / (ms * 1e-3)
+    # the same split step with its noise drawn on the device each step (seeded generator,
+    # device counter advanced by every draw)
+    ctr = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tEs = torch.empty((streams * 4, N, N), dtype=torch.complex128, device="cuda")
+    tU = tU0.clone()
+
+    def seeded_step():
+        nspt.tek_noise(N, streams * 4, syn.SEED_BASE + 4, 0, d_counter=ctr, out=tEs)
+        nspt.tek_langevin_step(tU, tEs.view(streams, 4, N, N), flux, eps, algo="fft", prec="split")
+
+    out["split_seeded_noise_ms_per_step"] = time_steps(torch, seeded_step, 5, 1, barrier) / 5
     t0 = time.perf_counter()
     tek.langevin_step(U[0], eta[0], tek.twist_phases(L, flux), eps)
     out["oracle_ms_per_stream"] = 1e3 * (time.perf_counter() - t0)
