@@ -638,6 +638,12 @@ def run_ours(args):
                          barrier) / 3
         extras["split_naive_T31"] = {"products_per_s": BATCH / (msn * 1e-3), "ms_per_step": msn,
                                      "eff_tflops": naive_flops(N, 31) * BATCH / (msn * 1e-3) / 1e12}
+        g31 = torch.from_numpy(syn.gaussian(syn.rng(syn.SEED_BASE + 10), A31.shape, 1.0)).cuda()
+        msb = time_steps(torch, lambda: nspt.polymat_mul_backward(a31, b31, g31, algo="naive", prec="split"), 2, 1,
+                         barrier) / 2
+        extras["backward_split_naive_T31"] = {"ms_per_batch": msb, "products_per_s": BATCH / (msb * 1e-3),
+                                              "note": "gA and gB, one tensor-core GEMM per pair of orders each"}
+        del g31
         del a31, b31, c31
 
     cpu = None

@@ -55,8 +55,8 @@ typedef enum nspt_status {
 /* algorithm of the star product */
 enum { NSPT_ALGO_NAIVE = 0, /* Eq. 5: C_k = sum_l A_l B_{k-l}, (T+1)(T+2)/2 GEMMs */
        NSPT_ALGO_FFT = 1,   /* Sec. 2 Steps 1-5: M-point order FFT, M mode GEMMs, inverse FFT */
-       NSPT_ALGO_AUTO = 2 };/* FFT when T >= 3, else naive (split form: FFT in every entry
-                               point but nspt_polymat_mul) */
+       NSPT_ALGO_AUTO = 2 };/* FFT when T >= 3, else naive (split form: FFT in the entry
+                               points that have no naive split form) */
 
 /* arithmetic of the mode GEMMs */
 enum { NSPT_PREC_FP64 = 0,  /* plain FP64 everywhere (the paper's ZGEMM form) */
@@ -72,8 +72,9 @@ enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_
 typedef struct nspt_opts {
   int algo;            /* NSPT_ALGO_*; default NSPT_ALGO_AUTO */
   int prec;            /* NSPT_PREC_*; default NSPT_PREC_FP64; NSPT_PREC_SPLIT needs N <= 1024,
-                          and the FFT form except in nspt_polymat_mul (and its workspace
-                          query), which also takes the naive form (else NSPT_ERR_UNSUPPORTED) */
+                          and the FFT form except in nspt_polymat_mul, nspt_polymat_mul_host and
+                          nspt_polymat_mul_backward (and their workspace queries), which also
+                          take the naive form (else NSPT_ERR_UNSUPPORTED) */
   int fft_len;         /* M; 0 = smallest power of two >= 2(T+1); else a power of two
                           >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
@@ -141,7 +142,10 @@ NSPT_API int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int 
  * (the truncated correlations obtained by differentiating Eq. 5):
  *   gA_j = sum_{k=j}^{T} gC_k (B_{k-j})^H,   gB_j = sum_{k=j}^{T} (A_{k-j})^H gC_k.
  * FFT form: gA~_p = G~_p (B~_p)^H and gB~_p = (A~_p)^H G~_p, inverse
- * transform, keep 0..T (wrap-free for M >= 2T+1).
+ * transform, keep 0..T (wrap-free for M >= 2T+1).  Split form, NAIVE: one
+ * tensor-core GEMM per pair (k, k - j), every order sliced once from FP64,
+ * double-float sums; a fixed rescale_log2r shifts the slices' exponents (gC_k
+ * by -k log2r, A_m and B_m by m log2r) and is undone on the output.
  *   A, B, gC : [batch][T+1][N][N] inputs;  gA, gB : outputs, either may be NULL.
  */
 NSPT_API int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB,

@@ -39,9 +39,11 @@ struct Plan {
 };
 
 // allow_3m: the entry point takes complex_mode = 3 (the plain product)
-// product: the plan is for nspt_polymat_mul, which alone takes the 3M variant and the naive form
-// of the split products
-int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool product = false) {
+// op: the NSPT_OP_* call the plan is for (-1: a plan used inside another entry point).  The
+// product (NSPT_OP_MUL) alone takes the 3M variant; the product and its backward take the naive
+// form of the split products
+int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, int op = -1) {
+  const bool product = op == NSPT_OP_MUL, naive_split_ok = product || op == NSPT_OP_MUL_BACKWARD;
   nspt_opts d;
   nspt_opts_default(&d);
   if (!o) o = &d;
@@ -53,7 +55,7 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool product
   // auto: naive below T = 3, where the transforms cost more than the few pair products save;
   // the split form's naive products exist for nspt_polymat_mul only
   if (p->algo == NSPT_ALGO_AUTO)
-    p->algo = (T >= 3 || (p->prec == NSPT_PREC_SPLIT && !product)) ? NSPT_ALGO_FFT : NSPT_ALGO_NAIVE;
+    p->algo = (T >= 3 || (p->prec == NSPT_PREC_SPLIT && !naive_split_ok)) ? NSPT_ALGO_FFT : NSPT_ALGO_NAIVE;
   if (p->algo != NSPT_ALGO_NAIVE && p->algo != NSPT_ALGO_FFT) return NSPT_ERR_ARG;
   p->M = o->fft_len ? o->fft_len : next_pow2(2 * (T + 1));
   if (ilog2_exact(p->M) < 0 || p->M < 2 * (T + 1) || p->M > 512) return NSPT_ERR_ARG;
@@ -71,7 +73,7 @@ int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, bool product
   p->rescale_auto = (o->rescale_log2r == NSPT_RESCALE_AUTO);
   p->log2r = p->rescale_auto ? 0 : o->rescale_log2r;
   if (!p->rescale_auto && (p->log2r < -60 || p->log2r > 60)) return NSPT_ERR_ARG;
-  if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE && !product) return NSPT_ERR_UNSUPPORTED;
+  if (p->prec == NSPT_PREC_SPLIT && p->algo == NSPT_ALGO_NAIVE && !naive_split_ok) return NSPT_ERR_UNSUPPORTED;
   // the split form's slicers hold up to 8 spectrum rows of N entries in shared memory
   if (p->prec == NSPT_PREC_SPLIT && N > 1024) return NSPT_ERR_UNSUPPORTED;
   return NSPT_OK;
@@ -156,7 +158,8 @@ int mul_fp64(const Plan& p, const double2* A, const double2* B, double2* C, void
 
 // --- backward, FP64 ---
 size_t ws_bwd(const Plan& p) {
-  if (p.algo == NSPT_ALGO_NAIVE) return 0;
+  if (p.algo == NSPT_ALGO_NAIVE)
+    return p.prec == NSPT_PREC_SPLIT ? nspt_split_ws_naive(p.N, p.T, p.batch, p.slices) : 0;
   const size_t spec = (size_t)p.batch * p.M * p.E * sizeof(double2);
   if (p.prec == NSPT_PREC_FP64) return 4 * ((spec + 255) & ~(size_t)255);
   return nspt_split_ws_bwd(p.N, p.T, p.batch, p.M, p.slices);
@@ -801,7 +804,7 @@ int nspt_init(void) {
 
 size_t nspt_workspace_size(int op, int N, int T, int batch, const nspt_opts* opts) {
   Plan p;
-  if (make_plan(N, T, batch, opts, &p, op == NSPT_OP_MUL) != NSPT_OK) return 0;
+  if (make_plan(N, T, batch, opts, &p, op) != NSPT_OK) return 0;
   switch (op) {
     case NSPT_OP_MUL: return ws_mul(p);
     case NSPT_OP_MUL_BACKWARD: return ws_bwd(p);
@@ -822,7 +825,7 @@ static int check_ws(const nspt_opts* o, size_t need) {
 int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int batch, const nspt_opts* opts,
                      void* stream) {
   Plan p;
-  int rc = make_plan(N, T, batch, opts, &p, true);
+  int rc = make_plan(N, T, batch, opts, &p, NSPT_OP_MUL);
   if (rc) return rc;
   if (!A || !B || !C) return NSPT_ERR_ARG;
   const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
@@ -840,7 +843,7 @@ int nspt_polymat_mul(const void* A, const void* B, void* C, int N, int T, int ba
 int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void* gA, void* gB, int N, int T,
                               int batch, const nspt_opts* opts, void* stream) {
   Plan p;
-  int rc = make_plan(N, T, batch, opts, &p);
+  int rc = make_plan(N, T, batch, opts, &p, NSPT_OP_MUL_BACKWARD);
   if (rc) return rc;
   if (!A || !B || !gC) return NSPT_ERR_ARG;
   if (!gA && !gB) return NSPT_OK;
@@ -859,6 +862,9 @@ int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void
   if (p.prec == NSPT_PREC_FP64)
     return bwd_fp64(p, (const double2*)A, (const double2*)B, (const double2*)gC, (double2*)gA, (double2*)gB,
                     opts ? opts->workspace : nullptr, st);
+  if (p.algo == NSPT_ALGO_NAIVE)
+    return nspt_split_bwd_naive(p.N, p.T, p.batch, p.slices, p.log2r, (const double2*)A, (const double2*)B,
+                                (const double2*)gC, (double2*)gA, (double2*)gB, opts->workspace, st);
   return nspt_split_bwd(p.N, p.T, p.batch, p.M, p.slices, p.log2r, (const double2*)A, (const double2*)B,
                         (const double2*)gC, (double2*)gA, (double2*)gB, opts->workspace, st);
 }
@@ -1045,16 +1051,16 @@ int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int 
 
 size_t nspt_workspace_size_host(int N, int T, int batch, const nspt_opts* opts) {
   Plan pc;
-  if (batch < 1 || make_plan(N, T, 1, opts, &pc)) return 0;
+  if (batch < 1 || make_plan(N, T, 1, opts, &pc, NSPT_OP_MUL)) return 0;
   return ws_host(pc);
 }
 
 int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, int batch, const nspt_opts* opts,
                           void* stream) {
   Plan p, pc;
-  int rc = make_plan(N, T, batch, opts, &p);
+  int rc = make_plan(N, T, batch, opts, &p, NSPT_OP_MUL);
   if (rc) return rc;
-  if ((rc = make_plan(N, T, 1, opts, &pc))) return rc;
+  if ((rc = make_plan(N, T, 1, opts, &pc, NSPT_OP_MUL))) return rc;
   if (!A || !B || !C) return NSPT_ERR_ARG;
   if (pc.rescale_auto) return NSPT_ERR_UNSUPPORTED;  // it synchronises the stream per element
   const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);

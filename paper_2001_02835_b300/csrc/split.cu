@@ -43,7 +43,8 @@ using namespace digits;
 // source matrix (trans = 0) or its column r (trans = 1), conjugated if conj;
 // P = 2 planes per digit (re, im) for a left operand, P = 3 (re, im, -re) for a
 // right operand of the tensor-core GEMM;
-// the source of plane q = b*M + p is mode p (rev = 0) or (M - p) mod M (rev = 1)
+// the source of plane q = b*M + p is mode p (rev = 0), (M - p) mod M (rev = 1) or
+// M - 1 - p (rev = 2, this kernel only: order series stored from the last order down)
 // of batch element b.
 constexpr int RB = 8;  // output rows per CTA
 
@@ -71,7 +72,7 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
   InT* tile = reinterpret_cast<InT*>(tile_raw);
   const int q = blockIdx.y;
   const int b = q / M, p = q % M;
-  const int sp = rev ? (M - p) % M : p;
+  const int sp = rev == 2 ? M - 1 - p : (rev ? (M - p) % M : p);
   const InT* Xm = X + ((long long)b * bstride + sp) * N * N;
   const int r0 = blockIdx.x * RBK;
   const int nr = min(RBK, N - r0);
@@ -272,8 +273,10 @@ int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int co
 template <int S, typename InT>
 int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp, int Q, int P,
                  int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
+  if (rev < 0 || rev > 2) return NSPT_ERR_ARG;
   if constexpr (std::is_same<InT, float4>::value) {
     if (!trans && N <= 512) {
+      if (rev == 2) return NSPT_ERR_UNSUPPORTED;   // the row form takes rev = 0, 1
       if (N <= 128) return launch_slice_rows<S, 1, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
       if (N <= 256) return launch_slice_rows<S, 1, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
       return launch_slice_rows<S, 2, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
@@ -672,28 +675,29 @@ NaiveWs carve_naive(void* ws, int N, int T, int batch, int S, size_t* total) {
   return s;
 }
 
-// e_r += k log2r on the rows of order k of both operands (count = batch (T+1) N rows each): the
-// slices then stand for 2^(k log2r) A_k and 2^(k log2r) B_k exactly, and every product
-// A_l B_{k-l} comes out scaled by 2^(k log2r).  A zero row keeps zero digits whatever its exponent.
-__global__ void naive_shift_exps_kernel(int* expA, int* expB, int N, int T1, long long count, int log2r,
-                                        const int* dlr) {
+// e_r += (m k + c) log2r on the rows of slot k (k = 0..T) of the two slice sets (m, c per set;
+// count = batch (T+1) N rows each): the slices then stand for exactly 2^((m k + c) log2r) times
+// their orders.  Products: m = 1, c = 0 for both operands, so every A_l B_{k-l} comes out scaled
+// by 2^(k log2r).  A zero row keeps zero digits whatever its exponent.
+__global__ void naive_shift_exps_kernel(int* expA, int* expB, int N, int T1, long long count, int mA, int cA,
+                                        int mB, int cB, int log2r, const int* dlr) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int k = (int)((i / N) % T1);
   const int lr = dlr ? *dlr : log2r;
-  expA[i] += k * lr;
-  expB[i] += k * lr;
+  expA[i] += (mA * k + cA) * lr;
+  expB[i] += (mB * k + cB) * lr;
 }
 
-// C_k = 2^(-k log2r) (hi + lo) in FP64 of the sum of the two accumulators (Ct2 may be null), for
-// count = batch (T+1) E entries
+// C_k = 2^(sgn k log2r) (hi + lo) in FP64 of the sum of the two accumulators (Ct2 may be null),
+// for count = batch (T+1) E entries (products: sgn = -1)
 __global__ void naive_out_kernel(const float4* __restrict__ Ct, const float4* __restrict__ Ct2,
-                                 double2* __restrict__ C, long long E, int T1, long long count, int log2r,
-                                 const int* dlr) {
+                                 double2* __restrict__ C, long long E, int T1, long long count, int sgn,
+                                 int log2r, const int* dlr) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= count) return;
   const int k = (int)((i / E) % T1);
-  const int sh = -k * (dlr ? *dlr : log2r);
+  const int sh = sgn * k * (dlr ? *dlr : log2r);
   const float4 a = Ct[i];
   cdf v{dfl{a.x, a.y}, dfl{a.z, a.w}};
   if (Ct2) {
@@ -703,6 +707,25 @@ __global__ void naive_out_kernel(const float4* __restrict__ Ct, const float4* __
   double re = df_to_double(v.re), im = df_to_double(v.im);
   if (sh != 0) { re = scalbn(re, sh); im = scalbn(im, sh); }
   C[i] = make_double2(re, im);
+}
+
+int naive_shift(const NaiveWs& w, int N, int T, int batch, int mA, int cA, int mB, int cB, int log2r,
+                const int* dlr, cudaStream_t st) {
+  const long long rows = (long long)batch * (T + 1) * N;
+  ProfScope ps(NSPT_STAGE_OTHER, st);
+  naive_shift_exps_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(w.expA, w.expB, N, T + 1, rows, mA, cA,
+                                                                         mB, cB, log2r, dlr);
+  TRYC(cudaGetLastError());
+  return NSPT_OK;
+}
+
+int naive_out(const NaiveWs& w, double2* C, int N, int T, int batch, int sgn, int log2r, const int* dlr,
+              cudaStream_t st) {
+  const long long E = (long long)N * N, cnt = (long long)batch * (T + 1) * E;
+  ProfScope ps(NSPT_STAGE_OTHER, st);
+  naive_out_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.Ct, w.Ct2, C, E, T + 1, cnt, sgn, log2r, dlr);
+  TRYC(cudaGetLastError());
+  return NSPT_OK;
 }
 
 // the launches of the schedule above
@@ -746,6 +769,73 @@ int naive_gemms(const NaiveWs& w, int N, int T, int batch, int S, cudaStream_t s
   return NSPT_OK;
 }
 
+// The backward's schedule.  gA_j = sum_k gC_k (B_{k-j})^H and gB_j = sum_k (A_{k-j})^H gC_k
+// are sums over the pairs (k, m = k - j).  Group s (0..2T) holds the pairs with k + m = s,
+// max(ceil(s/2), s - T) <= k <= min(s, T): its output j = 2k - s runs over every second order,
+// and the operand indexed by m is sliced in reversed order (slot T - m), so both operands' slots
+// rise by one with k (left_rev: the left operand is the m-indexed one).  Groups of one parity
+// write one parity of j.  Accumulator 0 takes the groups s <= T, accumulator 1 the groups
+// s > T (both zeroed first); in each, the even groups in ascending size go with the odd groups
+// in descending size, one such pair per accumulator per launch, so that the launches hold
+// about T + 2 GEMMs per batch element each.
+int corr_gemms(const NaiveWs& w, int N, int T, int batch, int S, bool left_rev, cudaStream_t st) {
+  const int T1 = T + 1, Kp = kpad(N);
+  const long long sa = (long long)S * 2 * N * Kp, sb = (long long)S * 3 * N * Kp, E = (long long)N * N;
+  struct Grp { int s, k0, cnt; };
+  std::vector<std::vector<Grp>> lists[2];
+  for (int a = 0; a < 2; ++a) {
+    std::vector<Grp> ev, od;
+    for (int s = (a == 0 ? 0 : T + 1); s <= (a == 0 ? T : 2 * T); ++s) {
+      Grp g;
+      g.s = s;
+      g.k0 = std::max((s + 1) / 2, s - T);
+      g.cnt = std::min(s, T) - g.k0 + 1;
+      if (g.cnt >= 1) (s % 2 ? od : ev).push_back(g);
+    }
+    auto smaller = [](const Grp& x, const Grp& y) { return x.cnt < y.cnt || (x.cnt == y.cnt && x.s < y.s); };
+    std::sort(ev.begin(), ev.end(), smaller);
+    std::sort(od.begin(), od.end(), smaller);
+    for (size_t i = 0; i < std::max(ev.size(), od.size()); ++i) {
+      std::vector<Grp> l;
+      if (i < ev.size()) l.push_back(ev[i]);
+      if (i < od.size()) l.push_back(od[od.size() - 1 - i]);
+      lists[a].push_back(l);
+    }
+  }
+  if (!lists[1].empty() && !w.Ct2) return NSPT_ERR_ARG;
+  TRYC(cudaMemsetAsync(w.Ct, 0, (size_t)batch * T1 * E * sizeof(float4), st));
+  if (w.Ct2) TRYC(cudaMemsetAsync(w.Ct2, 0, (size_t)batch * T1 * E * sizeof(float4), st));
+  std::vector<SplitGemmArgs> probs;
+  for (size_t li = 0; li < std::max(lists[0].size(), lists[1].size()); ++li) {
+    probs.clear();
+    for (int a = 0; a < 2; ++a) {
+      if (li >= lists[a].size()) continue;
+      for (const Grp& g : lists[a][li]) {
+        const long long up = g.k0, down = T - g.s + g.k0;   // slots of the k- and m-indexed operands
+        const long long l0 = left_rev ? down : up, r0 = left_rev ? up : down, j0 = 2LL * g.k0 - g.s;
+        for (int b = 0; b < batch; ++b) {
+          const long long base = (long long)b * T1;
+          SplitGemmArgs x;
+          x.slicesA = w.slA + (base + l0) * sa;
+          x.slicesB = w.slB + (base + r0) * sb;
+          x.expA = w.expA + (base + l0) * N;
+          x.expB = w.expB + (base + r0) * N;
+          x.C = (a == 0 ? w.Ct : w.Ct2) + (base + j0) * E;
+          x.ldc_q = 2 * E;
+          x.N = N; x.Kp = Kp; x.Q = g.cnt; x.S = S; x.num_sms = g_num_sms; x.err = w.err; x.bn = 48;
+          x.alpha = make_double2(1.0, 0.0); x.use_alpha = 0; x.accumulate = 1;
+          probs.push_back(x);
+        }
+      }
+    }
+    for (size_t o = 0; o < probs.size(); o += NSPT_SPLIT_MAX_PROBLEMS) {
+      const int n = (int)std::min<size_t>(NSPT_SPLIT_MAX_PROBLEMS, probs.size() - o);
+      TRYS(nspt_split_gemm_batch(probs.data() + o, n, S, 48, g_num_sms, st));
+    }
+  }
+  return NSPT_OK;
+}
+
 }  // namespace
 
 size_t nspt_split_ws_naive(int N, int T, int batch, int S) {
@@ -771,20 +861,39 @@ int nspt_split_mul_naive(int N, int T, int batch, int S, int log2r, bool rescale
     if (i == 0) return slice_any<double2>(S, A, T1, T1, 0, 0, 0, N, Q, 2, w.slA, w.expA, s);
     return slice_any<double2>(S, B, T1, T1, 0, 1, 0, N, Q, 3, w.slB, w.expB, s);
   }));
-  const long long rows = (long long)Q * N, E = (long long)N * N;
-  if (rescale_auto || log2r != 0) {
-    ProfScope ps(NSPT_STAGE_OTHER, st);
-    naive_shift_exps_kernel<<<(unsigned)((rows + 255) / 256), 256, 0, st>>>(w.expA, w.expB, N, T1, rows, log2r,
-                                                                           dlr);
-    TRYC(cudaGetLastError());
-  }
+  if (rescale_auto || log2r != 0) TRYS(naive_shift(w, N, T, batch, 1, 0, 1, 0, log2r, dlr, st));
   // a3 (Eq. 5): the pair GEMMs, accumulated in double-float
   TRYS(naive_gemms(w, N, T, batch, S, st));
-  {
-    ProfScope ps(NSPT_STAGE_OTHER, st);
-    const long long cnt = (long long)Q * E;
-    naive_out_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(w.Ct, w.Ct2, C, E, T1, cnt, log2r, dlr);
-    TRYC(cudaGetLastError());
+  return naive_out(w, C, N, T, batch, -1, log2r, dlr, st);
+}
+
+int nspt_split_bwd_naive(int N, int T, int batch, int S, int log2r, const double2* A, const double2* B,
+                         const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st) {
+  NaiveWs w = carve_naive(ws, N, T, batch, S, nullptr);
+  const int T1 = T + 1, Q = batch * T1;
+  TRYC(cudaMemsetAsync(w.err, 0, sizeof(int), st));
+  // with the rescale, gC_k stands for 2^(-k log2r) gC_k and A_m, B_m for 2^(m log2r) A_m, B_m
+  // (exponent shifts), so the order-j outputs come out scaled by 2^(-j log2r)
+  if (gA) {
+    // left: rows of gC_k (slots k); right: rows of (B_m^H)^T = conj(B_m) (slots T - m)
+    TRYS(fork_join(2, st, [&](int i, cudaStream_t s) -> int {
+      if (i == 0) return slice_any<double2>(S, G, T1, T1, 0, 0, 0, N, Q, 2, w.slA, w.expA, s);
+      return slice_any<double2>(S, B, T1, T1, 2, 0, 1, N, Q, 3, w.slB, w.expB, s);
+    }));
+    if (log2r) TRYS(naive_shift(w, N, T, batch, -1, 0, -1, T, log2r, nullptr, st));
+    TRYS(corr_gemms(w, N, T, batch, S, false, st));
+    TRYS(naive_out(w, gA, N, T, batch, 1, log2r, nullptr, st));
+  }
+  if (gB) {
+    // left: rows of A_m^H = conjugated columns of A_m (slots T - m); right: rows of gC_k^T =
+    // columns of gC_k (slots k)
+    TRYS(fork_join(2, st, [&](int i, cudaStream_t s) -> int {
+      if (i == 0) return slice_any<double2>(S, A, T1, T1, 2, 1, 1, N, Q, 2, w.slA, w.expA, s);
+      return slice_any<double2>(S, G, T1, T1, 0, 1, 0, N, Q, 3, w.slB, w.expB, s);
+    }));
+    if (log2r) TRYS(naive_shift(w, N, T, batch, -1, T, -1, 0, log2r, nullptr, st));
+    TRYS(corr_gemms(w, N, T, batch, S, true, st));
+    TRYS(naive_out(w, gB, N, T, batch, 1, log2r, nullptr, st));
   }
   return NSPT_OK;
 }

@@ -17,6 +17,9 @@ int nspt_split_mul(int N, int T, int batch, int M, int slices, int log2r, bool r
 size_t nspt_split_ws_naive(int N, int T, int batch, int slices);
 int nspt_split_mul_naive(int N, int T, int batch, int slices, int log2r, bool rescale_auto, const double2* A,
                          const double2* B, double2* C, void* ws, cudaStream_t st);
+// backward of the naive form with the split pair GEMMs (same workspace as the product)
+int nspt_split_bwd_naive(int N, int T, int batch, int slices, int log2r, const double2* A, const double2* B,
+                         const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
 int nspt_split_bwd(int N, int T, int batch, int M, int slices, int log2r, const double2* A, const double2* B,
                    const double2* G, double2* gA, double2* gB, void* ws, cudaStream_t st);
 // mode: NSPT_LMODE_* (tek.cuh); Yin: i X for NSPT_LMODE_UPDATE; log2r: every order transform of the

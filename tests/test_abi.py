@@ -97,9 +97,9 @@ def test_complex_mode_plans_need_no_gpu(L):
 
 
 def test_naive_split_plans_need_no_gpu(L):
-    """The naive form of the split products is planned for nspt_polymat_mul only: its
-    workspace holds the slices of every order of both operands (2 and 3 BF16 planes per
-    digit) and two double-float accumulators; the other entry points, and 3M, refuse it."""
+    """The naive form of the split products is planned for nspt_polymat_mul and its backward:
+    the workspace holds the slices of every order of both operands (2 and 3 BF16 planes per
+    digit) and two double-float accumulators; the TEK entry points, and 3M, refuse it."""
     import paper_2001_02835_b300 as n
     N, T, b, S = 225, 31, 4, 6
     kp = (N + 7) & ~7
@@ -108,16 +108,18 @@ def test_naive_split_plans_need_no_gpu(L):
     ws = n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="naive", prec="split"))
     assert need <= ws <= need + 2 * Q * N * 4 + 8 * 256
     assert n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="naive", prec="fp64")) == 0
-    for op in (n.OP_MUL_BACKWARD, n.OP_LANGEVIN, n.OP_MD, n.OP_UNITARIZE):
+    # the backward reuses the product's layout (its two operands' slices, two accumulators)
+    assert n.workspace_size(n.OP_MUL_BACKWARD, N, T, b, n.make_opts(algo="naive", prec="split")) == ws
+    for op in (n.OP_LANGEVIN, n.OP_MD, n.OP_UNITARIZE):
         assert n.workspace_size(op, N, T, b, n.make_opts(algo="naive", prec="split")) == 0
     o3 = n.make_opts(algo="naive", prec="split", complex_mode=3)
     assert n.workspace_size(n.OP_MUL, N, T, b, o3) == 0
     assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, N, T, b, ctypes.byref(o3), None) == -3
     on = n.make_opts(algo="naive", prec="split")
-    assert L.nspt_polymat_mul_backward(1 << 20, 2 << 20, 3 << 20, 4 << 20, 5 << 20, N, T, b, ctypes.byref(on),
-                                       None) == -3
-    # a valid request without its workspace: the workspace check refuses it
+    # valid requests without their workspace: the workspace check refuses them
     assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, N, T, b, ctypes.byref(on), None) == -4
+    assert L.nspt_polymat_mul_backward(1 << 20, 1 << 34, 1 << 36, 1 << 38, 1 << 40, N, T, b, ctypes.byref(on),
+                                       None) == -4
 
 
 def test_noise_argument_checks_need_no_gpu(L):

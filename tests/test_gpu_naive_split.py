@@ -33,7 +33,9 @@ def naive_split(nspt, A, B, C=None, **kw):
 # (N, T, batch): ragged N against the 128 x 48 tile and the 16-wide K steps; T = 0 is the
 # single pair; T = 15 has 136 pairs in 8 launches
 NAIVE_CASES = [(1, 0, 1), (3, 2, 2), (9, 8, 4), (33, 15, 2), (48, 7, 1), (130, 5, 1), (225, 3, 1),
-               (600, 1, 1)]
+               (600, 1, 1),
+               # the largest split size; the largest truncation order (129 launches); T = 63
+               (1024, 1, 1), (3, 255, 1), (10, 63, 3)]
 
 
 @pytest.mark.parametrize("N,T,batch", NAIVE_CASES)
@@ -133,3 +135,71 @@ def test_naive_split_su225_t31_full_oracle(nspt):
     err = max_order_rel(C, pm.star_dftconv(A, B))
     record("naive_split_su225_t31", err=err)
     assert err <= split_bound(6), err
+
+
+# ---- the backward (truncated correlations) of the naive split form ----
+
+BWD_CASES = [(1, 0, 1), (3, 2, 2), (9, 8, 4), (33, 15, 2), (130, 5, 1), (10, 63, 2)]
+
+
+@pytest.mark.parametrize("N,T,batch", BWD_CASES)
+def test_naive_split_backward_matches_oracle(nspt, N, T, batch):
+    g = syn.rng(8800 + N + 100 * T)
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    G = syn.gaussian(g, A.shape, 1.0)
+    rA, rB = pm.star_backward(A, B, G)
+    tA, tB, tG = dev(A), dev(B), dev(G)
+    errs = {}
+    for S in (6, 5):
+        gA, gB = nspt.polymat_mul_backward(tA, tB, tG, algo="naive", prec="split", slices=S)
+        errs[S] = max(max_order_rel(host(gA), rA), max_order_rel(host(gB), rB))
+    record("naive_split_backward", N=N, T=T, batch=batch, err_S6=errs[6], err_S5=errs[5])
+    assert errs[6] <= split_bound(6, "backward"), errs
+    if N >= 9:
+        assert errs[5] > split_bound(6, "backward"), errs
+
+
+def test_naive_split_backward_single_outputs_and_rescale_shift(nspt):
+    """gA alone and gB alone equal the pair; a fixed rescale only shifts exponents, so every
+    log2r gives the same bits."""
+    g = syn.rng(8900)
+    N, T, batch = 21, 15, 2
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    G = syn.gaussian(g, A.shape, 1.0)
+    tA, tB, tG = dev(A), dev(B), dev(G)
+    kw = dict(algo="naive", prec="split")
+    gA, gB = nspt.polymat_mul_backward(tA, tB, tG, **kw)
+    assert torch.equal(nspt.polymat_mul_backward(tA, tB, tG, need_gB=False, **kw)[0], gA)
+    assert torch.equal(nspt.polymat_mul_backward(tA, tB, tG, need_gA=False, **kw)[1], gB)
+    for lr in (-2, 3):
+        gA2, gB2 = nspt.polymat_mul_backward(tA, tB, tG, rescale_log2r=lr, **kw)
+        assert torch.equal(gA2, gA) and torch.equal(gB2, gB)
+
+
+def test_naive_split_backward_su225_t31_full_oracle(nspt):
+    """SU(225), O(g^31), one pair: every entry of gA and gB against the oracle's sums."""
+    g = syn.rng(9000)
+    N, T = 225, 31
+    A = syn.series_batch(g, N, T, 1)
+    B = syn.series_batch(g, N, T, 1)
+    G = syn.gaussian(g, A.shape, 1.0)
+    gA, gB = nspt.polymat_mul_backward(dev(A), dev(B), dev(G), algo="naive", prec="split")
+    rA, rB = pm.star_backward(A, B, G)
+    err = max(max_order_rel(host(gA), rA), max_order_rel(host(gB), rB))
+    record("naive_split_backward_su225_t31", err=err)
+    assert err <= split_bound(6, "backward"), err
+
+
+def test_naive_split_host_product(nspt):
+    """The host-memory product (pinned series, device slots) in the naive split form."""
+    g = syn.rng(9100)
+    N, T, batch = 17, 9, 3
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    C = nspt.polymat_mul_host(hA, hB, algo="naive", prec="split")
+    torch.cuda.synchronize()
+    assert max_order_rel(C.numpy(), pm.star(A, B)) <= split_bound(6)
