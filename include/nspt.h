@@ -290,7 +290,7 @@ NSPT_API int nspt_tek_noise(void* eta, int N, int count, unsigned long long seed
  *   A, B : host [batch][T+1][N][N] complex128;  C : host, same shape, no overlap
  * Workspace: nspt_workspace_size_host() bytes of DEVICE memory (two slots of
  * three series plus the product workspace of one element).
- * NSPT_RESCALE_AUTO is not supported here (NSPT_ERR_UNSUPPORTED).
+ * NSPT_RESCALE_AUTO fits the rescale per batch element (on the device).
  */
 NSPT_API size_t nspt_workspace_size_host(int N, int T, int batch, const nspt_opts* opts);
 NSPT_API int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, int batch,

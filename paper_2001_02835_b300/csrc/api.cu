@@ -1062,7 +1062,6 @@ int nspt_polymat_mul_host(const void* A, const void* B, void* C, int N, int T, i
   if (rc) return rc;
   if ((rc = make_plan(N, T, 1, opts, &pc, NSPT_OP_MUL))) return rc;
   if (!A || !B || !C) return NSPT_ERR_ARG;
-  if (pc.rescale_auto) return NSPT_ERR_UNSUPPORTED;  // it synchronises the stream per element
   const size_t bytes = (size_t)batch * (T + 1) * p.E * sizeof(double2);
   if (overlaps(C, bytes, A, bytes) || overlaps(C, bytes, B, bytes)) return NSPT_ERR_ALIAS;
   if ((rc = check_ws(opts, ws_host(pc)))) return rc;

@@ -148,12 +148,12 @@ def test_argument_checks_of_md_wilson_and_host_product(L):
     assert L.nspt_tek_wilson_loops(1 << 20, 9, 2, 1, 1, 2, (1 << 20) + 16, ctypes.byref(o), None) == -2
     assert L.nspt_workspace_size_wilson(9, 2, 1, 0, ctypes.byref(o)) == 0
     assert L.nspt_workspace_size_wilson(9, 2, 1, 2, ctypes.byref(o)) > 0
-    # host product: NULL buffers, C overlapping A, missing workspace, automatic rescale refused
+    # host product: NULL buffers, C overlapping A, missing workspace (also with the fitted rescale)
     assert L.nspt_polymat_mul_host(None, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(o), None) == -1
     assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, (1 << 20) + 16, 4, 3, 2, ctypes.byref(o), None) == -2
     assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(o), None) == -4
     auto = n.make_opts(algo="fft", prec="split", rescale_log2r=n.RESCALE_AUTO)
-    assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(auto), None) == -3
+    assert L.nspt_polymat_mul_host(1 << 20, 1 << 24, 1 << 28, 4, 3, 2, ctypes.byref(auto), None) == -4
     # two slots of three series of one element, plus the product workspace of one element
     ser = 4 * 4 * 16
     assert L.nspt_workspace_size_host(4, 3, 2, ctypes.byref(o)) >= 6 * ser

@@ -6,8 +6,9 @@ import pytest
 import torch
 
 import nspt_synth as syn
+from oracle import polymat as pm
 
-from tests.gpu_util import dev, host
+from tests.gpu_util import dev, host, max_order_rel, split_bound
 
 pytestmark = pytest.mark.gpu
 
@@ -41,7 +42,16 @@ def test_host_product_equals_device_product(nspt, prec, N, T, batch):
             assert np.abs(hC.numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_host_product_refuses_auto_rescale(nspt):
-    A = torch.zeros((1, 4, 3, 3), dtype=torch.complex128).pin_memory()
-    with pytest.raises(RuntimeError):
-        nspt.polymat_mul_host(A, A.clone(), prec="split", rescale_log2r=nspt.RESCALE_AUTO)
+def test_host_product_with_fitted_rescale(nspt):
+    """The fitted rescale in the host product is fitted per batch element on the device:
+    a series whose orders grow as 4^k stays within the split bound per order."""
+    g = syn.rng(2600)
+    N, T, batch = 20, 15, 3
+    w = 4.0 ** np.arange(T + 1)[None, :, None, None]
+    A = syn.series_batch(g, N, T, batch) * w
+    B = syn.series_batch(g, N, T, batch) * w
+    for algo in ("fft", "naive"):
+        C = nspt.polymat_mul_host(torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), algo=algo,
+                                  prec="split", rescale_log2r=nspt.RESCALE_AUTO)
+        torch.cuda.synchronize()
+        assert max_order_rel(C.numpy(), pm.star(A, B)) <= split_bound(6), algo
