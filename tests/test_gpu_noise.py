@@ -30,7 +30,7 @@ def nspt():
 
 @pytest.mark.parametrize("N,count,seed,counter", [(1, 3, 5, 0), (2, 5, 1, 7), (9, 16, 2001, 0),
                                                   (33, 7, (3 << 32) | 99, (1 << 32) + 5), (121, 4, 42, 123),
-                                                  (225, 2, 7, 0)])
+                                                  (225, 2, 7, 0), (1024, 1, 11, 3)])
 def test_noise_matches_oracle(nspt, N, count, seed, counter):
     eta = host(nspt.tek_noise(N, count, seed, counter))
     ref = nz.langevin_noise(N, count, seed, counter)
