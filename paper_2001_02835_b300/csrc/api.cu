@@ -39,11 +39,17 @@ struct Plan {
 };
 
 // allow_3m: the entry point takes complex_mode = 3 (the plain product)
-// op: the NSPT_OP_* call the plan is for (-1: a plan used inside another entry point).  The
-// product (NSPT_OP_MUL) alone takes the 3M variant; the product and its backward take the naive
-// form of the split products
+// plan of the Wilson loops (no workspace-query constant of its own)
+constexpr int kPlanWilson = 100;
+
+// op: the NSPT_OP_* call the plan is for (kPlanWilson: the Wilson loops; -1: a plan used inside
+// another entry point).  The product (NSPT_OP_MUL) alone takes the 3M variant; the entry points
+// whose products all go through the product call (the product, its backward, the unitarity
+// projection and the Wilson loops) take the naive form of the split products
 int make_plan(int N, int T, int batch, const nspt_opts* o, Plan* p, int op = -1) {
-  const bool product = op == NSPT_OP_MUL, naive_split_ok = product || op == NSPT_OP_MUL_BACKWARD;
+  const bool product = op == NSPT_OP_MUL;
+  const bool naive_split_ok = product || op == NSPT_OP_MUL_BACKWARD || op == NSPT_OP_UNITARIZE ||
+                              op == kPlanWilson;
   nspt_opts d;
   nspt_opts_default(&d);
   if (!o) o = &d;
@@ -871,7 +877,7 @@ int nspt_polymat_mul_backward(const void* A, const void* B, const void* gC, void
 
 int nspt_tek_unitarize(void* U, int N, int T, int batch, int special, const nspt_opts* opts, void* stream) {
   Plan p;
-  int rc = make_plan(N, T, batch, opts, &p);
+  int rc = make_plan(N, T, batch, opts, &p, NSPT_OP_UNITARIZE);
   if (rc) return rc;
   if (!U) return NSPT_ERR_ARG;
   if ((rc = check_ws(opts, ws_unitarize(p)))) return rc;
@@ -1022,14 +1028,14 @@ int nspt_tek_md_trajectory(void* U, void* P, const void* eta_refresh, int N, int
 
 size_t nspt_workspace_size_wilson(int N, int T, int batch, int amax, const nspt_opts* opts) {
   Plan p;
-  if (make_plan(N, T, batch, opts, &p) || amax < 1 || amax > kWilsonMaxExtent) return 0;
+  if (make_plan(N, T, batch, opts, &p, kPlanWilson) || amax < 1 || amax > kWilsonMaxExtent) return 0;
   return ws_wilson(p, amax);
 }
 
 int nspt_tek_wilson_loops(const void* U, int N, int T, int batch, int flux, int amax, void* W, const nspt_opts* opts,
                           void* stream) {
   Plan p;
-  int rc = make_plan(N, T, batch, opts, &p);
+  int rc = make_plan(N, T, batch, opts, &p, kPlanWilson);
   if (rc) return rc;
   if (!U || !W || amax < 1 || amax > kWilsonMaxExtent) return NSPT_ERR_ARG;
   const int L = (int)llround(sqrt((double)N));

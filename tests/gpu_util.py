@@ -26,6 +26,14 @@ bound times the growth (0.34 for the Langevin step at SU(121), O(g^31); 1.09 for
 at SU(225), O(g^31) with the fitted rescale; 1.72 for the Wilson loops at SU(121), O(g^31);
 0.21 for the backward; 0.14 for the unitarity projection).
 
+The naive split form (one tensor-core GEMM per pair of orders, no transforms) makes each
+pair's error relative to that pair's own size, so its chained computations (the unitarity
+projection and the Wilson loops, whose products all go through the product call) neither mix
+the orders nor grow with T: they take the product bound itself (CHAIN["naive_chain"] = 1, no
+growth), over four times the largest observed ratio (0.07: the projection with the U(1) phase at
+N = 25, T = 15; the Wilson loops stayed below 0.03); the projection with one slice fewer
+exceeds it (4.6e-12 to 2.3e-11 for N = 9..121).
+
 The 3M products (three real products per complex product, `complex_mode=3`) take the
 product bound times CHAIN["product3m"]: their imaginary part P3 - P1 - P2 comes from the
 digits of re + im, sliced at twice the row bound, and cancels; the largest observed ratio to
@@ -44,7 +52,7 @@ F_OBS = 2.0 ** -44            # max err of the product cases at S = 7, 8
 SPLIT_C = 4 * C_OBS
 SPLIT_FLOOR = 4 * F_OBS
 CHAIN = {"product": 1.0, "product3m": 2.0, "backward": 2.0, "langevin": 2.0, "md": 6.0, "wilson": 8.0,
-         "unitarize": 2.0}
+         "unitarize": 2.0, "naive_chain": 1.0}
 
 
 def dev(x: np.ndarray) -> torch.Tensor:
@@ -73,9 +81,12 @@ def max_order_rel(X, ref) -> float:
     return float(e.max()) if e.size else 0.0
 
 
-def split_bound(S: int, kind: str = "product", T: int = 0) -> float:
+def split_bound(S: int, kind: str = "product", T: int = 0, algo: str = "fft") -> float:
     """Stated per-order bound of the split form with S slices (module docstring); T, the
-    truncation order, matters for the chained kinds only."""
+    truncation order, matters for the chained kinds of FFT-CONV only; with algo="naive" the
+    chained kinds take the naive form's bound ("naive_chain")."""
+    if algo == "naive" and kind in ("langevin", "md", "wilson", "unitarize"):
+        kind = "naive_chain"
     growth = 2.0 ** max(0.0, (T - 24) / 8.0) if kind in ("langevin", "md", "wilson", "unitarize") else 1.0
     return CHAIN[kind] * growth * (SPLIT_C * 2.0 ** -(8 * S - 1) + SPLIT_FLOOR)
 

@@ -97,9 +97,10 @@ def test_complex_mode_plans_need_no_gpu(L):
 
 
 def test_naive_split_plans_need_no_gpu(L):
-    """The naive form of the split products is planned for nspt_polymat_mul and its backward:
-    the workspace holds the slices of every order of both operands (2 and 3 BF16 planes per
-    digit) and two double-float accumulators; the TEK entry points, and 3M, refuse it."""
+    """The naive form of the split products is planned for nspt_polymat_mul, its backward, the
+    unitarity projection and the Wilson loops: the product workspace holds the slices of every
+    order of both operands (2 and 3 BF16 planes per digit) and two double-float accumulators;
+    the Langevin step and MD, and 3M, refuse it."""
     import paper_2001_02835_b300 as n
     N, T, b, S = 225, 31, 4, 6
     kp = (N + 7) & ~7
@@ -110,8 +111,11 @@ def test_naive_split_plans_need_no_gpu(L):
     assert n.workspace_size(n.OP_MUL, N, T, b, n.make_opts(algo="naive", prec="fp64")) == 0
     # the backward reuses the product's layout (its two operands' slices, two accumulators)
     assert n.workspace_size(n.OP_MUL_BACKWARD, N, T, b, n.make_opts(algo="naive", prec="split")) == ws
-    for op in (n.OP_LANGEVIN, n.OP_MD, n.OP_UNITARIZE):
+    for op in (n.OP_LANGEVIN, n.OP_MD):
         assert n.workspace_size(op, N, T, b, n.make_opts(algo="naive", prec="split")) == 0
+    # the unitarity projection and the Wilson loops run all their products through the product call
+    assert n.workspace_size(n.OP_UNITARIZE, N, T, b, n.make_opts(algo="naive", prec="split")) > ws
+    assert L.nspt_workspace_size_wilson(N, T, b, 2, ctypes.byref(n.make_opts(algo="naive", prec="split"))) > ws
     o3 = n.make_opts(algo="naive", prec="split", complex_mode=3)
     assert n.workspace_size(n.OP_MUL, N, T, b, o3) == 0
     assert L.nspt_polymat_mul(1 << 20, 1 << 34, 1 << 36, N, T, b, ctypes.byref(o3), None) == -3

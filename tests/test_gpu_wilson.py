@@ -19,8 +19,8 @@ def nspt():
     return n
 
 
-def split_tol(T):
-    return split_bound(6, "wilson", T)
+def split_tol(T, algo="fft"):
+    return split_bound(6, "wilson", T, algo)
 
 
 def per_order(got, ref):
@@ -31,14 +31,14 @@ def per_order(got, ref):
     return float((num / np.where(den == 0, den.max(), den)).max())
 
 
-@pytest.mark.parametrize("algo,prec", [("naive", "fp64"), ("fft", "fp64"), ("fft", "split")])
+@pytest.mark.parametrize("algo,prec", [("naive", "fp64"), ("fft", "fp64"), ("fft", "split"), ("naive", "split")])
 @pytest.mark.parametrize("L,flux,T,batch,amax", [(3, 1, 4, 2, 2), (2, 1, 6, 1, 3), (5, 2, 3, 1, 2)])
 def test_wilson_loops_match_oracle(nspt, algo, prec, L, flux, T, batch, amax):
     g = syn.rng(7300 + 10 * L + T)
     U = syn.link_series(g, L, flux, T, batch)
     ref = tek.wilson_loops(U, tek.twist_phases(L, flux), amax)
     got = host(nspt.tek_wilson_loops(dev(U), flux, amax, algo=algo, prec=prec))
-    tol = 1e-12 if prec == "fp64" else split_tol(T)
+    tol = 1e-12 if prec == "fp64" else split_tol(T, algo)
     err = per_order(got, ref)
     record("wilson", algo=algo, prec=prec, L=L, T=T, err=err)
     assert err <= tol, err
