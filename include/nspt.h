@@ -72,9 +72,10 @@ enum { NSPT_OP_MUL = 0, NSPT_OP_MUL_BACKWARD = 1, NSPT_OP_LANGEVIN = 2, NSPT_OP_
 typedef struct nspt_opts {
   int algo;            /* NSPT_ALGO_*; default NSPT_ALGO_AUTO */
   int prec;            /* NSPT_PREC_*; default NSPT_PREC_FP64; NSPT_PREC_SPLIT needs N <= 1024,
-                          and the FFT form except in nspt_polymat_mul, nspt_polymat_mul_host and
-                          nspt_polymat_mul_backward (and their workspace queries), which also
-                          take the naive form (else NSPT_ERR_UNSUPPORTED) */
+                          and the FFT form except in nspt_polymat_mul, nspt_polymat_mul_host,
+                          nspt_polymat_mul_backward, nspt_tek_unitarize and
+                          nspt_tek_wilson_loops (and their workspace queries), which also take
+                          the naive form (else NSPT_ERR_UNSUPPORTED) */
   int fft_len;         /* M; 0 = smallest power of two >= 2(T+1); else a power of two
                           >= 2(T+1) and <= 512 (wrap-free linear convolution, Step 1) */
   int slices;          /* split form: BF16 slices per operand, 0 = default 6, range 2..8 */
