@@ -185,3 +185,25 @@ def test_grouped_and_noise_stay_in_bounds(nspt):
     assert E.intact() and ctr.intact()
     assert int(ctr.tensor((1,), torch.int64).item()) == 1
     assert torch.equal(E.tensor((count, N, N)), nspt.tek_noise(N, count, 3, 0))
+
+
+def test_naive_split_wilson_and_projection_stay_in_bounds(nspt):
+    """The Wilson loops and the unitarity projection on the naive split products."""
+    L = nspt.lib()
+    Lx, flux, T, batch, amax = 3, 1, 4, 2, 2
+    N = Lx * Lx
+    U = syn.link_series(syn.rng(9800), Lx, flux, T, batch)
+    kw = dict(algo="naive", prec="split")
+    gU = guarded_copy(U)
+    W = Guarded(batch * amax * amax * (T + 1) * 16)
+    opts = nspt.make_opts(**kw)
+    ws = guarded_ws(nspt, L.nspt_workspace_size_wilson(N, T, batch, amax, ctypes.byref(opts)), opts)
+    assert L.nspt_tek_wilson_loops(gU.ptr, N, T, batch, flux, amax, W.ptr, ctypes.byref(opts), None) == 0
+    assert W.intact() and ws.intact()
+    check_inputs([(gU, U)])
+    rW = nspt.tek_wilson_loops(torch.from_numpy(U).cuda(), flux, amax, **kw)
+    assert torch.equal(W.tensor(tuple(rW.shape)), rW)
+    opts = nspt.make_opts(**kw)
+    ws = guarded_ws(nspt, L.nspt_workspace_size(nspt.OP_UNITARIZE, N, T, batch, ctypes.byref(opts)), opts)
+    assert L.nspt_tek_unitarize(gU.ptr, N, T, batch, 1, ctypes.byref(opts), None) == 0
+    assert gU.intact() and ws.intact()
