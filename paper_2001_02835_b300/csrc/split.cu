@@ -165,25 +165,29 @@ __device__ __forceinline__ void store_bf16(__nv_bfloat16* o, const float (&d)[W]
 }
 
 // W adjacent entries per lane and chunk (4: 8-byte stores, 8: 16-byte stores); NQ chunks of
-// 32 W entries per row
-template <int S, int NQ, int W, bool SUM3>
+// LPR W entries per row, LPR lanes per row: 32, or 16 with two rows per warp (TWO, for rows of at
+// most 16 W entries, which then keep every lane busy)
+template <int S, int NQ, int W, bool SUM3, bool TWO = false>
 __global__ void __launch_bounds__(256, NQ * W <= 8 ? 4 : 2)
 slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int rev, int conj, int N, int Kp, int P,
                   __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   constexpr bool sum3 = SUM3;
+  constexpr int LPR = TWO ? 16 : 32, RPW = 32 / LPR;
   const int q = blockIdx.y;
   const int b = q / M, p = q % M;
   const int sp = rev ? (M - p) % M : p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int r = blockIdx.x * RB + warp;
-  if (r >= N) return;
-  const float4* src = X + ((long long)b * bstride + sp) * N * N + (long long)r * N;
+  const int ln = lane % LPR, r0 = (blockIdx.x * RB + warp) * RPW;
+  const int r = r0 + lane / LPR;
+  if (r0 >= N) return;                 // every row of the warp is past the end
+  const bool rv = r < N;               // (TWO) the warp's second row may be past the end
+  const float4* src = X + ((long long)b * bstride + sp) * N * N + (long long)(rv ? r : r0) * N;
   float4 v[NQ][W];
 #pragma unroll
   for (int t = 0; t < NQ; ++t) {
-    const int k = W * lane + 32 * W * t;
+    const int k = W * ln + LPR * W * t;
 #pragma unroll
-    for (int c = 0; c < W; ++c) v[t][c] = (k + c < N) ? src[k + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int c = 0; c < W; ++c) v[t][c] = (rv && k + c < N) ? src[k + c] : make_float4(0.f, 0.f, 0.f, 0.f);
   }
   int mx = -100000;
 #pragma unroll
@@ -191,9 +195,10 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
 #pragma unroll
     for (int c = 0; c < W; ++c) mx = max(mx, exp_bound(v[t][c]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  for (int o = LPR / 2; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (!rv) return;                     // no shuffles below
   const int e = (mx == -100000) ? -1000 : mx;  // |x| < 2^e for every part of the row
-  if (lane == 0) exps[(long long)q * N + r] = e;
+  if (ln == 0) exps[(long long)q * N + r] = e;
   const long long plane = (long long)N * Kp;
   __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
   float f1, f2, g1, g2;
@@ -201,7 +206,7 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   pow2_pair(-e - 1, g1, g2);
 #pragma unroll
   for (int t = 0; t < NQ; ++t) {
-    const int k = W * lane + 32 * W * t;
+    const int k = W * ln + LPR * W * t;
     if (k >= N) break;
     // residuals of x 2^-e (|.| < 1) for the real and imaginary parts of the W entries,
     // and (3M) of (re + im) 2^-(e+1)
@@ -251,19 +256,20 @@ slice_rows_kernel(const float4* __restrict__ X, long long bstride, int M, int re
   }
 }
 
-template <int S, int NQ, int W>
+template <int S, int NQ, int W, bool TWO = false>
 int launch_slice_rows(const float4* X, long long bstride, int M, int rev, int conj, int N, int Kp, int Q, int P,
                       int sum3, __nv_bfloat16* out, int* exps, cudaStream_t st) {
-  dim3 grid((N + RB - 1) / RB, Q);
+  constexpr int rows = RB * (TWO ? 2 : 1);   // rows per CTA
+  dim3 grid((N + rows - 1) / rows, Q);
   ProfScope ps(NSPT_STAGE_SLICE, st);
   if (sum3) {
     if constexpr (S <= 6) {
-      slice_rows_kernel<S, NQ, W, true><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+      slice_rows_kernel<S, NQ, W, true, TWO><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
     } else {
       return NSPT_ERR_UNSUPPORTED;
     }
   } else {
-    slice_rows_kernel<S, NQ, W, false><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
+    slice_rows_kernel<S, NQ, W, false, TWO><<<grid, 256, 0, st>>>(X, bstride, M, rev, conj, N, Kp, P, out, exps);
   }
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
@@ -277,7 +283,9 @@ int launch_slice(const InT* X, long long bstride, int M, int rev, int trans, int
   if constexpr (std::is_same<InT, float4>::value) {
     if (!trans && N <= 512) {
       if (rev == 2) return NSPT_ERR_UNSUPPORTED;   // the row form takes rev = 0, 1
-      if (N <= 128) return launch_slice_rows<S, 1, 4>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      // two rows per warp up to 16 W entries a row
+      if (N <= 64) return launch_slice_rows<S, 1, 4, true>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
+      if (N <= 128) return launch_slice_rows<S, 1, 8, true>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
       if (N <= 256) return launch_slice_rows<S, 1, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
       return launch_slice_rows<S, 2, 8>(X, bstride, M, rev, conj, N, Kp, Q, P, sum3, out, exps, st);
     }
