@@ -109,16 +109,16 @@ int nspt_tek_noise(void* eta, int N, int count, unsigned long long seed, unsigne
   const long long nb = ((long long)N * N + 1) / 2, total = nb * count;
   // grid-stride over the blocks: eight CTAs of 256 threads per SM at most
   int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
-                                                cudaSuccess)
-    return NSPT_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   const long long want = (total + 255) / 256, cap = 8LL * sms;
   const int grid = (int)(want < cap ? want : cap);
   {
     ProfScope ps(NSPT_STAGE_TEK, st);
     noise_gauss_kernel<<<grid, 256, 0, st>>>((double2*)eta, N, nb, total, seed, counter, d_counter);
   }
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) { nspt_set_last_cuda_error(e); return NSPT_ERR_CUDA; }
   {
     ProfScope ps(NSPT_STAGE_TEK, st);
