@@ -365,6 +365,18 @@ NSPT_API int nspt_device_status(const nspt_opts* opts, void* stream);
 NSPT_API int nspt_debug_wait_budget(long long ns);
 
 /*
+ * Test hook, host only (no GPU needed): the pair-GEMM schedule of the naive split
+ * form at truncation order T (0..255) -- kind 0: the product's pairs (l, k - l);
+ * 1: the backward's gA pairs; 2: its gB pairs.  Writes 7 ints per batched GEMM,
+ * (launch, accumulator, left slot, right slot, first output order, count, plain),
+ * for as many as fit in `cap` ints of `out`, and returns the number of GEMMs
+ * (NSPT_ERR_ARG for a bad T or kind).  Within a GEMM the slots rise by 1 and the
+ * output order by 2 per pair.  Product slots are orders (l, then k - l); the
+ * backward's operand indexed by m = k - j sits at slot T - m, the other at slot k.
+ */
+NSPT_API int nspt_debug_pair_schedule(int T, int kind, int* out, int cap);
+
+/*
  * Stage entry points of the split form, for stage tests and timing.
  *
  * nspt_split_slices (FFT-CONV Step 3 operand preparation): cuts each of the Q

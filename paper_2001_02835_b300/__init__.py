@@ -68,6 +68,7 @@ _SIGS = {
     "nspt_workspace_size_wilson": (_sz, [_i, _i, _i, _i, ctypes.POINTER(Opts)]),
     "nspt_workspace_size_host": (_sz, [_i, _i, _i, ctypes.POINTER(Opts)]),
     "nspt_debug_wait_budget": (_i, [ctypes.c_longlong]),
+    "nspt_debug_pair_schedule": (_i, [_i, _i, ctypes.POINTER(ctypes.c_int), _i]),
     "nspt_polymat_mul_host": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),
     "nspt_tek_wilson_loops": (_i, [_vp, _i, _i, _i, _i, _i, _vp, ctypes.POINTER(Opts), _vp]),
     "nspt_polymat_mul": (_i, [_vp, _vp, _vp, _i, _i, _i, ctypes.POINTER(Opts), _vp]),

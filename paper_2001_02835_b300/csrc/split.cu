@@ -743,45 +743,69 @@ int naive_out(const NaiveWs& w, double2* C, int N, int T, int batch, int sgn, in
   return NSPT_OK;
 }
 
-// the launches of the schedule above
-int naive_gemms(const NaiveWs& w, int N, int T, int batch, int S, cudaStream_t st) {
+// One batched GEMM of a pair schedule, the same for every batch element: cnt pair products whose
+// left and right slices start at slots l0 and r0 (both rising by one) and whose outputs start at
+// order o0 (rising by two), written into accumulator acc (0 or 1) plainly or added to it.
+struct PairGroup { int launch, acc, l0, r0, o0, cnt, plain; };
+
+// the product's schedule above: launch i holds set i (accumulator 0, plain for i = 0) and set
+// T - i (accumulator 1, zeroed first)
+std::vector<PairGroup> product_schedule(int T) {
+  std::vector<PairGroup> g;
+  auto add_set = [&](int launch, int i, int acc, bool plain) {
+    const int ds[2] = {i == 0 ? 0 : -i, i + 1};
+    for (int d : ds) {
+      if (d > T) continue;
+      const int j0 = std::max(0, -d);
+      const int cnt = (T - d) / 2 - j0 + 1;  // j = j0 .. floor((T - d) / 2)
+      if (cnt >= 1) g.push_back(PairGroup{launch, acc, j0 + d, j0, 2 * j0 + d, cnt, plain ? 1 : 0});
+    }
+  };
+  for (int i = 0; 2 * i <= T; ++i) {
+    add_set(i, i, 0, i == 0);
+    if (T - i > i) add_set(i, T - i, 1, false);
+  }
+  return g;
+}
+
+// enqueues a schedule's launches in order, each group expanded over the batch, at most
+// NSPT_SPLIT_MAX_PROBLEMS problems per launch
+int run_pair_schedule(const NaiveWs& w, const std::vector<PairGroup>& sched, int N, int T, int batch, int S,
+                      cudaStream_t st) {
   const int T1 = T + 1, Kp = kpad(N);
   const long long sa = (long long)S * 2 * N * Kp, sb = (long long)S * 3 * N * Kp, E = (long long)N * N;
   std::vector<SplitGemmArgs> probs;
-  // the GEMMs of set i into accumulator C (plain: the first write of every order it touches)
-  auto add_set = [&](int i, float4* Cacc, bool plain) {
-    const int ds[2] = {i == 0 ? 0 : -i, i + 1};
-    for (int b = 0; b < batch; ++b) {
-      for (int d : ds) {
-        if (d > T) continue;
-        const int j0 = std::max(0, -d);
-        const int cnt = (T - d) / 2 - j0 + 1;  // j = j0 .. floor((T - d) / 2)
-        if (cnt < 1) continue;
-        const long long l0 = j0 + d, k0 = 2LL * j0 + d, base = (long long)b * T1;
+  for (size_t gi = 0; gi < sched.size();) {
+    probs.clear();
+    const int launch = sched[gi].launch;
+    for (; gi < sched.size() && sched[gi].launch == launch; ++gi) {
+      const PairGroup& g = sched[gi];
+      if (g.acc == 1 && !w.Ct2) return NSPT_ERR_ARG;
+      for (int b = 0; b < batch; ++b) {
+        const long long base = (long long)b * T1;
         SplitGemmArgs a;
-        a.slicesA = w.slA + (base + l0) * sa;
-        a.slicesB = w.slB + (base + j0) * sb;
-        a.expA = w.expA + (base + l0) * N;
-        a.expB = w.expB + (base + j0) * N;
-        a.C = Cacc + (base + k0) * E;
+        a.slicesA = w.slA + (base + g.l0) * sa;
+        a.slicesB = w.slB + (base + g.r0) * sb;
+        a.expA = w.expA + (base + g.l0) * N;
+        a.expB = w.expB + (base + g.r0) * N;
+        a.C = (g.acc == 0 ? w.Ct : w.Ct2) + (base + g.o0) * E;
         a.ldc_q = 2 * E;
-        a.N = N; a.Kp = Kp; a.Q = cnt; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = default_bn(N);
-        a.alpha = make_double2(1.0, 0.0); a.use_alpha = 0; a.accumulate = !plain;
+        a.N = N; a.Kp = Kp; a.Q = g.cnt; a.S = S; a.num_sms = g_num_sms; a.err = w.err; a.bn = default_bn(N);
+        a.alpha = make_double2(1.0, 0.0); a.use_alpha = 0; a.accumulate = !g.plain;
         probs.push_back(a);
       }
     }
-  };
-  if (T > 0) TRYC(cudaMemsetAsync(w.Ct2, 0, (size_t)batch * T1 * E * sizeof(float4), st));
-  for (int i = 0; 2 * i <= T; ++i) {
-    probs.clear();
-    add_set(i, w.Ct, i == 0);
-    if (T - i > i) add_set(T - i, w.Ct2, false);
     for (size_t o = 0; o < probs.size(); o += NSPT_SPLIT_MAX_PROBLEMS) {
       const int n = (int)std::min<size_t>(NSPT_SPLIT_MAX_PROBLEMS, probs.size() - o);
       TRYS(nspt_split_gemm_batch(probs.data() + o, n, S, default_bn(N), g_num_sms, st));
     }
   }
   return NSPT_OK;
+}
+
+int naive_gemms(const NaiveWs& w, int N, int T, int batch, int S, cudaStream_t st) {
+  if (T > 0) TRYC(cudaMemsetAsync(w.Ct2, 0, (size_t)batch * (T + 1) * N * N * sizeof(float4), st));
+  return run_pair_schedule(w, product_schedule(T), N, T, batch, S, st);
 }
 
 // The backward's schedule.  gA_j = sum_k gC_k (B_{k-j})^H and gB_j = sum_k (A_{k-j})^H gC_k
@@ -793,9 +817,7 @@ int naive_gemms(const NaiveWs& w, int N, int T, int batch, int S, cudaStream_t s
 // s > T (both zeroed first); in each, the even groups in ascending size go with the odd groups
 // in descending size, one such pair per accumulator per launch, so that the launches hold
 // about T + 2 GEMMs per batch element each.
-int corr_gemms(const NaiveWs& w, int N, int T, int batch, int S, bool left_rev, cudaStream_t st) {
-  const int T1 = T + 1, Kp = kpad(N);
-  const long long sa = (long long)S * 2 * N * Kp, sb = (long long)S * 3 * N * Kp, E = (long long)N * N;
+std::vector<PairGroup> corr_schedule(int T, bool left_rev) {
   struct Grp { int s, k0, cnt; };
   std::vector<std::vector<Grp>> lists[2];
   for (int a = 0; a < 2; ++a) {
@@ -817,41 +839,36 @@ int corr_gemms(const NaiveWs& w, int N, int T, int batch, int S, bool left_rev, 
       lists[a].push_back(l);
     }
   }
-  if (!lists[1].empty() && !w.Ct2) return NSPT_ERR_ARG;
-  TRYC(cudaMemsetAsync(w.Ct, 0, (size_t)batch * T1 * E * sizeof(float4), st));
-  if (w.Ct2) TRYC(cudaMemsetAsync(w.Ct2, 0, (size_t)batch * T1 * E * sizeof(float4), st));
-  std::vector<SplitGemmArgs> probs;
-  for (size_t li = 0; li < std::max(lists[0].size(), lists[1].size()); ++li) {
-    probs.clear();
+  std::vector<PairGroup> out;
+  for (size_t li = 0; li < std::max(lists[0].size(), lists[1].size()); ++li)
     for (int a = 0; a < 2; ++a) {
       if (li >= lists[a].size()) continue;
       for (const Grp& g : lists[a][li]) {
-        const long long up = g.k0, down = T - g.s + g.k0;   // slots of the k- and m-indexed operands
-        const long long l0 = left_rev ? down : up, r0 = left_rev ? up : down, j0 = 2LL * g.k0 - g.s;
-        for (int b = 0; b < batch; ++b) {
-          const long long base = (long long)b * T1;
-          SplitGemmArgs x;
-          x.slicesA = w.slA + (base + l0) * sa;
-          x.slicesB = w.slB + (base + r0) * sb;
-          x.expA = w.expA + (base + l0) * N;
-          x.expB = w.expB + (base + r0) * N;
-          x.C = (a == 0 ? w.Ct : w.Ct2) + (base + j0) * E;
-          x.ldc_q = 2 * E;
-          x.N = N; x.Kp = Kp; x.Q = g.cnt; x.S = S; x.num_sms = g_num_sms; x.err = w.err; x.bn = default_bn(N);
-          x.alpha = make_double2(1.0, 0.0); x.use_alpha = 0; x.accumulate = 1;
-          probs.push_back(x);
-        }
+        const int up = g.k0, down = T - g.s + g.k0;   // slots of the k- and m-indexed operands
+        out.push_back(PairGroup{(int)li, a, left_rev ? down : up, left_rev ? up : down, 2 * g.k0 - g.s, g.cnt, 0});
       }
     }
-    for (size_t o = 0; o < probs.size(); o += NSPT_SPLIT_MAX_PROBLEMS) {
-      const int n = (int)std::min<size_t>(NSPT_SPLIT_MAX_PROBLEMS, probs.size() - o);
-      TRYS(nspt_split_gemm_batch(probs.data() + o, n, S, default_bn(N), g_num_sms, st));
-    }
-  }
-  return NSPT_OK;
+  return out;
+}
+
+int corr_gemms(const NaiveWs& w, int N, int T, int batch, int S, bool left_rev, cudaStream_t st) {
+  const size_t bytes = (size_t)batch * (T + 1) * N * N * sizeof(float4);
+  TRYC(cudaMemsetAsync(w.Ct, 0, bytes, st));
+  if (w.Ct2) TRYC(cudaMemsetAsync(w.Ct2, 0, bytes, st));
+  return run_pair_schedule(w, corr_schedule(T, left_rev), N, T, batch, S, st);
 }
 
 }  // namespace
+
+int nspt_debug_pair_schedule(int T, int kind, int* out, int cap) {
+  if (T < 0 || T > 255 || kind < 0 || kind > 2 || cap < 0 || (cap > 0 && !out)) return NSPT_ERR_ARG;
+  const std::vector<PairGroup> g = kind == 0 ? product_schedule(T) : corr_schedule(T, kind == 2);
+  for (size_t i = 0; i < g.size() && (int)(7 * i + 7) <= cap; ++i) {
+    const int v[7] = {g[i].launch, g[i].acc, g[i].l0, g[i].r0, g[i].o0, g[i].cnt, g[i].plain};
+    for (int c = 0; c < 7; ++c) out[7 * i + c] = v[c];
+  }
+  return (int)g.size();
+}
 
 size_t nspt_split_ws_naive(int N, int T, int batch, int S) {
   size_t total = 0;
