@@ -55,3 +55,17 @@ def test_host_product_with_fitted_rescale(nspt):
                                   prec="split", rescale_log2r=nspt.RESCALE_AUTO)
         torch.cuda.synchronize()
         assert max_order_rel(C.numpy(), pm.star(A, B)) <= split_bound(6), algo
+
+
+def test_host_product_3m_matches_device_product(nspt):
+    """The host-memory product with three real products per complex product (3M)."""
+    g = syn.rng(2700)
+    N, T, batch = 33, 7, 3
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    kw = dict(algo="fft", prec="split", complex_mode=3)
+    C = nspt.polymat_mul_host(torch.from_numpy(A).pin_memory(), torch.from_numpy(B).pin_memory(), **kw)
+    torch.cuda.synchronize()
+    ref = host(nspt.polymat_mul(dev(A), dev(B), **kw))
+    assert np.abs(C.numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+    assert max_order_rel(C.numpy(), pm.star(A, B)) <= split_bound(6, "product3m")
