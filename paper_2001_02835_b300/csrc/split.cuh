@@ -3,9 +3,19 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <functional>
+
 #include "../../include/nspt.h"
 
 int nspt_split_init();
+// row pitch of the digit slices: N rounded up to 8 BF16 values (16 bytes)
+inline int nspt_split_kpad(int N) { return (N + 7) & ~7; }
+int nspt_split_num_sms();
+// untuned tile width (complex columns) of the tensor-core GEMMs for products of size <= nmax
+int nspt_split_default_bn(int nmax);
+// runs chain(i, stream) for i < count on the library's side streams, forked from and joined
+// back to st (on st itself when the side streams are missing)
+int nspt_split_fork_join(int count, cudaStream_t st, const std::function<int(int, cudaStream_t)>& chain);
 // cm: complex products as 4 real products (the embedding, every entry point) or 3 (3M: products only)
 size_t nspt_split_ws_mul(int N, int T, int batch, int M, int slices, int cm = 4);
 size_t nspt_split_ws_bwd(int N, int T, int batch, int M, int slices);
