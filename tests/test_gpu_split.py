@@ -330,3 +330,20 @@ def test_split_device_status_ok(nspt):
                                      nspt._stream_ptr(tA.device))
     assert rc == 0
     assert nspt.lib().nspt_device_status(ctypes.byref(opts), nspt._stream_ptr(tA.device)) == 0
+
+
+@pytest.mark.parametrize("N", [63, 64, 65, 100, 128, 129, 256, 257])
+def test_split_mul_at_row_slicer_boundaries(nspt, N):
+    """Sizes at the row slicer's layout changes: a half-warp per row with 4 entries per lane up to
+    N = 64 and 8 up to 128, a warp per row with 8 entries per lane up to 256, two chunks above;
+    both complex forms (the 3M form slices a third plane, re + im), and the tile-width change
+    at N = 128."""
+    g = syn.rng(5800 + N)
+    T, batch = 3, 2
+    A = syn.series_batch(g, N, T, batch)
+    B = syn.series_batch(g, N, T, batch)
+    ref = pm.star(A, B)
+    tA, tB = dev(A), dev(B)
+    for cm in (4, 3):
+        err = max_order_rel(host(nspt.polymat_mul(tA, tB, algo="fft", prec="split", complex_mode=cm)), ref)
+        assert err <= split_bound(6, "product" if cm == 4 else "product3m"), (cm, err)
