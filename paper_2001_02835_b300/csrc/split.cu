@@ -66,7 +66,7 @@ __device__ __forceinline__ int slice_swz(int k) { return k ^ ((k >> 3) & 3); }
 // RBK output rows per CTA: 8 for row sources, 16 for column sources (trans), whose staging then
 // reads 256-byte runs of 16 consecutive entries
 template <int S, typename InT, int RBK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int trans, int conj, int N, int Kp,
              int P, __nv_bfloat16* __restrict__ out, int* __restrict__ exps) {
   extern __shared__ __align__(16) unsigned char tile_raw[];
@@ -124,8 +124,16 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
     const int r = r0 + rr;
     if (lane == 0) exps[(long long)q * N + r] = e;
     __nv_bfloat16* orow = out + (long long)q * S * P * plane + (long long)r * Kp;
-    // four adjacent entries per lane, one 8-byte store per digit plane
-    for (int k = 4 * lane; k < N; k += 128) {
+    // four adjacent entries per lane; lanes 2j and 2j + 1 hold entries 8j..8j+7 of a chunk and
+    // trade halves (one shuffle per word), so that every plane leaves in 16-byte stores: the even
+    // lane stores the re (and -re: sign bits flipped, exact) digits of the eight entries, the odd
+    // lane the im digits.  Every lane runs every chunk, so the shuffles see the whole warp.  (Held
+    // to three CTAs per SM by the launch bounds: 80 registers, a few bytes of spills.)
+    const bool odd = lane & 1;
+    const int k8 = 8 * (lane >> 1);
+    for (int k0 = 0; k0 < N; k0 += 128) {
+      const int k = k0 + 4 * lane;
+      const bool act = k0 + k8 < N;   // the pair's eight entries start inside the row (and Kp)
       float re[4][S], im[4][S];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
@@ -134,11 +142,21 @@ slice_kernel(const InT* __restrict__ X, long long bstride, int M, int rev, int t
       }
 #pragma unroll
       for (int i = 0; i < S; ++i) {
-        __nv_bfloat16* o = orow + (long long)P * i * plane + k;
-        *reinterpret_cast<uint2*>(o) = pack_bf16x4(re[0][i], re[1][i], re[2][i], re[3][i]);
-        *reinterpret_cast<uint2*>(o + plane) = pack_bf16x4(im[0][i], im[1][i], im[2][i], im[3][i]);
-        if (P == 3)
-          *reinterpret_cast<uint2*>(o + 2 * plane) = pack_bf16x4(-re[0][i], -re[1][i], -re[2][i], -re[3][i]);
+        const uint2 pr = pack_bf16x4(re[0][i], re[1][i], re[2][i], re[3][i]);
+        const uint2 pi = pack_bf16x4(im[0][i], im[1][i], im[2][i], im[3][i]);
+        const uint2 send = odd ? pr : pi;
+        const unsigned gx = __shfl_xor_sync(0xffffffffu, send.x, 1), gy = __shfl_xor_sync(0xffffffffu, send.y, 1);
+        if (!act) continue;
+        __nv_bfloat16* o = orow + (long long)P * i * plane + k0 + k8;
+        if (!odd) {
+          const uint4 w = make_uint4(pr.x, pr.y, gx, gy);
+          *reinterpret_cast<uint4*>(o) = w;
+          if (P == 3)
+            *reinterpret_cast<uint4*>(o + 2 * plane) =
+                make_uint4(w.x ^ 0x80008000u, w.y ^ 0x80008000u, w.z ^ 0x80008000u, w.w ^ 0x80008000u);
+        } else {
+          *reinterpret_cast<uint4*>(o + plane) = make_uint4(gx, gy, pi.x, pi.y);
+        }
       }
     }
   }
